@@ -1,0 +1,407 @@
+"""Benchmark of the FCM pixel pass on GB300.
+
+Workload (one "step" = one whole FCM segmentation, Algorithm 1 of
+arXiv:1601.00072, to convergence): the 256^3 uint8 ellipsoid phantom with a
++/-20 % bias field and Rician-like noise (sigma 6), cast to FP32, C = 4,
+m = 2, eps = 1e-5 on max|dU|, max_iter = 300, initial U drawn from a seeded
+uniform Dirichlet (seed 103). Inputs (x, U^0) are resident in HBM before the
+timed region; each step reads U^0 (read only) and writes U^k and V^k.
+
+Metric: pixel-iterations per second (n x iterations, summed over steps and
+ranks, over the max-over-ranks timed duration). The working set (x 67 MB,
+U^0 268 MB, U 268 MB) exceeds the 129 MB L2, so no flush is needed between
+steps.
+
+With ``--gpus N`` under torchrun every rank runs its own copy of the workload
+(weak scaling; the pass has no cross-GPU exchange when images are independent).
+
+``--impl reference`` times the FP64 CPU oracle instead, on a bounded sample of
+the same workload (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "volume256"
+C = 4
+EPS = 1e-5
+MAX_ITER = 300
+METRIC = "FCM pixel-iterations/s (256^3 volume, C=4, m=2, eps=1e-5)"
+UNIT = "pixel-iter/s"
+PROFILE = os.path.join(ROOT, "profiles", "fcm_pass_volume256.md")
+KERNEL_SOURCES = ["paper_1601_00072_gb300/csrc/fcm_single_inst.cu",
+                  "paper_1601_00072_gb300/csrc/fcm_device.cuh",
+                  "paper_1601_00072_gb300/csrc/fcm_internal.h"]
+
+
+def kernel_hash() -> str:
+    h = hashlib.sha256()
+    for rel in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def measured_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def profiled_traffic():
+    """DRAM bytes per launch of the iteration kernel from the committed ncu
+    summary, if it was taken on the current kernel source; else None."""
+    try:
+        text = open(PROFILE).read()
+    except OSError:
+        return None
+    mh = re.search(r"kernel source hash:\s*`?([0-9a-f]{16})", text)
+    mt = re.search(r"dram bytes per launch \(scaled to volume256\):\s*([0-9.eE+]+)", text)
+    if not mh or not mt or mh.group(1) != kernel_hash():
+        return None
+    return float(mt.group(1))
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.lines = []
+        self.error = None
+
+    def start(self):
+        import torch
+        ident = str(self.dev)
+        try:
+            uuid = str(torch.cuda.get_device_properties(self.dev).uuid)
+            ident = uuid if uuid.startswith("GPU-") else "GPU-" + uuid
+        except Exception:
+            pass
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", ident, f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception as e:  # nvidia-smi missing
+            self.error = str(e)
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+        time.sleep(0.3)
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.15)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[3:7]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup():
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def allreduce(value: float, op: str, world: int) -> float:
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def load_workload(m: float):
+    import phantom
+    x, _, u0, c = phantom.single_image(WORKLOAD)
+    assert c == C
+    return x, u0
+
+
+def cpu_sample(x, u0):
+    """The bounded CPU sample: the 16 middle slices (1,048,576 voxels)."""
+    plane = 256 * 256
+    lo, hi = 120 * plane, 136 * plane
+    return x[lo:hi], np.ascontiguousarray(u0[:, lo:hi]), "voxels of slices z=120..135 (1,048,576 voxels)"
+
+
+def run_cpu_oracle_sample(x, u0, m: float, iters: int):
+    """The FP64 oracle, as it stands, on the sample for a fixed iteration count."""
+    import oracle
+    xs, us, desc = cpu_sample(x, u0)
+    t0 = time.perf_counter()
+    r = oracle.fcm(xs.astype(np.float64), C, m, 0.0, iters, U0=us, want_U=False)
+    dt = time.perf_counter() - t0
+    return xs.size * r["iters"] / dt, f"{desc}, {r['iters']} iterations (eps=0)", dt
+
+
+def cpu_baseline_leg(x, u0, m, gV, gU_sample, idx, g_iters, g_J):
+    """Everything that touches the oracle: its timed CPU throughput on a
+    bounded sample, and the FP64 reference of the timed workload for the
+    precision report (256-bin form of the oracle, exact for uint8 data)."""
+    import oracle
+    value, sample, dt = run_cpu_oracle_sample(x, u0, m, iters=30)
+    base = {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": sample, "seconds": round(dt, 2)}
+    eps = float(np.float32(EPS))
+    o = oracle.fcm_quantized(x, C, m, eps, MAX_ITER, U0=u0)
+    d_iters = g_iters - o["iters"]
+    if o["iters"] > g_iters:
+        o = oracle.fcm_quantized(x, C, m, eps, g_iters, U0=u0)
+    ref_V = o["V"]
+    Ubins = oracle.memberships(np.arange(256.0), ref_V, m)
+    ref_U = Ubins[:, x[idx]]
+    prec = {
+        "vs": "FP64 oracle (256-bin form), same x and U0",
+        "center_rel_err": float(np.max(np.abs(gV - ref_V) / np.maximum(np.abs(ref_V), 1.0))),
+        "max_abs_dU_sampled": float(np.max(np.abs(gU_sample - ref_U))) if o["iters"] == g_iters else None,
+        "label_agreement_sampled": float(np.mean(np.argmax(gU_sample, 0) == np.argmax(ref_U, 0))),
+        "d_iters": int(d_iters),
+        "J_rel_err": float(abs(g_J - o["J"][-1]) / abs(o["J"][-1])) if o["iters"] == g_iters else None,
+        "U_sample_voxels": int(idx.size),
+    }
+    return base, prec
+
+
+def bench_ours(args):
+    import torch
+
+    world, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    from paper_1601_00072_gb300 import _build
+    if rank == 0 or world == 1:
+        _build.build()
+    barrier(world)
+    from paper_1601_00072_gb300.fcm import FCM
+
+    m = args.m
+    x, u0 = load_workload(m)
+    n = x.size
+    dev = torch.device("cuda", local)
+    xd = torch.from_numpy(x.astype(np.float32)).to(dev)
+    U0d = torch.from_numpy(u0).to(dev)
+    Ud = torch.empty_like(U0d)
+    Vd = torch.empty(C, dtype=torch.float32, device=dev)
+    h = FCM(local)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        return h.run(xd, C, m, EPS, MAX_ITER, U0=U0d, U=Ud, V=Vd)
+
+    for _ in range(args.warmup):
+        r = step()
+    torch.cuda.synchronize(dev)
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    barrier(world)
+    torch.cuda.synchronize(dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    iters = []
+    for _ in range(args.steps):
+        r = step()
+        iters.append(r.iters)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    barrier(world)
+    clocks = sampler.stop()
+    ms_local = e0.elapsed_time(e1)
+    ms = allreduce(ms_local, "max", world)
+    units_local = float(n) * sum(iters)
+    units = allreduce(units_local, "sum", world)
+    value = units / (ms / 1e3)
+
+    # roofline of the pass kernels over the timed region (algorithmic bytes:
+    # pass 0 reads x and U^0; each iteration reads x and U^{k-1}, writes U^k)
+    bytes_local = sum((4 * n + 4 * C * n) + it * (4 * n + 8 * C * n) for it in iters)
+    launches = sum(1 + it for it in iters)
+    achieved = bytes_local / (ms_local / 1e3) / 1e9
+    peak, peak_kind = measured_peak()
+    traffic = profiled_traffic()
+
+    # end to end through the C ABI with host buffers: H2D of x and U^0,
+    # D2H of U^k and V^k inside the call
+    e2e = None
+    if not args.no_e2e:
+        xh = torch.from_numpy(x.astype(np.float32)).pin_memory()
+        U0h = torch.from_numpy(u0).pin_memory()
+        Uh = torch.empty_like(U0h).pin_memory()
+        Vh = torch.empty(C, dtype=torch.float32).pin_memory()
+        h.run(xh, C, m, EPS, MAX_ITER, U0=U0h, U=Uh, V=Vh)
+        e_steps = max(3, min(args.steps, 10))
+        barrier(world)
+        t0 = time.perf_counter()
+        e_units = 0
+        for _ in range(e_steps):
+            rr = h.run(xh, C, m, EPS, MAX_ITER, U0=U0h, U=Uh, V=Vh)
+            e_units += n * rr.iters
+        dt = time.perf_counter() - t0
+        dt = allreduce(dt, "max", world)
+        e_units = allreduce(float(e_units), "sum", world)
+        e2e = {"value": e_units / dt, "unit": UNIT,
+               "h2d_bytes_per_step": 4 * n + 4 * C * n,
+               "d2h_bytes_per_step": 4 * C * n + 4 * C}
+
+    out = {
+        "metric": METRIC,
+        "value": value,
+        "unit": UNIT,
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": "256^3 uint8 ellipsoid phantom (bias +/-20%, Rician sigma 6) as f32, "
+                               "C=4, m=%g, eps=1e-5, max_iter=300, Dirichlet U0 seed 103" % m,
+                   "n_pixels": n, "iters_per_step": statistics.median(iters),
+                   "parallelism": f"replicas x{world}",
+                   "l2": "working set 603 MB > 129 MB L2; no flush"},
+        "gpu_launches": launches,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "peak_source": f"{peak_kind} copy bandwidth",
+                     "kernel": "k_fcm_pass (all passes of the step, algorithmic bytes "
+                               "36 B/pixel-iteration at C=4)"},
+        "clocks": clocks,
+        "e2e": e2e,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        idx = np.random.default_rng(0).choice(n, 100_000, replace=False)
+        gU_sample = Ud[:, torch.from_numpy(idx).to(dev)].cpu().numpy().astype(np.float64)
+        gV = Vd.cpu().numpy().astype(np.float64)
+        base, prec = cpu_baseline_leg(x, u0, m, gV, gU_sample, idx, r.iters, r.J)
+        out["cpu_baseline"] = base
+        out["precision"] = prec
+    h.close()
+    if rank == 0:
+        print(json.dumps(out))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def bench_reference(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    x, u0 = load_workload(args.m)
+    xs, us, desc = cpu_sample(x, u0)
+    # a smaller slab per step keeps --steps K --warmup W within minutes
+    plane = 256 * 256
+    xs, us = xs[:4 * plane], np.ascontiguousarray(us[:, :4 * plane])
+    import oracle
+    it = 10
+
+    def step():
+        return oracle.fcm(xs.astype(np.float64), C, args.m, 0.0, it, U0=us, want_U=False)
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    units = 0
+    for _ in range(args.steps):
+        r = step()
+        units += xs.size * r["iters"]
+    dt = time.perf_counter() - t0
+    value = units / dt
+    sample = f"262,144 voxels (slices z=120..123) x {it} iterations per step"
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "impl": "reference",
+           "config": {"workload": "256^3 uint8 ellipsoid phantom as f64 (sampled), C=4, m=%g" % args.m},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--m", type=float, default=2.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours" and not os.environ.get("FCM_BENCH_ALLOW_SHORT"):
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    if args.impl == "reference":
+        bench_reference(args)
+    else:
+        bench_ours(args)
+
+
+if __name__ == "__main__":
+    main()

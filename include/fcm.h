@@ -1,0 +1,148 @@
+/*
+ * fcm.h — C ABI of the GB300 Fuzzy C-Means library (libfcm_gb300.so).
+ *
+ * The library runs the per-iteration pixel pass of Fuzzy C-Means image
+ * segmentation (arXiv:1601.00072, "GPU-Based Fuzzy C-Means Clustering
+ * Algorithm for Image Segmentation") on one CUDA device:
+ *
+ *   membership (Eq. 4)  u_ij = 1 / sum_k (d_ij / d_ik)^(2/(m-1)),
+ *                       d_ij = |x_i - v_j|   (Sec. 2.1; grey level feature)
+ *   centers    (Eq. 3)  v_j  = sum_i u_ij^m x_i / sum_i u_ij^m
+ *   objective  (Eq. 1)  J_m  = sum_i sum_j u_ij^m d_ij^2
+ *   loop (Algorithm 1)  V from U, then U from V, until the change of U
+ *                       between iterations falls below eps.
+ *
+ * Conventions shared by every entry point:
+ *   - Pixels x: n floats (grey levels; the paper's data is uint8 cast to
+ *     float). Memberships U: C*n floats, cluster-major, U[j*n + i] (the
+ *     paper's 1-D layout of the 3-D membership array, Sec. 5.1).
+ *     Centers V: C floats.
+ *   - 1 <= C <= FCM_MAX_CLUSTERS; m > 1 (Eq. 4's exponent 2/(m-1) needs it);
+ *     eps >= 0; max_iter >= 1; n >= 1.
+ *   - Zero distance (a pixel exactly equal to one or more centers): those
+ *     clusters share the membership equally, every other cluster gets 0
+ *     (Bezdek's rule; the paper does not define the case).
+ *   - Stopping test: iteration k computes U^k from V^k and
+ *     delta_k = max_{i,j} |u^k_ij - u^{k-1}_ij| (L-infinity, Algorithm 1
+ *     step 3); the run stops with (U^k, V^k) when delta_k < eps (strict),
+ *     else V^{k+1} = centers(U^k). V^1 comes from the initial U^0, or from
+ *     U^0 = membership(V^0) when initial centers are given.
+ *   - Arithmetic: memberships and per-thread sums in FP32; the sums across
+ *     thread blocks (center numerators/denominators and J) in FP64.
+ *   - Ownership: the caller owns x, U, V and every output array; the library
+ *     never frees them. A handle owns its device workspace, CUDA graphs and
+ *     autotuning cache, and frees them in fcm_destroy.
+ *   - Streams: work is issued on the handle's stream. Entry points that fill
+ *     host-side results (iters, reports, statuses) synchronise that stream
+ *     before returning.
+ *   - Errors: every entry point returns an int status (FCM_OK or
+ *     FCM_NOT_CONVERGED on success, a negative FCM_ERR_* otherwise);
+ *     fcm_status_string names it. A handle is not thread-safe.
+ */
+#ifndef FCM_GB300_H
+#define FCM_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FCM_MAX_CLUSTERS 8
+
+/* Status codes. */
+#define FCM_OK 0                 /* converged: delta_k < eps                 */
+#define FCM_NOT_CONVERGED 1      /* stopped at max_iter; results are valid   */
+#define FCM_ERR_INVALID_ARG (-1) /* bad size, m <= 1, null pointer, ...      */
+#define FCM_ERR_CUDA (-2)        /* a CUDA runtime call failed               */
+#define FCM_ERR_OOM (-3)         /* workspace allocation failed              */
+#define FCM_ERR_BAD_INPUT (-4)   /* NaN/Inf in x or V0, or NaN/Inf/negative U0 */
+#define FCM_ERR_TIMEOUT (-5)     /* a bounded device-side wait gave up       */
+
+/* Report flags. */
+#define FCM_FLAG_EMPTY_CLUSTER 1 /* some sum_i u_ij^m underflowed to 0: v_j kept */
+
+/* Initialisation modes (Algorithm 1 step 2). */
+#define FCM_INIT_U 0 /* U holds the initial membership U^0 on entry         */
+#define FCM_INIT_V 1 /* V holds initial centers V^0; U^0 = membership(V^0)  */
+
+/* Run options (bit flags). */
+#define FCM_OPT_TRACE 1    /* record delta_k, J_k and V^k of every iteration */
+#define FCM_OPT_NO_GRAPH 2 /* host-driven loop instead of a CUDA graph WHILE node */
+
+typedef struct fcm_ctx* fcm_handle;
+
+/* Result of one run. V64 holds the final centers as the FP64 quotients of the
+ * combined sums (V holds the same values rounded to float). */
+typedef struct {
+    int iters;      /* k of the returned (U^k, V^k)                         */
+    int status;     /* FCM_OK, FCM_NOT_CONVERGED or a negative FCM_ERR_*     */
+    int flags;      /* FCM_FLAG_* bits                                       */
+    int C;
+    double delta;   /* delta_k of the last iteration (L-infinity)            */
+    double J;       /* J_m(U^k, V^k), Eq. 1                                  */
+    double V64[FCM_MAX_CLUSTERS];
+} fcm_report;
+
+/* Create a handle on CUDA device `device`, issuing work on `cuda_stream`
+ * (a cudaStream_t; NULL = the legacy default stream). Allocates nothing on
+ * the device until the first run. Returns FCM_ERR_CUDA for a bad device. */
+int fcm_create(fcm_handle* out, int device, void* cuda_stream);
+
+/* Rebind the handle to another stream of the same device. */
+int fcm_set_stream(fcm_handle h, void* cuda_stream);
+
+/* Free the handle's workspace and graphs (never caller buffers). NULL is a
+ * no-op. */
+void fcm_destroy(fcm_handle h);
+
+/*
+ * fcm_run — Algorithm 1 on one image (Sec. 2.1, Eqs. 1, 3, 4; the paper's
+ * center kernels of Sec. 4.2 and membership kernel of Sec. 4.3 are one fused
+ * pass here, and its host-side convergence check of Sec. 4.3 runs on the
+ * device).
+ *
+ *   x         n floats, device or host memory (host memory is staged through
+ *             the handle's workspace; pinned host memory copies fastest).
+ *   n         number of pixels, >= 1.
+ *   C, m, eps, max_iter   as above.
+ *   init_mode FCM_INIT_U or FCM_INIT_V.
+ *   U0        nullable; C*n floats, cluster-major, device or host, read only.
+ *             With FCM_INIT_U and U0 != NULL the initial membership is read
+ *             from U0 and left unchanged; with U0 == NULL (or U0 == U) it is
+ *             read from U. Ignored with FCM_INIT_V.
+ *   U         C*n floats, cluster-major, device or host. Out: U^k (the run
+ *             updates it in place from the first iteration on).
+ *   V         C floats, device or host. In: V^0 when init_mode == FCM_INIT_V.
+ *             Out: V^k.
+ *   options   FCM_OPT_* bits.
+ *   rep       nullable; filled on return.
+ *
+ * Returns FCM_OK, FCM_NOT_CONVERGED, or an error. On FCM_ERR_BAD_INPUT the
+ * contents of U and V are unspecified.
+ */
+int fcm_run(fcm_handle h, const float* x, int64_t n, int C, float m,
+            float eps, int max_iter, int init_mode, const float* U0, float* U,
+            float* V, int options, fcm_report* rep);
+
+/* Copy the trace of the last run made with FCM_OPT_TRACE into host arrays
+ * (each nullable): delta[k-1], J[k-1] and V[(k-1)*C + j] for k = 1..iters.
+ * `cap` is the number of iterations the arrays hold. Returns the number of
+ * iterations copied, or a negative error. */
+int fcm_get_trace(fcm_handle h, double* delta, double* J, double* V, int cap);
+
+/* Text of the last error recorded on the handle ("" if none). */
+const char* fcm_last_error(fcm_handle h);
+
+/* Name of a status code (static string). */
+const char* fcm_status_string(int status);
+
+/* Library version as "major.minor.patch" (static string). */
+const char* fcm_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FCM_GB300_H */

@@ -1,0 +1,95 @@
+"""ctypes declarations of the C ABI in ``include/fcm.h``.
+
+Loading fails loudly when the library has not been built: there is no CPU
+fallback anywhere in this package.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from . import _build
+
+FCM_MAX_CLUSTERS = 8
+FCM_OK = 0
+FCM_NOT_CONVERGED = 1
+FCM_ERR_INVALID_ARG = -1
+FCM_ERR_CUDA = -2
+FCM_ERR_OOM = -3
+FCM_ERR_BAD_INPUT = -4
+FCM_ERR_TIMEOUT = -5
+FCM_FLAG_EMPTY_CLUSTER = 1
+FCM_INIT_U = 0
+FCM_INIT_V = 1
+FCM_OPT_TRACE = 1
+FCM_OPT_NO_GRAPH = 2
+
+
+class fcm_report(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("status", ctypes.c_int), ("flags", ctypes.c_int),
+                ("C", ctypes.c_int), ("delta", ctypes.c_double), ("J", ctypes.c_double),
+                ("V64", ctypes.c_double * FCM_MAX_CLUSTERS)]
+
+
+_vp = ctypes.c_void_p
+_i = ctypes.c_int
+_f = ctypes.c_float
+_i64 = ctypes.c_int64
+_dp = ctypes.POINTER(ctypes.c_double)
+
+# (name, restype, argtypes) of every entry point declared in include/fcm.h
+SIGNATURES = [
+    ("fcm_create", _i, [ctypes.POINTER(_vp), _i, _vp]),
+    ("fcm_set_stream", _i, [_vp, _vp]),
+    ("fcm_destroy", None, [_vp]),
+    ("fcm_run", _i, [_vp, _vp, _i64, _i, _f, _f, _i, _i, _vp, _vp, _vp, _i,
+                     ctypes.POINTER(fcm_report)]),
+    ("fcm_get_trace", _i, [_vp, _dp, _dp, _dp, _i]),
+    ("fcm_last_error", ctypes.c_char_p, [_vp]),
+    ("fcm_status_string", ctypes.c_char_p, [_i]),
+    ("fcm_version", ctypes.c_char_p, []),
+]
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = False):
+    """Load ``libfcm_gb300.so`` and declare its signatures."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = library_path()
+    if not os.path.exists(path):
+        if not build_if_missing:
+            raise RuntimeError(
+                f"the FCM CUDA library is not built ({path} missing); "
+                "run `python -c 'import __graft_entry__ as g; g.build()'` first")
+        _build.build()
+    lib = ctypes.CDLL(path)
+    for name, res, args in SIGNATURES:
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+class FcmError(RuntimeError):
+    def __init__(self, status: int, message: str = ""):
+        self.status = status
+        name = load().fcm_status_string(status).decode()
+        super().__init__(f"{name} ({status})" + (f": {message}" if message else ""))
+
+
+def check(status: int, handle=None) -> int:
+    if status < 0:
+        msg = ""
+        if handle is not None:
+            raw = load().fcm_last_error(handle)
+            msg = raw.decode() if raw else ""
+        raise FcmError(status, msg)
+    return status

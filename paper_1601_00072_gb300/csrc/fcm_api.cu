@@ -1,0 +1,414 @@
+// Host runtime and C ABI of the single-image FCM path.
+//
+// A handle owns a device workspace (run state, per-block partials, optional
+// trace, staging buffers for host inputs) and one instantiated CUDA graph per
+// launch shape. A graph is
+//
+//     first pass (P_ACCUM0 or P_INITV)  ->  WHILE(cond) { P_ITER pass }
+//
+// where the last block of every pass sets `cond` with
+// cudaGraphSetConditional, so the whole of Algorithm 1 (arXiv:1601.00072,
+// Sec. 2.1) runs on the device after one graph launch. The paper copies U to
+// the host every iteration to test convergence (Sec. 4.3); here the only
+// host-device traffic of a run is the 200-byte state upload, the state
+// read-back and, for host buffers, the input/output copies.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <tuple>
+
+#include "fcm.h"
+#include "fcm_device.cuh"
+#include "fcm_internal.h"
+#include "fcm_runtime.h"
+
+using namespace fcm;
+
+namespace {
+
+SingleTable g_table;
+std::once_flag g_table_once;
+
+void init_table() {
+    std::memset(&g_table, 0, sizeof(g_table));
+    register_single_c1(g_table);
+    register_single_c2(g_table);
+    register_single_c3(g_table);
+    register_single_c4(g_table);
+    register_single_c5(g_table);
+    register_single_c6(g_table);
+    register_single_c7(g_table);
+    register_single_c8(g_table);
+}
+
+bool is_device_pointer(const void* p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace
+
+namespace fcm {
+
+int ctx_fail(fcm_ctx* h, cudaError_t e, const char* what) {
+    if (h) {
+        char buf[256];
+        std::snprintf(buf, sizeof(buf), "%s: %s", what, cudaGetErrorString(e));
+        h->last_error = buf;
+    }
+    return e == cudaErrorMemoryAllocation ? FCM_ERR_OOM : FCM_ERR_CUDA;
+}
+
+int ctx_invalid(fcm_ctx* h, const char* what) {
+    if (h) h->last_error = what;
+    return FCM_ERR_INVALID_ARG;
+}
+
+int ctx_grow(fcm_ctx* h, void** p, size_t* cap, size_t bytes, const char* what) {
+    if (*cap >= bytes) return 0;
+    if (*p) cudaFree(*p);
+    *p = nullptr;
+    *cap = 0;
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        return ctx_fail(h, e, what);
+    }
+    *cap = bytes;
+    return 0;
+}
+
+}  // namespace fcm
+
+#define CK(call)                                                  \
+    do {                                                          \
+        cudaError_t e_ = (call);                                  \
+        if (e_ != cudaSuccess) return ctx_fail(h, e_, #call);     \
+    } while (0)
+
+namespace {
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+int ensure_single_workspace(fcm_ctx* h) {
+    if (h->d_st) return 0;
+    CK(cudaMalloc(&h->d_st, sizeof(RunState)));
+    CK(cudaMemset(h->d_st, 0, sizeof(RunState)));
+    CK(cudaMallocHost(&h->h_st, sizeof(RunState)));
+    h->partial_blocks = h->num_sms * 32;
+    CK(cudaMalloc(&h->d_partials, sizeof(double) * SLOTS_MAX * h->partial_blocks));
+    return 0;
+}
+
+int blocks_per_sm(fcm_ctx* h, PassFn k) {
+    auto it = h->occupancy.find((const void*)k);
+    if (it != h->occupancy.end()) return it->second;
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, (const void*)k, NT, 0) != cudaSuccess || nb < 1) {
+        cudaGetLastError();
+        nb = 1;
+    }
+    h->occupancy[(const void*)k] = nb;
+    return nb;
+}
+
+int build_graph(fcm_ctx* h, PassFn kfirst, PassFn kiter, int nblocks, GraphEntry* out) {
+    cudaGraph_t g = nullptr;
+    CK(cudaGraphCreate(&g, 0));
+    cudaGraphConditionalHandle cond;
+    cudaError_t e = cudaGraphConditionalHandleCreate(&cond, g, 1, cudaGraphCondAssignDefault);
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(g);
+        return ctx_fail(h, e, "cudaGraphConditionalHandleCreate");
+    }
+    int use_cond = 1;
+    void* args[4] = {&h->d_st, &h->d_partials, &cond, &use_cond};
+    cudaKernelNodeParams kp;
+    std::memset(&kp, 0, sizeof(kp));
+    kp.func = (void*)kfirst;
+    kp.gridDim = dim3(nblocks);
+    kp.blockDim = dim3(NT);
+    kp.kernelParams = args;
+    cudaGraphNode_t n1, n2, n3;
+    e = cudaGraphAddKernelNode(&n1, g, nullptr, 0, &kp);
+    // cudaGraphNodeParams holds a union without a default constructor:
+    // zero-initialised raw storage stands in for it.
+    alignas(cudaGraphNodeParams) unsigned char cp_raw[sizeof(cudaGraphNodeParams)];
+    std::memset(cp_raw, 0, sizeof(cp_raw));
+    cudaGraphNodeParams& cp = *reinterpret_cast<cudaGraphNodeParams*>(cp_raw);
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = cond;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    if (e == cudaSuccess) e = cudaGraphAddNode(&n2, g, &n1, nullptr, 1, &cp);
+    if (e == cudaSuccess) {
+        cudaGraph_t body = cp.conditional.phGraph_out[0];
+        kp.func = (void*)kiter;
+        e = cudaGraphAddKernelNode(&n3, body, nullptr, 0, &kp);
+    }
+    cudaGraphExec_t ex = nullptr;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&ex, g, 0);
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(g);
+        return ctx_fail(h, e, "building the FCM graph");
+    }
+    out->graph = g;
+    out->exec = ex;
+    return 0;
+}
+
+int run_host_loop(fcm_ctx* h, PassFn kfirst, PassFn kiter, int nblocks) {
+    const cudaGraphConditionalHandle none = 0;
+    kfirst<<<nblocks, NT, 0, h->stream>>>(h->d_st, h->d_partials, none, 0);
+    CK(cudaGetLastError());
+    int chunk = 4;
+    int launched = 0;
+    const int max_iter = h->h_st->max_iter;
+    int* done_host = &h->h_done;
+    while (true) {
+        const int todo = std::min(chunk, max_iter - launched);
+        for (int t = 0; t < todo; ++t)
+            kiter<<<nblocks, NT, 0, h->stream>>>(h->d_st, h->d_partials, none, 0);
+        CK(cudaGetLastError());
+        launched += todo;
+        CK(cudaMemcpyAsync(done_host, &h->d_st->done, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+        CK(cudaStreamSynchronize(h->stream));
+        if (*done_host || launched >= max_iter) break;
+        chunk = std::min(chunk * 2, 64);
+    }
+    return 0;
+}
+
+}  // namespace
+
+extern "C" {
+
+int fcm_create(fcm_handle* out, int device, void* cuda_stream) {
+    if (!out) return FCM_ERR_INVALID_ARG;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+        cudaGetLastError();
+        return FCM_ERR_CUDA;
+    }
+    std::call_once(g_table_once, init_table);
+    fcm_ctx* h = new fcm_ctx();
+    h->device = device;
+    h->stream = (cudaStream_t)cuda_stream;
+    DeviceGuard g(device);
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) {
+        delete h;
+        return FCM_ERR_CUDA;
+    }
+    h->num_sms = prop.multiProcessorCount;
+    h->max_smem_optin = (int)prop.sharedMemPerBlockOptin;
+    h->device_name = prop.name;
+    *out = h;
+    return FCM_OK;
+}
+
+int fcm_set_stream(fcm_handle h, void* cuda_stream) {
+    if (!h) return FCM_ERR_INVALID_ARG;
+    h->stream = (cudaStream_t)cuda_stream;
+    return FCM_OK;
+}
+
+void fcm_destroy(fcm_handle h) {
+    if (!h) return;
+    {
+        DeviceGuard g(h->device);
+        cudaStreamSynchronize(h->stream);
+        for (auto& kv : h->graphs) {
+            if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+            if (kv.second.graph) cudaGraphDestroy(kv.second.graph);
+        }
+        if (h->d_st) cudaFree(h->d_st);
+        if (h->h_st) cudaFreeHost(h->h_st);
+        if (h->d_partials) cudaFree(h->d_partials);
+        if (h->d_trace) cudaFree(h->d_trace);
+        if (h->d_stage_x) cudaFree(h->d_stage_x);
+        if (h->d_stage_U) cudaFree(h->d_stage_U);
+        fcm_release_batched(h);
+        fcm_release_mlp(h);
+    }
+    delete h;
+}
+
+const char* fcm_status_string(int s) {
+    switch (s) {
+        case FCM_OK: return "FCM_OK";
+        case FCM_NOT_CONVERGED: return "FCM_NOT_CONVERGED";
+        case FCM_ERR_INVALID_ARG: return "FCM_ERR_INVALID_ARG";
+        case FCM_ERR_CUDA: return "FCM_ERR_CUDA";
+        case FCM_ERR_OOM: return "FCM_ERR_OOM";
+        case FCM_ERR_BAD_INPUT: return "FCM_ERR_BAD_INPUT";
+        case FCM_ERR_TIMEOUT: return "FCM_ERR_TIMEOUT";
+        default: return "FCM_UNKNOWN_STATUS";
+    }
+}
+
+const char* fcm_version(void) { return "0.1.0"; }
+
+const char* fcm_last_error(fcm_handle h) {
+    return h ? h->last_error.c_str() : "null handle";
+}
+
+int fcm_run(fcm_handle h, const float* x, int64_t n, int C, float m, float eps, int max_iter,
+            int init_mode, const float* U0, float* U, float* V, int options, fcm_report* rep) {
+    if (!h) return FCM_ERR_INVALID_ARG;
+    if (!x || !U || !V) return ctx_invalid(h, "null x, U or V");
+    if (n < 1) return ctx_invalid(h, "n must be >= 1");
+    if (C < 1 || C > FCM_MAX_CLUSTERS) return ctx_invalid(h, "C must be in [1, 8]");
+    if (!(m > 1.0f) || !std::isfinite(m)) return ctx_invalid(h, "m must be a finite number > 1");
+    if (!(eps >= 0.0f) || !std::isfinite(eps)) return ctx_invalid(h, "eps must be finite and >= 0");
+    if (max_iter < 1) return ctx_invalid(h, "max_iter must be >= 1");
+    if (init_mode != FCM_INIT_U && init_mode != FCM_INIT_V) return ctx_invalid(h, "bad init_mode");
+    if (n > (int64_t)1 << 40) return ctx_invalid(h, "n too large");
+
+    DeviceGuard g(h->device);
+    int rc = ensure_single_workspace(h);
+    if (rc) return rc;
+
+    // Host buffers are staged through the workspace.
+    if (init_mode == FCM_INIT_U && !U0) U0 = U;
+    const bool x_dev = is_device_pointer(x);
+    const bool U_dev = is_device_pointer(U);
+    const bool V_dev = is_device_pointer(V);
+    const bool U0_dev = init_mode == FCM_INIT_U && is_device_pointer(U0);
+    const size_t xb = sizeof(float) * (size_t)n, Ub = sizeof(float) * (size_t)n * C;
+    const float* dx = x;
+    float* dU = U;
+    const float* dU0 = init_mode == FCM_INIT_U ? U0 : nullptr;
+    if (!x_dev) {
+        if ((rc = ctx_grow(h, (void**)&h->d_stage_x, &h->stage_x_cap, xb, "staging x"))) return rc;
+        CK(cudaMemcpyAsync(h->d_stage_x, x, xb, cudaMemcpyHostToDevice, h->stream));
+        dx = h->d_stage_x;
+    }
+    if (!U_dev) {
+        if ((rc = ctx_grow(h, (void**)&h->d_stage_U, &h->stage_U_cap, Ub, "staging U"))) return rc;
+        dU = h->d_stage_U;
+    }
+    if (init_mode == FCM_INIT_U && !U0_dev) {
+        // a host U^0 is staged into the U buffer and updated in place there
+        CK(cudaMemcpyAsync(dU, U0, Ub, cudaMemcpyHostToDevice, h->stream));
+        dU0 = dU;
+    }
+
+    const bool trace = (options & FCM_OPT_TRACE) != 0;
+    if (trace) {
+        if ((rc = ctx_grow(h, (void**)&h->d_trace, &h->trace_cap,
+                           sizeof(double) * (size_t)max_iter * (2 + C), "trace buffer")))
+            return rc;
+    }
+
+    RunState* hs = h->h_st;
+    std::memset(hs, 0, sizeof(RunState));
+    hs->x = dx;
+    hs->Uprev = init_mode == FCM_INIT_U ? dU0 : dU;
+    hs->U = dU;
+    hs->trace = trace ? h->d_trace : nullptr;
+    hs->n = n;
+    hs->m = m;
+    hs->inv_m1 = (float)(1.0 / ((double)m - 1.0));
+    hs->eps = eps;
+    hs->max_iter = max_iter;
+    hs->C = C;
+    hs->status = STATUS_RUNNING;
+    if (init_mode == FCM_INIT_V && !V_dev) std::memcpy(hs->V0, V, sizeof(float) * C);
+    CK(cudaMemcpyAsync(h->d_st, hs, sizeof(RunState), cudaMemcpyHostToDevice, h->stream));
+    if (init_mode == FCM_INIT_V && V_dev)
+        CK(cudaMemcpyAsync(&h->d_st->V0, V, sizeof(float) * C, cudaMemcpyDeviceToDevice, h->stream));
+
+    const int mk = mkind_of(m);
+    const bool vec = (n % 4 == 0) && ((uintptr_t)dx % 16 == 0) && ((uintptr_t)dU % 16 == 0) &&
+                     ((uintptr_t)hs->Uprev % 16 == 0);
+    const int pass0 = init_mode == FCM_INIT_U ? P_ACCUM0 : P_INITV;
+    PassFn kfirst = g_table.k[C][mk][pass0][vec ? 1 : 0];
+    PassFn kiter = g_table.k[C][mk][P_ITER][vec ? 1 : 0];
+    const int64_t work = vec ? n / 4 : n;
+    const int bps = blocks_per_sm(h, kiter);
+    const int64_t want = (work + NT - 1) / NT;
+    const int nblocks = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)h->num_sms * bps));
+
+    if (options & FCM_OPT_NO_GRAPH) {
+        if ((rc = run_host_loop(h, kfirst, kiter, nblocks))) return rc;
+    } else {
+        const GraphKey key{C, mk, pass0, vec ? 1 : 0, nblocks};
+        auto it = h->graphs.find(key);
+        if (it == h->graphs.end()) {
+            GraphEntry ge;
+            if ((rc = build_graph(h, kfirst, kiter, nblocks, &ge))) return rc;
+            it = h->graphs.emplace(key, ge).first;
+        }
+        CK(cudaGraphLaunch(it->second.exec, h->stream));
+    }
+
+    CK(cudaMemcpyAsync(hs, h->d_st, sizeof(RunState), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaMemcpyAsync(V, &h->d_st->V, sizeof(float) * C,
+                       V_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->stream));
+    if (!U_dev) CK(cudaMemcpyAsync(U, h->d_stage_U, Ub, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+
+    h->last_trace_iters = trace ? hs->iters : 0;
+    h->last_C = C;
+    if (rep) {
+        std::memset(rep, 0, sizeof(*rep));
+        rep->iters = hs->iters;
+        rep->status = hs->status;
+        rep->flags = hs->flags;
+        rep->C = C;
+        rep->delta = hs->delta;
+        rep->J = hs->J;
+        for (int j = 0; j < C; ++j) rep->V64[j] = hs->V64[j];
+    }
+    if (hs->status == STATUS_RUNNING) {
+        h->last_error = "run ended without a status";
+        return FCM_ERR_CUDA;
+    }
+    return hs->status;
+}
+
+int fcm_get_trace(fcm_handle h, double* delta, double* J, double* V, int cap) {
+    if (!h || cap < 0) return FCM_ERR_INVALID_ARG;
+    const int k = std::min(cap, h->last_trace_iters);
+    if (k == 0) return 0;
+    const int C = h->last_C, row = 2 + C;
+    DeviceGuard g(h->device);
+    double* tmp = new double[(size_t)k * row];
+    cudaError_t e = cudaMemcpy(tmp, h->d_trace, sizeof(double) * (size_t)k * row, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) {
+        delete[] tmp;
+        return ctx_fail(h, e, "reading the trace");
+    }
+    for (int t = 0; t < k; ++t) {
+        if (delta) delta[t] = tmp[(size_t)t * row];
+        if (J) J[t] = tmp[(size_t)t * row + 1];
+        if (V)
+            for (int j = 0; j < C; ++j) V[(size_t)t * C + j] = tmp[(size_t)t * row + 2 + j];
+    }
+    delete[] tmp;
+    return k;
+}
+
+}  // extern "C"

@@ -1,0 +1,72 @@
+// Host/device shared definitions of the single-image FCM path.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "fcm.h"
+
+namespace fcm {
+
+constexpr int NT = 256;                                  // threads per block of the pass
+constexpr int NWARP = NT / 32;
+constexpr int SLOTS_MAX = 2 * FCM_MAX_CLUSTERS + 2;      // num[C], den[C], J, delta
+constexpr int STATUS_RUNNING = 2;
+
+// Which half-step a launch of the pass performs.
+enum Pass : int {
+    P_ACCUM0 = 0,  // V^1 from a given U^0 (Eq. 3); validates x and U^0
+    P_INITV = 1,   // U^0 = membership(V^0) (Eq. 4), written to U; V^1 from it
+    P_ITER = 2,    // U^k from V^k in place, delta_k, J_k, V^{k+1} (Eqs. 4, 1, 3)
+    P_COUNT = 3
+};
+
+// Device-resident state of one run. The host writes the whole struct before a
+// run; the passes read their inputs from it and the last block of each pass
+// writes the evolving part. Kernels and graphs therefore never need new
+// parameters when the caller's buffers change.
+struct alignas(128) RunState {
+    // per-run inputs
+    const float* x;
+    const float* Uprev;  // U^{k-1}: the caller's U^0 for the first pass, then U
+    float* U;            // U^k, written in place
+    double* trace;   // nullable: (max_iter) rows of (delta, J, V^k[C])
+    int64_t n;
+    float m;
+    float inv_m1;    // 1 / (m - 1)
+    float eps;
+    int max_iter;
+    int C;
+    int pad0;
+    float V0[FCM_MAX_CLUSTERS];
+    // evolving
+    float V[FCM_MAX_CLUSTERS];      // V^k used by the next pass
+    double V64[FCM_MAX_CLUSTERS];   // the FP64 quotients V rounds
+    double delta;
+    double J;
+    int k;          // index of the next iteration
+    int status;
+    int done;
+    int flags;
+    int iters;
+    unsigned int ticket;  // last-block-done counter of the current pass
+    int launches;         // passes started in this run (loop guard)
+};
+
+typedef void (*PassFn)(RunState*, double*, cudaGraphConditionalHandle, int);
+
+// Kernel table: [C][m kind][pass][vectorised].
+struct SingleTable {
+    PassFn k[FCM_MAX_CLUSTERS + 1][4][P_COUNT][2];
+};
+
+void register_single_c1(SingleTable&);
+void register_single_c2(SingleTable&);
+void register_single_c3(SingleTable&);
+void register_single_c4(SingleTable&);
+void register_single_c5(SingleTable&);
+void register_single_c6(SingleTable&);
+void register_single_c7(SingleTable&);
+void register_single_c8(SingleTable&);
+
+}  // namespace fcm

@@ -1,0 +1,69 @@
+// The handle behind fcm_handle, shared by the host modules of the library.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <map>
+#include <string>
+#include <tuple>
+
+#include "fcm.h"
+#include "fcm_internal.h"
+
+namespace fcm {
+
+struct GraphKey {
+    int C, mk, pass0, vec, nblocks;
+    bool operator<(const GraphKey& o) const {
+        return std::tie(C, mk, pass0, vec, nblocks) < std::tie(o.C, o.mk, o.pass0, o.vec, o.nblocks);
+    }
+};
+
+struct GraphEntry {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
+struct BatchedWorkspace;  // fcm_batched.cu
+struct MlpWorkspace;      // fcm_mlp.cu
+
+}  // namespace fcm
+
+struct fcm_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int num_sms = 0;
+    int max_smem_optin = 0;
+    std::string device_name;
+    std::string last_error;
+
+    // single-image path
+    fcm::RunState* d_st = nullptr;
+    fcm::RunState* h_st = nullptr;   // pinned
+    int h_done = 0;
+    double* d_partials = nullptr;
+    int partial_blocks = 0;
+    double* d_trace = nullptr;
+    size_t trace_cap = 0;
+    int last_trace_iters = 0;
+    int last_C = 0;
+    float* d_stage_x = nullptr;
+    size_t stage_x_cap = 0;
+    float* d_stage_U = nullptr;
+    size_t stage_U_cap = 0;
+    std::map<fcm::GraphKey, fcm::GraphEntry> graphs;
+    std::map<const void*, int> occupancy;
+
+    // other paths
+    fcm::BatchedWorkspace* batched = nullptr;
+    fcm::MlpWorkspace* mlp = nullptr;
+};
+
+namespace fcm {
+int ctx_fail(fcm_ctx* h, cudaError_t e, const char* what);
+int ctx_invalid(fcm_ctx* h, const char* what);
+int ctx_grow(fcm_ctx* h, void** p, size_t* cap, size_t bytes, const char* what);
+}  // namespace fcm
+
+void fcm_release_batched(fcm_ctx* h);
+void fcm_release_mlp(fcm_ctx* h);

@@ -1,0 +1,147 @@
+"""Python binding of the single-image FCM entry points (argument marshalling only).
+
+Every step of the computation runs in the CUDA library; this module only
+turns torch tensors or numpy arrays into pointers, picks the current torch
+stream, and turns status codes into exceptions.
+"""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import _lib
+
+
+def _ptr(a) -> int:
+    """Device or host pointer of a contiguous float32 torch tensor / numpy array."""
+    if isinstance(a, np.ndarray):
+        if a.dtype != np.float32 or not a.flags["C_CONTIGUOUS"]:
+            raise TypeError("numpy arrays must be C-contiguous float32")
+        return a.ctypes.data
+    import torch
+    if not isinstance(a, torch.Tensor):
+        raise TypeError(f"expected a torch tensor or numpy array, got {type(a)}")
+    if a.dtype != torch.float32 or not a.is_contiguous():
+        raise TypeError("tensors must be contiguous float32")
+    return a.data_ptr()
+
+
+def _numel(a) -> int:
+    return int(a.size) if isinstance(a, np.ndarray) else int(a.numel())
+
+
+@dataclass
+class FCMResult:
+    U: object
+    V: object
+    iters: int
+    status: int
+    delta: float
+    J: float
+    V64: np.ndarray
+    flags: int
+    trace: dict | None = field(default=None)
+
+    @property
+    def converged(self) -> bool:
+        return self.status == _lib.FCM_OK
+
+
+class FCM:
+    """A handle of the CUDA FCM library bound to one device.
+
+    Work is issued on torch's current CUDA stream of that device at each call.
+    """
+
+    def __init__(self, device: int | None = None):
+        import torch
+        self._lib = _lib.load()
+        self.device = torch.cuda.current_device() if device is None else int(device)
+        self._h = ctypes.c_void_p()
+        _lib.check(self._lib.fcm_create(ctypes.byref(self._h), self.device, None))
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            self._lib.fcm_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    @property
+    def handle(self):
+        return self._h
+
+    def _bind_stream(self):
+        import torch
+        s = torch.cuda.current_stream(self.device).cuda_stream
+        _lib.check(self._lib.fcm_set_stream(self._h, ctypes.c_void_p(s)), self._h)
+
+    def run(self, x, C: int, m: float = 2.0, eps: float = 1e-5, max_iter: int = 300, *,
+            U0=None, V0=None, U=None, V=None, trace: bool = False, graph: bool = True,
+            raise_on_error: bool = True) -> FCMResult:
+        """Algorithm 1 on one image.
+
+        ``x``: n float32 pixels (CUDA tensor, pinned/CPU tensor or numpy).
+        Start from memberships: ``U0`` [C, n] (read only), or no ``U0`` and
+        ``U`` holding U^0 (updated in place). Start from centers: ``V0`` [C].
+        ``U`` (allocated when None) receives U^k and ``V`` (allocated when
+        None, or V0 itself) receives V^k.
+        """
+        import torch
+        n = _numel(x)
+        on_device = isinstance(x, torch.Tensor) and x.is_cuda
+
+        def alloc(shape):
+            return (torch.empty(shape, dtype=torch.float32, device=x.device) if on_device
+                    else np.empty(shape, dtype=np.float32))
+
+        if V0 is not None:
+            mode = _lib.FCM_INIT_V
+            if V is None:
+                V = V0
+            elif V is not V0:
+                V[...] = V0
+            u0p = None
+        else:
+            mode = _lib.FCM_INIT_U
+            if U0 is None and U is None:
+                raise ValueError("give U0, V0, or U holding U^0")
+            u0p = U0
+        if U is None:
+            U = alloc((C, n))
+        if V is None:
+            V = alloc((C,))
+        if _numel(U) != C * n or _numel(V) != C or (u0p is not None and _numel(u0p) != C * n):
+            raise ValueError("U and U0 must hold C*n floats and V C floats")
+        opts = (_lib.FCM_OPT_TRACE if trace else 0) | (0 if graph else _lib.FCM_OPT_NO_GRAPH)
+        rep = _lib.fcm_report()
+        self._bind_stream()
+        st = self._lib.fcm_run(self._h, _ptr(x), n, int(C), float(m), float(eps), int(max_iter),
+                               mode, None if u0p is None else _ptr(u0p), _ptr(U), _ptr(V), opts,
+                               ctypes.byref(rep))
+        if raise_on_error:
+            _lib.check(st, self._h)
+        tr = None
+        if trace and st >= 0:
+            k = rep.iters
+            d = np.zeros(k)
+            J = np.zeros(k)
+            Vt = np.zeros((k, C))
+            got = self._lib.fcm_get_trace(self._h, d.ctypes.data_as(_lib._dp),
+                                          J.ctypes.data_as(_lib._dp), Vt.ctypes.data_as(_lib._dp), k)
+            _lib.check(got, self._h)
+            tr = {"delta": d[:got], "J": J[:got], "V": Vt[:got]}
+        return FCMResult(U=U, V=V, iters=rep.iters, status=st, delta=rep.delta, J=rep.J,
+                         V64=np.array(rep.V64[:C]), flags=rep.flags, trace=tr)

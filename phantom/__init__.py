@@ -132,9 +132,9 @@ def phantom3d(seed: int, D: int, H: int, W: int, sigma: float = 6.0,
         cz += g.uniform(-0.1, 0.1) * az
         cy += g.uniform(-0.1, 0.1) * ay
         cx += g.uniform(-0.1, 0.1) * ax
-        az *= g.uniform(0.55, 0.8)
-        ay *= g.uniform(0.55, 0.8)
-        ax *= g.uniform(0.55, 0.8)
+        az *= g.uniform(0.7, 0.88)
+        ay *= g.uniform(0.7, 0.88)
+        ax *= g.uniform(0.7, 0.88)
         th += g.uniform(-0.3, 0.3)
     # bias polynomial: 1, z, y, x, z^2, y^2, x^2, zy, zx, yx
     coef = g.normal(0.0, 1.0, size=10)

@@ -1,0 +1,241 @@
+"""Parity of the single-image CUDA path with the FP64 oracle (needs a GPU).
+
+Every test calls the CUDA library through its C ABI (via the ctypes binding)
+and compares with the oracle on the same seeded inputs.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import phantom
+from parity import U_TOL, assert_within, center_err, eps32, precision_report
+
+pytestmark = pytest.mark.gpu
+
+EPS = 1e-5
+MAX_ITER = 300
+
+
+@pytest.fixture(scope="module")
+def fcm():
+    from paper_1601_00072_gb300 import _build
+    _build.build()
+    from paper_1601_00072_gb300.fcm import FCM
+    h = FCM(0)
+    yield h
+    h.close()
+
+
+def _cuda(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+
+
+def gpu_run(fcm, x, C, m, eps=EPS, max_iter=MAX_ITER, u0=None, V0=None, **kw):
+    xt = _cuda(x)
+    if u0 is not None:
+        r = fcm.run(xt, C, m, eps, max_iter, U=_cuda(u0), **kw)
+    else:
+        r = fcm.run(xt, C, m, eps, max_iter, V0=_cuda(V0), **kw)
+    return r, r.U.cpu().numpy(), r.V.cpu().numpy()
+
+
+def oracle_run(x, C, m, eps, max_iter, u0=None, V0=None, quantized=False, want_U=True):
+    if quantized:
+        return oracle.fcm_quantized(np.asarray(x, np.uint8), C, m, eps32(eps), max_iter,
+                                    U0=u0, V0=V0, want_U=want_U)
+    return oracle.fcm(np.asarray(x, np.float64), C, m, eps32(eps), max_iter, U0=u0, V0=V0,
+                      want_U=want_U)
+
+
+def paired(fcm, x, C, m, u0=None, V0=None, quantized=False, eps=EPS, max_iter=MAX_ITER):
+    """Run both sides; if the iteration counts differ, rerun the longer one
+    with max_iter equal to the shorter count, so both return the same iterate."""
+    g, gU, gV = gpu_run(fcm, x, C, m, eps, max_iter, u0=u0, V0=V0)
+    o = oracle_run(x, C, m, eps, max_iter, u0=u0, V0=V0, quantized=quantized)
+    d_iters = g.iters - o["iters"]
+    k = min(g.iters, o["iters"])
+    if g.iters > k:
+        g, gU, gV = gpu_run(fcm, x, C, m, eps, k, u0=u0, V0=V0)
+    if o["iters"] > k:
+        o = oracle_run(x, C, m, eps, k, u0=u0, V0=V0, quantized=quantized)
+    rep = precision_report(gU, gV, g.iters + d_iters, o["U"], o["V"], o["iters"], g.J, o["J"][-1])
+    return rep, g, gU, gV, o
+
+
+@pytest.mark.parametrize("m", [2.0, 1.5, 3.0, 2.5])
+def test_phantom200_matches_oracle(fcm, m):
+    x, _, u0, C = phantom.single_image("phantom200")
+    rep, g, gU, *_ = paired(fcm, x, C, m, u0=u0)
+    assert_within(rep)
+    assert rep["J_rel_err"] < 1e-5
+    assert np.max(np.abs(gU.sum(0) - 1.0)) < 1e-6
+    assert gU.min() >= 0.0 and gU.max() <= 1.0 + 1e-6
+
+
+def test_phantom1024_matches_oracle(fcm):
+    x, _, u0, C = phantom.single_image("phantom1024")
+    rep, *_ = paired(fcm, x, C, 2.0, u0=u0, quantized=True)
+    assert_within(rep)
+
+
+@pytest.mark.parametrize("m", [2.0, 1.5, 3.0])
+def test_volume256_matches_oracle(fcm, m):
+    """Full 16.7M-voxel run; U compared on a 200k-voxel sample."""
+    x, _, u0, C = phantom.single_image("volume256")
+    g, gU, gV = gpu_run(fcm, x, C, m, u0=u0)
+    o = oracle_run(x, C, m, EPS, MAX_ITER, u0=u0, quantized=True, want_U=False)
+    assert abs(g.iters - o["iters"]) <= 1
+    k = min(g.iters, o["iters"])
+    if g.iters > k:
+        g, gU, gV = gpu_run(fcm, x, C, m, max_iter=k, u0=u0)
+    if o["iters"] > k:
+        o = oracle_run(x, C, m, EPS, k, u0=u0, quantized=True, want_U=False)
+    idx = np.random.default_rng(0).choice(x.size, 200_000, replace=False)
+    Ubins = oracle.memberships(np.arange(256.0), o["V"], m)
+    rep = precision_report(gU[:, idx], gV, g.iters, Ubins[:, x[idx]], o["V"], o["iters"],
+                           g.J, o["J"][-1])
+    assert_within(rep)
+
+
+@pytest.mark.parametrize("n,C,m", [(1, 1, 2.0), (3, 2, 2.0), (1001, 3, 1.5), (4099, 5, 3.0),
+                                   (65538, 8, 2.0), (123457, 4, 2.7), (40000, 1, 2.0)])
+def test_ragged_sizes_match_oracle(fcm, n, C, m):
+    side = int(np.ceil(np.sqrt(n)))
+    img, _ = phantom.phantom2d(1000 + n, side, side, 9.0)
+    x = img.reshape(-1)[:n]
+    u0 = phantom.dirichlet_u0((1000 + n, 7), C, n)
+    rep, g, *_ = paired(fcm, x, C, m, u0=u0)
+    assert_within(rep)
+
+
+def test_init_from_centers_matches_oracle(fcm):
+    x, _, _, C = phantom.single_image("phantom200")
+    V0 = np.array([5.0, 45.0, 100.0, 160.0])
+    rep, *_ = paired(fcm, x, C, 2.0, V0=V0)
+    assert_within(rep)
+
+
+def test_max_iter_reached(fcm):
+    x, _, u0, C = phantom.single_image("phantom200")
+    g, gU, gV = gpu_run(fcm, x, C, 2.0, max_iter=7, u0=u0)
+    o = oracle_run(x, C, 2.0, EPS, 7, u0=u0)
+    assert g.status == 1 and g.iters == 7 and o["status"] == oracle.NOT_CONVERGED
+    rep = precision_report(gU, gV, g.iters, o["U"], o["V"], o["iters"])
+    assert_within(rep)
+
+
+def test_trace_matches_oracle(fcm):
+    x, _, u0, C = phantom.single_image("phantom200")
+    g, _, _ = gpu_run(fcm, x, C, 2.0, u0=u0, trace=True)
+    o = oracle_run(x, C, 2.0, EPS, MAX_ITER, u0=u0, want_U=False)
+    k = min(g.iters, o["iters"])
+    tr = g.trace
+    assert np.max(np.abs(tr["delta"][:k] - o["delta"][:k])) < 1e-5
+    assert np.max(np.abs(tr["J"][:k] - o["J"][:k]) / o["J"][:k]) < 1e-5
+    for t in range(k):
+        assert center_err(tr["V"][t], o["Vtrace"][t]) < 1e-5
+    # J is non-increasing along the CUDA iteration too (FP32 noise allowed)
+    assert np.all(np.diff(tr["J"]) <= 1e-6 * tr["J"][0])
+
+
+def test_graph_and_host_loop_agree_bitwise(fcm):
+    x, _, u0, C = phantom.single_image("phantom200")
+    a, aU, aV = gpu_run(fcm, x, C, 2.0, u0=u0)
+    b, bU, bV = gpu_run(fcm, x, C, 2.0, u0=u0, graph=False)
+    assert a.iters == b.iters and np.array_equal(aU, bU) and np.array_equal(aV, bV)
+    assert np.array_equal(a.V64, b.V64)
+
+
+def test_repeatable(fcm):
+    x, _, u0, C = phantom.single_image("phantom200")
+    a, aU, aV = gpu_run(fcm, x, C, 3.0, u0=u0)
+    b, bU, bV = gpu_run(fcm, x, C, 3.0, u0=u0)
+    assert a.iters == b.iters and np.array_equal(aU, bU) and np.array_equal(aV, bV)
+
+
+def test_host_buffers_match_device_buffers(fcm):
+    import torch
+    x, _, u0, C = phantom.single_image("phantom200")
+    a, aU, aV = gpu_run(fcm, x, C, 2.0, u0=u0)
+    xh = torch.from_numpy(x.astype(np.float32)).pin_memory()
+    Uh = torch.from_numpy(u0.copy()).pin_memory()
+    b = fcm.run(xh, C, 2.0, EPS, MAX_ITER, U=Uh)
+    assert b.iters == a.iters and np.array_equal(Uh.numpy(), aU)
+    assert np.array_equal(b.V.numpy(), aV)
+    # pageable numpy arrays too, with a separate read-only U0
+    U0n = u0.copy()
+    c = fcm.run(x.astype(np.float32), C, 2.0, EPS, MAX_ITER, U0=U0n)
+    assert c.iters == a.iters and np.array_equal(c.U, aU) and np.array_equal(U0n, u0)
+
+
+def test_separate_u0_is_left_unchanged(fcm):
+    x, _, u0, C = phantom.single_image("phantom200")
+    a, aU, aV = gpu_run(fcm, x, C, 2.0, u0=u0)
+    U0 = _cuda(u0)
+    for _ in range(2):
+        b = fcm.run(_cuda(x), C, 2.0, EPS, MAX_ITER, U0=U0)
+        assert b.iters == a.iters and np.array_equal(b.U.cpu().numpy(), aU)
+    assert np.array_equal(U0.cpu().numpy(), u0)
+
+
+def test_zero_distance_fixed_point(fcm):
+    x = np.array([0.0, 10.0] * 64)
+    g, gU, gV = gpu_run(fcm, x, 2, 2.0, V0=[0.0, 10.0])
+    assert g.status == 0 and g.iters == 1 and g.delta == 0.0
+    assert np.array_equal(gV, [0.0, 10.0])
+    assert np.array_equal(gU, np.stack([x == 0.0, x == 10.0]).astype(np.float32))
+
+
+def test_constant_image(fcm):
+    """Degenerate image: every center lands exactly on the one grey level (a
+    power of two, so the weighted means are exact in any precision), every
+    pixel is at distance 0 from all C centers and gets 1/C each."""
+    x = np.full(1024, 64.0)
+    u0 = phantom.dirichlet_u0((77,), 3, x.size)
+    g, gU, gV = gpu_run(fcm, x, 3, 2.0, u0=u0)
+    o = oracle_run(x, 3, 2.0, EPS, MAX_ITER, u0=u0)
+    assert g.status == 0 and g.iters == o["iters"] == 2
+    assert np.array_equal(gV, [64.0, 64.0, 64.0]) and np.array_equal(o["V"], [64.0] * 3)
+    assert np.array_equal(gU, np.full((3, 1024), np.float32(1.0) / np.float32(3.0)))
+
+
+def test_bad_input_is_reported(fcm):
+    from paper_1601_00072_gb300 import FcmError
+    x, _, u0, C = phantom.single_image("phantom200")
+    xb = x.astype(np.float32).copy()
+    xb[1234] = np.nan
+    with pytest.raises(FcmError) as e:
+        gpu_run(fcm, xb, C, 2.0, u0=u0)
+    assert e.value.status == -4
+    ub = u0.copy()
+    ub[2, 77] = -0.25
+    with pytest.raises(FcmError) as e:
+        gpu_run(fcm, x, C, 2.0, u0=ub)
+    assert e.value.status == -4
+    with pytest.raises(FcmError) as e:
+        gpu_run(fcm, x, C, 2.0, V0=[1.0, np.inf, 3.0, 4.0])
+    assert e.value.status == -4
+    # the handle stays usable afterwards
+    g, *_ = gpu_run(fcm, x, C, 2.0, u0=u0)
+    assert g.status == 0
+
+
+def test_invalid_arguments(fcm):
+    import ctypes
+    from paper_1601_00072_gb300 import _lib
+    L = _lib.load()
+    x = _cuda(np.arange(16.0))
+    U = _cuda(np.full((2, 16), 0.5))
+    V = _cuda(np.zeros(2))
+    p = lambda t: ctypes.c_void_p(t.data_ptr())
+    h = fcm.handle
+    assert L.fcm_run(h, p(x), 16, 2, 1.0, 1e-5, 10, 0, None, p(U), p(V), 0, None) == -1   # m <= 1
+    assert L.fcm_run(h, p(x), 16, 0, 2.0, 1e-5, 10, 0, None, p(U), p(V), 0, None) == -1   # C < 1
+    assert L.fcm_run(h, p(x), 16, 9, 2.0, 1e-5, 10, 0, None, p(U), p(V), 0, None) == -1   # C > 8
+    assert L.fcm_run(h, p(x), 0, 2, 2.0, 1e-5, 10, 0, None, p(U), p(V), 0, None) == -1    # n < 1
+    assert L.fcm_run(h, p(x), 16, 2, 2.0, -1.0, 10, 0, None, p(U), p(V), 0, None) == -1   # eps < 0
+    assert L.fcm_run(h, p(x), 16, 2, 2.0, 1e-5, 0, 0, None, p(U), p(V), 0, None) == -1    # max_iter
+    assert L.fcm_run(h, None, 16, 2, 2.0, 1e-5, 10, 0, None, p(U), p(V), 0, None) == -1   # null x
+    assert L.fcm_run(h, p(x), 16, 2, 2.0, 1e-5, 10, 5, None, p(U), p(V), 0, None) == -1   # init mode
+    assert L.fcm_run(None, p(x), 16, 2, 2.0, 1e-5, 10, 0, None, p(U), p(V), 0, None) == -1
