@@ -249,7 +249,7 @@ def bench_ours(args):
     stream = torch.cuda.current_stream(dev)
 
     def step():
-        return h.run(xd, C, m, EPS, MAX_ITER, U0=U0d, U=Ud, V=Vd)
+        return h.run(xd, C, m, EPS, MAX_ITER, U0=U0d, U=Ud, V=Vd, graph=not args.no_graph)
 
     for _ in range(args.warmup):
         r = step()
@@ -320,8 +320,8 @@ def bench_ours(args):
         "vs_baseline": None,
         "dtype": "f32",
         "data": "synthetic",
-        "config": {"workload": "256^3 uint8 ellipsoid phantom (bias +/-20%, Rician sigma 6) as f32, "
-                               "C=4, m=%g, eps=1e-5, max_iter=300, Dirichlet U0 seed 103" % m,
+        "config": {"workload": "256^3 uint8 ellipsoid phantom (bias +/-20 percent, Rician sigma 6) "
+                               f"as f32, C=4, m={m:g}, eps=1e-5, max_iter=300, Dirichlet U0 seed 103",
                    "n_pixels": n, "iters_per_step": statistics.median(iters),
                    "parallelism": f"replicas x{world}",
                    "l2": "working set 603 MB > 129 MB L2; no flush"},
@@ -379,7 +379,7 @@ def bench_reference(args):
            "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "impl": "reference",
-           "config": {"workload": "256^3 uint8 ellipsoid phantom as f64 (sampled), C=4, m=%g" % args.m},
+           "config": {"workload": f"256^3 uint8 ellipsoid phantom as f64 (sampled), C=4, m={args.m:g}"},
            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
@@ -394,6 +394,9 @@ def main():
     ap.add_argument("--m", type=float, default=2.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-graph", action="store_true",
+                    help="launch the same pass kernels from a host loop instead of the CUDA graph "
+                         "WHILE node (for profilers that cannot see kernels inside conditional graphs)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours" and not os.environ.get("FCM_BENCH_ALLOW_SHORT"):
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)

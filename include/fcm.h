@@ -70,6 +70,7 @@ extern "C" {
 /* Run options (bit flags). */
 #define FCM_OPT_TRACE 1    /* record delta_k, J_k and V^k of every iteration */
 #define FCM_OPT_NO_GRAPH 2 /* host-driven loop instead of a CUDA graph WHILE node */
+#define FCM_OPT_NO_TMA 4   /* plain-load pass kernel instead of the TMA-fed one */
 
 typedef struct fcm_ctx* fcm_handle;
 

@@ -23,6 +23,7 @@ FCM_INIT_U = 0
 FCM_INIT_V = 1
 FCM_OPT_TRACE = 1
 FCM_OPT_NO_GRAPH = 2
+FCM_OPT_NO_TMA = 4
 
 
 class fcm_report(ctypes.Structure):

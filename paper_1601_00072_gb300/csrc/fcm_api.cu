@@ -120,19 +120,27 @@ int ensure_single_workspace(fcm_ctx* h) {
     return 0;
 }
 
-int blocks_per_sm(fcm_ctx* h, PassFn k) {
+// Blocks per SM of a pass kernel with `smem` bytes of dynamic shared memory;
+// the first call also raises the kernel's dynamic shared memory limit.
+int blocks_per_sm(fcm_ctx* h, PassFn k, int smem) {
     auto it = h->occupancy.find((const void*)k);
     if (it != h->occupancy.end()) return it->second;
-    int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, (const void*)k, NT, 0) != cudaSuccess || nb < 1) {
+    if (smem > 48 * 1024 &&
+        cudaFuncSetAttribute((const void*)k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess) {
         cudaGetLastError();
-        nb = 1;
+        return 0;
+    }
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, (const void*)k, NT, smem) != cudaSuccess) {
+        cudaGetLastError();
+        nb = 0;
     }
     h->occupancy[(const void*)k] = nb;
     return nb;
 }
 
-int build_graph(fcm_ctx* h, PassFn kfirst, PassFn kiter, int nblocks, GraphEntry* out) {
+int build_graph(fcm_ctx* h, PassFn kfirst, int smem_first, PassFn kiter, int smem_iter, int nblocks,
+                GraphEntry* out) {
     cudaGraph_t g = nullptr;
     CK(cudaGraphCreate(&g, 0));
     cudaGraphConditionalHandle cond;
@@ -148,6 +156,7 @@ int build_graph(fcm_ctx* h, PassFn kfirst, PassFn kiter, int nblocks, GraphEntry
     kp.func = (void*)kfirst;
     kp.gridDim = dim3(nblocks);
     kp.blockDim = dim3(NT);
+    kp.sharedMemBytes = smem_first;
     kp.kernelParams = args;
     cudaGraphNode_t n1, n2, n3;
     e = cudaGraphAddKernelNode(&n1, g, nullptr, 0, &kp);
@@ -164,6 +173,7 @@ int build_graph(fcm_ctx* h, PassFn kfirst, PassFn kiter, int nblocks, GraphEntry
     if (e == cudaSuccess) {
         cudaGraph_t body = cp.conditional.phGraph_out[0];
         kp.func = (void*)kiter;
+        kp.sharedMemBytes = smem_iter;
         e = cudaGraphAddKernelNode(&n3, body, nullptr, 0, &kp);
     }
     cudaGraphExec_t ex = nullptr;
@@ -177,9 +187,9 @@ int build_graph(fcm_ctx* h, PassFn kfirst, PassFn kiter, int nblocks, GraphEntry
     return 0;
 }
 
-int run_host_loop(fcm_ctx* h, PassFn kfirst, PassFn kiter, int nblocks) {
+int run_host_loop(fcm_ctx* h, PassFn kfirst, int smem_first, PassFn kiter, int smem_iter, int nblocks) {
     const cudaGraphConditionalHandle none = 0;
-    kfirst<<<nblocks, NT, 0, h->stream>>>(h->d_st, h->d_partials, none, 0);
+    kfirst<<<nblocks, NT, smem_first, h->stream>>>(h->d_st, h->d_partials, none, 0);
     CK(cudaGetLastError());
     int chunk = 4;
     int launched = 0;
@@ -188,7 +198,7 @@ int run_host_loop(fcm_ctx* h, PassFn kfirst, PassFn kiter, int nblocks) {
     while (true) {
         const int todo = std::min(chunk, max_iter - launched);
         for (int t = 0; t < todo; ++t)
-            kiter<<<nblocks, NT, 0, h->stream>>>(h->d_st, h->d_partials, none, 0);
+            kiter<<<nblocks, NT, smem_iter, h->stream>>>(h->d_st, h->d_partials, none, 0);
         CK(cudaGetLastError());
         launched += todo;
         CK(cudaMemcpyAsync(done_host, &h->d_st->done, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
@@ -340,25 +350,40 @@ int fcm_run(fcm_handle h, const float* x, int64_t n, int C, float m, float eps, 
     if (init_mode == FCM_INIT_V && V_dev)
         CK(cudaMemcpyAsync(&h->d_st->V0, V, sizeof(float) * C, cudaMemcpyDeviceToDevice, h->stream));
 
+    // Kernel variant: the TMA ring needs n % 4 == 0 and 16-byte aligned rows
+    // (every bulk copy starts and ends on a 16-byte boundary).
     const int mk = mkind_of(m);
-    const bool vec = (n % 4 == 0) && ((uintptr_t)dx % 16 == 0) && ((uintptr_t)dU % 16 == 0) &&
-                     ((uintptr_t)hs->Uprev % 16 == 0);
+    const bool aligned = (n % 4 == 0) && ((uintptr_t)dx % 16 == 0) && ((uintptr_t)dU % 16 == 0) &&
+                         ((uintptr_t)hs->Uprev % 16 == 0);
+    int var = aligned && !(options & FCM_OPT_NO_TMA) ? 1 : 0;
     const int pass0 = init_mode == FCM_INIT_U ? P_ACCUM0 : P_INITV;
-    PassFn kfirst = g_table.k[C][mk][pass0][vec ? 1 : 0];
-    PassFn kiter = g_table.k[C][mk][P_ITER][vec ? 1 : 0];
-    const int64_t work = vec ? n / 4 : n;
-    const int bps = blocks_per_sm(h, kiter);
-    const int64_t want = (work + NT - 1) / NT;
-    const int nblocks = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)h->num_sms * bps));
+    int bps = 0, bps0 = 0;
+    for (; var >= 0; --var) {
+        bps = blocks_per_sm(h, g_table.k[C][mk][P_ITER][var], g_table.smem[C][mk][P_ITER][var]);
+        bps0 = blocks_per_sm(h, g_table.k[C][mk][pass0][var], g_table.smem[C][mk][pass0][var]);
+        if (bps > 0 && bps0 > 0) break;
+    }
+    if (var < 0) {
+        h->last_error = "no pass kernel fits on this device";
+        return FCM_ERR_CUDA;
+    }
+    PassFn kfirst = g_table.k[C][mk][pass0][var];
+    PassFn kiter = g_table.k[C][mk][P_ITER][var];
+    const int smem_first = g_table.smem[C][mk][pass0][var];
+    const int smem_iter = g_table.smem[C][mk][P_ITER][var];
+    const int64_t per_block = var == 1 ? 1024 : NT;  // pixels one block covers per step
+    const int64_t want = (n + per_block - 1) / per_block;
+    const int nblocks = (int)std::max<int64_t>(
+        1, std::min<int64_t>(want, (int64_t)h->num_sms * std::min(bps, bps0)));
 
     if (options & FCM_OPT_NO_GRAPH) {
-        if ((rc = run_host_loop(h, kfirst, kiter, nblocks))) return rc;
+        if ((rc = run_host_loop(h, kfirst, smem_first, kiter, smem_iter, nblocks))) return rc;
     } else {
-        const GraphKey key{C, mk, pass0, vec ? 1 : 0, nblocks};
+        const GraphKey key{C, mk, pass0, var, nblocks};
         auto it = h->graphs.find(key);
         if (it == h->graphs.end()) {
             GraphEntry ge;
-            if ((rc = build_graph(h, kfirst, kiter, nblocks, &ge))) return rc;
+            if ((rc = build_graph(h, kfirst, smem_first, kiter, smem_iter, nblocks, &ge))) return rc;
             it = h->graphs.emplace(key, ge).first;
         }
         CK(cudaGraphLaunch(it->second.exec, h->stream));

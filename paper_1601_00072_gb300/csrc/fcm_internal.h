@@ -10,7 +10,7 @@ namespace fcm {
 
 constexpr int NT = 256;                                  // threads per block of the pass
 constexpr int NWARP = NT / 32;
-constexpr int SLOTS_MAX = 2 * FCM_MAX_CLUSTERS + 2;      // num[C], den[C], J, delta
+constexpr int SLOTS_MAX = 2 * FCM_MAX_CLUSTERS + 4;      // num[C], den[C], J, delta, 2 flags
 constexpr int STATUS_RUNNING = 2;
 
 // Which half-step a launch of the pass performs.
@@ -55,9 +55,12 @@ struct alignas(128) RunState {
 
 typedef void (*PassFn)(RunState*, double*, cudaGraphConditionalHandle, int);
 
-// Kernel table: [C][m kind][pass][vectorised].
+// Kernel table: [C][m kind][pass][variant], variant 0 = grid-stride scalar
+// loads (any n), 1 = TMA ring (n % 4 == 0, 16-byte aligned rows); smem holds
+// each kernel's dynamic shared memory in bytes.
 struct SingleTable {
     PassFn k[FCM_MAX_CLUSTERS + 1][4][P_COUNT][2];
+    int smem[FCM_MAX_CLUSTERS + 1][4][P_COUNT][2];
 };
 
 void register_single_c1(SingleTable&);

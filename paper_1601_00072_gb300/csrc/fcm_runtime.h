@@ -52,7 +52,7 @@ struct fcm_ctx {
     float* d_stage_U = nullptr;
     size_t stage_U_cap = 0;
     std::map<fcm::GraphKey, fcm::GraphEntry> graphs;
-    std::map<const void*, int> occupancy;
+    std::map<const void*, int> occupancy;   // blocks per SM of each kernel (smem attribute set)
 
     // other paths
     fcm::BatchedWorkspace* batched = nullptr;

@@ -90,7 +90,7 @@ class FCM:
 
     def run(self, x, C: int, m: float = 2.0, eps: float = 1e-5, max_iter: int = 300, *,
             U0=None, V0=None, U=None, V=None, trace: bool = False, graph: bool = True,
-            raise_on_error: bool = True) -> FCMResult:
+            tma: bool = True, raise_on_error: bool = True) -> FCMResult:
         """Algorithm 1 on one image.
 
         ``x``: n float32 pixels (CUDA tensor, pinned/CPU tensor or numpy).
@@ -101,11 +101,13 @@ class FCM:
         """
         import torch
         n = _numel(x)
-        on_device = isinstance(x, torch.Tensor) and x.is_cuda
 
         def alloc(shape):
-            return (torch.empty(shape, dtype=torch.float32, device=x.device) if on_device
-                    else np.empty(shape, dtype=np.float32))
+            # outputs follow the kind of x: CUDA tensor, (pinned) CPU tensor or numpy
+            if isinstance(x, torch.Tensor):
+                t = torch.empty(shape, dtype=torch.float32, device=x.device)
+                return t.pin_memory() if (not x.is_cuda and x.is_pinned()) else t
+            return np.empty(shape, dtype=np.float32)
 
         if V0 is not None:
             mode = _lib.FCM_INIT_V
@@ -125,7 +127,8 @@ class FCM:
             V = alloc((C,))
         if _numel(U) != C * n or _numel(V) != C or (u0p is not None and _numel(u0p) != C * n):
             raise ValueError("U and U0 must hold C*n floats and V C floats")
-        opts = (_lib.FCM_OPT_TRACE if trace else 0) | (0 if graph else _lib.FCM_OPT_NO_GRAPH)
+        opts = ((_lib.FCM_OPT_TRACE if trace else 0) | (0 if graph else _lib.FCM_OPT_NO_GRAPH)
+                | (0 if tma else _lib.FCM_OPT_NO_TMA))
         rep = _lib.fcm_report()
         self._bind_stream()
         st = self._lib.fcm_run(self._h, _ptr(x), n, int(C), float(m), float(eps), int(max_iter),
