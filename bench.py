@@ -249,7 +249,8 @@ def bench_ours(args):
     stream = torch.cuda.current_stream(dev)
 
     def step():
-        return h.run(xd, C, m, EPS, MAX_ITER, U0=U0d, U=Ud, V=Vd, graph=not args.no_graph)
+        return h.run(xd, C, m, EPS, MAX_ITER, U0=U0d, U=Ud, V=Vd, graph=not args.no_graph,
+                     tma=args.variant == "tma")
 
     for _ in range(args.warmup):
         r = step()
@@ -394,6 +395,8 @@ def main():
     ap.add_argument("--m", type=float, default=2.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--variant", choices=["tma", "ldg"], default="tma",
+                    help="pass kernel: TMA-fed ring (default) or plain loads")
     ap.add_argument("--no-graph", action="store_true",
                     help="launch the same pass kernels from a host loop instead of the CUDA graph "
                          "WHILE node (for profilers that cannot see kernels inside conditional graphs)")

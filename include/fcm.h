@@ -71,6 +71,8 @@ extern "C" {
 #define FCM_OPT_TRACE 1    /* record delta_k, J_k and V^k of every iteration */
 #define FCM_OPT_NO_GRAPH 2 /* host-driven loop instead of a CUDA graph WHILE node */
 #define FCM_OPT_NO_TMA 4   /* plain-load pass kernel instead of the TMA-fed one */
+#define FCM_OPT_NO_PERSISTENT 8 /* one launch per pass (graph or host loop) instead of
+                                    one cooperative launch for the whole run */
 
 typedef struct fcm_ctx* fcm_handle;
 
@@ -117,7 +119,12 @@ void fcm_destroy(fcm_handle h);
  *             updates it in place from the first iteration on).
  *   V         C floats, device or host. In: V^0 when init_mode == FCM_INIT_V.
  *             Out: V^k.
- *   options   FCM_OPT_* bits.
+ *   options   FCM_OPT_* bits. By default, when n % 4 == 0 and the buffers are
+ *             16-byte aligned, the whole run is one cooperative kernel launch
+ *             (grid-wide exchange of the per-block sums after each pass);
+ *             otherwise, or with FCM_OPT_NO_PERSISTENT, one launch per pass
+ *             inside a CUDA graph WHILE loop (or a host loop with
+ *             FCM_OPT_NO_GRAPH).
  *   rep       nullable; filled on return.
  *
  * Returns FCM_OK, FCM_NOT_CONVERGED, or an error. On FCM_ERR_BAD_INPUT the
@@ -126,6 +133,18 @@ void fcm_destroy(fcm_handle h);
 int fcm_run(fcm_handle h, const float* x, int64_t n, int C, float m,
             float eps, int max_iter, int init_mode, const float* U0, float* U,
             float* V, int options, fcm_report* rep);
+
+/*
+ * fcm_time_pass — profiling aid: time `launches` back-to-back launches of the
+ * iteration pass (one Algorithm 1 iteration each: Eq. 4, Eq. 1, Eq. 3) on the
+ * handle's stream with CUDA events, starting from centers V (device or host,
+ * C floats) and updating U (device, C*n floats, cluster-major) in place; the
+ * stopping test is disabled. x is n device floats. Writes the average
+ * milliseconds per launch and returns FCM_OK or an error. The same launch
+ * configuration as fcm_run is used (options: FCM_OPT_NO_TMA).
+ */
+int fcm_time_pass(fcm_handle h, const float* x, int64_t n, int C, float m, float* U,
+                  const float* V, int launches, int options, float* ms_per_launch);
 
 /* Copy the trace of the last run made with FCM_OPT_TRACE into host arrays
  * (each nullable): delta[k-1], J[k-1] and V[(k-1)*C + j] for k = 1..iters.

@@ -24,6 +24,7 @@ FCM_INIT_V = 1
 FCM_OPT_TRACE = 1
 FCM_OPT_NO_GRAPH = 2
 FCM_OPT_NO_TMA = 4
+FCM_OPT_NO_PERSISTENT = 8
 
 
 class fcm_report(ctypes.Structure):
@@ -45,6 +46,7 @@ SIGNATURES = [
     ("fcm_destroy", None, [_vp]),
     ("fcm_run", _i, [_vp, _vp, _i64, _i, _f, _f, _i, _i, _vp, _vp, _vp, _i,
                      ctypes.POINTER(fcm_report)]),
+    ("fcm_time_pass", _i, [_vp, _vp, _i64, _i, _f, _vp, _vp, _i, _i, ctypes.POINTER(_f)]),
     ("fcm_get_trace", _i, [_vp, _dp, _dp, _dp, _i]),
     ("fcm_last_error", ctypes.c_char_p, [_vp]),
     ("fcm_status_string", ctypes.c_char_p, [_i]),

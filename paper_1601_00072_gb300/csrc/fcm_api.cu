@@ -122,21 +122,54 @@ int ensure_single_workspace(fcm_ctx* h) {
 
 // Blocks per SM of a pass kernel with `smem` bytes of dynamic shared memory;
 // the first call also raises the kernel's dynamic shared memory limit.
-int blocks_per_sm(fcm_ctx* h, PassFn k, int smem) {
-    auto it = h->occupancy.find((const void*)k);
+int blocks_per_sm(fcm_ctx* h, const void* k, int smem) {
+    auto it = h->occupancy.find(k);
     if (it != h->occupancy.end()) return it->second;
     if (smem > 48 * 1024 &&
-        cudaFuncSetAttribute((const void*)k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess) {
+        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess) {
         cudaGetLastError();
         return 0;
     }
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, (const void*)k, NT, smem) != cudaSuccess) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, NT, smem) != cudaSuccess) {
         cudaGetLastError();
         nb = 0;
     }
-    h->occupancy[(const void*)k] = nb;
+    h->occupancy[k] = nb;
     return nb;
+}
+
+struct Launch {
+    PassFn kfirst, kiter;
+    int smem_first, smem_iter, var, nblocks;
+};
+
+// Kernel variant and grid of a run. The TMA ring needs n % 4 == 0 and 16-byte
+// aligned rows (every bulk copy starts and ends on a 16-byte boundary).
+int choose_launch(fcm_ctx* h, int64_t n, int C, int mk, int pass0, const void* x, const void* U,
+                  const void* Uprev, int options, Launch* L) {
+    const bool aligned = (n % 4 == 0) && ((uintptr_t)x % 16 == 0) && ((uintptr_t)U % 16 == 0) &&
+                         ((uintptr_t)Uprev % 16 == 0);
+    int var = aligned && !(options & FCM_OPT_NO_TMA) ? 1 : 0;
+    int bps = 0, bps0 = 0;
+    for (; var >= 0; --var) {
+        bps = blocks_per_sm(h, (const void*)g_table.k[C][mk][P_ITER][var], g_table.smem[C][mk][P_ITER][var]);
+        bps0 = blocks_per_sm(h, (const void*)g_table.k[C][mk][pass0][var], g_table.smem[C][mk][pass0][var]);
+        if (bps > 0 && bps0 > 0) break;
+    }
+    if (var < 0) {
+        h->last_error = "no pass kernel fits on this device";
+        return FCM_ERR_CUDA;
+    }
+    L->var = var;
+    L->kfirst = g_table.k[C][mk][pass0][var];
+    L->kiter = g_table.k[C][mk][P_ITER][var];
+    L->smem_first = g_table.smem[C][mk][pass0][var];
+    L->smem_iter = g_table.smem[C][mk][P_ITER][var];
+    const int64_t per_block = var == 1 ? 4 * NT : NT;  // pixels one block covers per step
+    const int64_t want = (n + per_block - 1) / per_block;
+    L->nblocks = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)h->num_sms * std::min(bps, bps0)));
+    return 0;
 }
 
 int build_graph(fcm_ctx* h, PassFn kfirst, int smem_first, PassFn kiter, int smem_iter, int nblocks,
@@ -232,6 +265,9 @@ int fcm_create(fcm_handle* out, int device, void* cuda_stream) {
         return FCM_ERR_CUDA;
     }
     h->num_sms = prop.multiProcessorCount;
+    int coop = 0;
+    if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, device) != cudaSuccess) coop = 0;
+    h->coop = coop != 0;
     h->max_smem_optin = (int)prop.sharedMemPerBlockOptin;
     h->device_name = prop.name;
     *out = h;
@@ -350,31 +386,31 @@ int fcm_run(fcm_handle h, const float* x, int64_t n, int C, float m, float eps, 
     if (init_mode == FCM_INIT_V && V_dev)
         CK(cudaMemcpyAsync(&h->d_st->V0, V, sizeof(float) * C, cudaMemcpyDeviceToDevice, h->stream));
 
-    // Kernel variant: the TMA ring needs n % 4 == 0 and 16-byte aligned rows
-    // (every bulk copy starts and ends on a 16-byte boundary).
     const int mk = mkind_of(m);
+    const int pass0 = init_mode == FCM_INIT_U ? P_ACCUM0 : P_INITV;
     const bool aligned = (n % 4 == 0) && ((uintptr_t)dx % 16 == 0) && ((uintptr_t)dU % 16 == 0) &&
                          ((uintptr_t)hs->Uprev % 16 == 0);
-    int var = aligned && !(options & FCM_OPT_NO_TMA) ? 1 : 0;
-    const int pass0 = init_mode == FCM_INIT_U ? P_ACCUM0 : P_INITV;
-    int bps = 0, bps0 = 0;
-    for (; var >= 0; --var) {
-        bps = blocks_per_sm(h, g_table.k[C][mk][P_ITER][var], g_table.smem[C][mk][P_ITER][var]);
-        bps0 = blocks_per_sm(h, g_table.k[C][mk][pass0][var], g_table.smem[C][mk][pass0][var]);
-        if (bps > 0 && bps0 > 0) break;
+    int run_blocks = 0;
+    const void* krun = (const void*)g_table.run[C][mk][init_mode == FCM_INIT_U ? 0 : 1];
+    const int run_smem = g_table.run_smem[C];
+    if (aligned && h->coop && !(options & (FCM_OPT_NO_TMA | FCM_OPT_NO_PERSISTENT | FCM_OPT_NO_GRAPH))) {
+        const int bps = blocks_per_sm(h, krun, run_smem);
+        const int64_t want = (n + (int64_t)WARP_TILE * NWARP - 1) / ((int64_t)WARP_TILE * NWARP);
+        run_blocks = (int)std::min<int64_t>(want, (int64_t)h->num_sms * bps);
     }
-    if (var < 0) {
-        h->last_error = "no pass kernel fits on this device";
-        return FCM_ERR_CUDA;
-    }
-    PassFn kfirst = g_table.k[C][mk][pass0][var];
-    PassFn kiter = g_table.k[C][mk][P_ITER][var];
-    const int smem_first = g_table.smem[C][mk][pass0][var];
-    const int smem_iter = g_table.smem[C][mk][P_ITER][var];
-    const int64_t per_block = var == 1 ? 1024 : NT;  // pixels one block covers per step
-    const int64_t want = (n + per_block - 1) / per_block;
-    const int nblocks = (int)std::max<int64_t>(
-        1, std::min<int64_t>(want, (int64_t)h->num_sms * std::min(bps, bps0)));
+    if (run_blocks > 0) {
+        // the whole run: one cooperative launch (all blocks co-resident)
+        void* args[2] = {&h->d_st, &h->d_partials};
+        CK(cudaLaunchCooperativeKernel(krun, dim3(run_blocks), dim3(NT), args, run_smem, h->stream));
+        h->last_blocks = run_blocks;
+        h->last_path = 2;
+    } else {
+    Launch L;
+    if ((rc = choose_launch(h, n, C, mk, pass0, dx, dU, hs->Uprev, options, &L))) return rc;
+    PassFn kfirst = L.kfirst, kiter = L.kiter;
+    const int smem_first = L.smem_first, smem_iter = L.smem_iter, var = L.var, nblocks = L.nblocks;
+    h->last_blocks = nblocks;
+    h->last_path = (options & FCM_OPT_NO_GRAPH) ? 0 : 1;
 
     if (options & FCM_OPT_NO_GRAPH) {
         if ((rc = run_host_loop(h, kfirst, smem_first, kiter, smem_iter, nblocks))) return rc;
@@ -387,6 +423,7 @@ int fcm_run(fcm_handle h, const float* x, int64_t n, int C, float m, float eps, 
             it = h->graphs.emplace(key, ge).first;
         }
         CK(cudaGraphLaunch(it->second.exec, h->stream));
+    }
     }
 
     CK(cudaMemcpyAsync(hs, h->d_st, sizeof(RunState), cudaMemcpyDeviceToHost, h->stream));
@@ -412,6 +449,57 @@ int fcm_run(fcm_handle h, const float* x, int64_t n, int C, float m, float eps, 
         return FCM_ERR_CUDA;
     }
     return hs->status;
+}
+
+int fcm_time_pass(fcm_handle h, const float* x, int64_t n, int C, float m, float* U, const float* V,
+                  int launches, int options, float* ms_per_launch) {
+    if (!h) return FCM_ERR_INVALID_ARG;
+    if (!x || !U || !V || !ms_per_launch) return ctx_invalid(h, "null argument");
+    if (n < 1 || C < 1 || C > FCM_MAX_CLUSTERS || !(m > 1.0f) || launches < 1)
+        return ctx_invalid(h, "bad size, C, m or launch count");
+    if (!is_device_pointer(x) || !is_device_pointer(U)) return ctx_invalid(h, "x and U must be device memory");
+    DeviceGuard g(h->device);
+    int rc = ensure_single_workspace(h);
+    if (rc) return rc;
+    RunState* hs = h->h_st;
+    std::memset(hs, 0, sizeof(RunState));
+    hs->x = x;
+    hs->Uprev = U;
+    hs->U = U;
+    hs->n = n;
+    hs->m = m;
+    hs->inv_m1 = (float)(1.0 / ((double)m - 1.0));
+    hs->eps = 0.0f;                 // delta < 0 never holds: no stop
+    hs->max_iter = launches + 2;    // nor does the iteration bound
+    hs->C = C;
+    hs->k = 1;
+    hs->status = STATUS_RUNNING;
+    const bool V_dev = is_device_pointer(V);
+    if (!V_dev)
+        for (int j = 0; j < C; ++j) {
+            hs->V[j] = V[j];
+            hs->V64[j] = V[j];
+        }
+    CK(cudaMemcpyAsync(h->d_st, hs, sizeof(RunState), cudaMemcpyHostToDevice, h->stream));
+    if (V_dev) CK(cudaMemcpyAsync(&h->d_st->V, V, sizeof(float) * C, cudaMemcpyDeviceToDevice, h->stream));
+    Launch L;
+    if ((rc = choose_launch(h, n, C, mkind_of(m), P_ACCUM0, x, U, U, options, &L))) return rc;
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    const cudaGraphConditionalHandle none = 0;
+    cudaEventRecord(e0, h->stream);
+    for (int t = 0; t < launches; ++t)
+        L.kiter<<<L.nblocks, NT, L.smem_iter, h->stream>>>(h->d_st, h->d_partials, none, 0);
+    cudaEventRecord(e1, h->stream);
+    cudaError_t e = cudaEventSynchronize(e1);
+    float ms = 0.0f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (e != cudaSuccess) return ctx_fail(h, e, "timing the pass");
+    *ms_per_launch = ms / launches;
+    return FCM_OK;
 }
 
 int fcm_get_trace(fcm_handle h, double* delta, double* J, double* V, int cap) {

@@ -65,7 +65,10 @@ __device__ __forceinline__ float pow_m(float u, float m) {
 }
 
 // Memberships of one pixel x against C centers v (Eq. 4). Writes u[j] and
-// um[j] = u[j]^m; returns this pixel's term of J_m, sum_j u_j^m d_j^2 (Eq. 1).
+// um[j] = u[j]^m; returns this pixel's term of J_m, sum_j u_j^m d_j^2 (Eq. 1),
+// through its closed form under Eq. 4: with u_j = w_j / S and
+// w_j = (d2min / d2_j)^(1/(m-1)), u_j^m d2_j = d2min w_j / S^m, so the term is
+// d2min * S^(1-m) (and 0 when the pixel sits on a center).
 template <int C, int MK>
 __device__ __forceinline__ float membership(float x, const float (&v)[C], float m,
                                             float inv_m1, float (&u)[C], float (&um)[C]) {
@@ -77,6 +80,7 @@ __device__ __forceinline__ float membership(float x, const float (&v)[C], float 
         d2[j] = __fmul_rn(d, d);
         dmin = fminf(dmin, d2[j]);
     }
+    float Ji = 0.0f;
     if (dmin > 0.0f) {
         float w[C];
         if (MK == M_GENERIC) {
@@ -100,6 +104,10 @@ __device__ __forceinline__ float membership(float x, const float (&v)[C], float 
         const float r = rcp_approx(S);
 #pragma unroll
         for (int j = 0; j < C; ++j) u[j] = w[j] * r;
+        if (MK == M_TWO) Ji = dmin * r;
+        else if (MK == M_THREE) Ji = dmin * r * r;
+        else if (MK == M_ONE_HALF) Ji = dmin * sqrt_approx(r);
+        else Ji = dmin * ex2_approx((1.0f - m) * lg2_approx(S));
     } else {
         int nz = 0;
 #pragma unroll
@@ -108,13 +116,115 @@ __device__ __forceinline__ float membership(float x, const float (&v)[C], float 
 #pragma unroll
         for (int j = 0; j < C; ++j) u[j] = (d2[j] == 0.0f) ? share : 0.0f;
     }
-    float Ji = 0.0f;
+#pragma unroll
+    for (int j = 0; j < C; ++j) um[j] = pow_m<MK>(u[j], m);
+    return Ji;
+}
+
+// ---------------------------------------------------------------------------
+// Two pixels at once with the packed FP32x2 instructions of sm_100+ (PTX
+// add/sub/mul/fma.rn.f32x2). A pair lives in one 64-bit register pair:
+// the low half is the first pixel.
+// ---------------------------------------------------------------------------
+typedef uint64_t f2;
+
+__device__ __forceinline__ f2 pack2(float a, float b) {
+    f2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void unpack2(f2 r, float& a, float& b) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(r));
+}
+__device__ __forceinline__ float lo2(f2 r) { float a, b; unpack2(r, a, b); return a; }
+__device__ __forceinline__ float hi2(f2 r) { float a, b; unpack2(r, a, b); return b; }
+__device__ __forceinline__ f2 add2(f2 a, f2 b) {
+    f2 r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f2 sub2(f2 a, f2 b) {
+    f2 r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f2 mul2(f2 a, f2 b) {
+    f2 r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) {
+    f2 r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
+}
+__device__ __forceinline__ f2 abs2(f2 a) { return a & 0x7fffffff7fffffffull; }
+
+// Memberships of two pixels (packed x2) against C centers (each packed as
+// (v_j, v_j)), Eq. 4. Writes u2[j], um2[j] = u^m and returns the pair of J
+// terms sum_j u_j^m d_j^2.
+//
+// m = 2 and m = 3 use the product form: with b_j = d_j^2 (m = 2) or |d_j|
+// (m = 3) the weights 1/b_j share the denominator prod_k b_k, so
+//   u_j = P_j / sum_k P_k,   P_j = prod_{k != j} b_k,
+// one reciprocal per pixel; a pixel equal to exactly one center gets u = 1
+// there and 0 elsewhere without a special case. The J term is u_j b_j for any
+// j when m = 2 (both equal 1 / sum_k 1/d_k^2), and (u_j b_j)^2 when m = 3.
+// A pixel whose sum_k P_k is 0 (two or more centers hit exactly) or not
+// finite (products out of FP32 range) takes the scalar weight form above,
+// as do the other fuzzifiers.
+template <int C, int MK>
+__device__ __forceinline__ f2 membership_pair(f2 x2, const f2 (&v2)[C], float m, float inv_m1,
+                                              const float (&v)[C], f2 (&u2)[C], f2 (&um2)[C]) {
+    if (MK == M_TWO || MK == M_THREE) {
+        f2 b[C];
+#pragma unroll
+        for (int j = 0; j < C; ++j) {
+            const f2 d = sub2(x2, v2[j]);
+            b[j] = (MK == M_TWO) ? mul2(d, d) : abs2(d);
+        }
+        f2 P[C];
+        if (C == 1) {
+            P[0] = pack2(1.0f, 1.0f);
+        } else {
+            f2 pre[C], suf[C];
+#pragma unroll
+            for (int j = 1; j < C; ++j) pre[j] = (j == 1) ? b[0] : mul2(pre[j - 1], b[j - 1]);
+#pragma unroll
+            for (int j = C - 2; j >= 0; --j) suf[j] = (j == C - 2) ? b[C - 1] : mul2(suf[j + 1], b[j + 1]);
+#pragma unroll
+            for (int j = 0; j < C; ++j) P[j] = (j == 0) ? suf[0] : (j == C - 1) ? pre[C - 1] : mul2(pre[j], suf[j]);
+        }
+        f2 S = P[0];
+#pragma unroll
+        for (int j = 1; j < C; ++j) S = add2(S, P[j]);
+        float s0, s1;
+        unpack2(S, s0, s1);
+        const float inf = __int_as_float(0x7f800000);
+        if (s0 > 0.0f && s0 < inf && s1 > 0.0f && s1 < inf) {
+            const f2 r = pack2(rcp_approx(s0), rcp_approx(s1));
+#pragma unroll
+            for (int j = 0; j < C; ++j) {
+                u2[j] = mul2(P[j], r);
+                const f2 uu = mul2(u2[j], u2[j]);
+                um2[j] = (MK == M_TWO) ? uu : mul2(uu, u2[j]);
+            }
+            const f2 t = mul2(u2[0], b[0]);
+            return (MK == M_TWO) ? t : mul2(t, t);
+        }
+    }
+    // scalar weight form, one pixel at a time
+    float xa, xb;
+    unpack2(x2, xa, xb);
+    float ua[C], uma[C], ub[C], umb[C];
+    const float ja = membership<C, MK>(xa, v, m, inv_m1, ua, uma);
+    const float jb = membership<C, MK>(xb, v, m, inv_m1, ub, umb);
 #pragma unroll
     for (int j = 0; j < C; ++j) {
-        um[j] = pow_m<MK>(u[j], m);
-        Ji = fmaf(um[j], d2[j], Ji);
+        u2[j] = pack2(ua[j], ub[j]);
+        um2[j] = pack2(uma[j], umb[j]);
     }
-    return Ji;
+    return pack2(ja, jb);
 }
 
 __device__ __forceinline__ float warp_sum(float v) {

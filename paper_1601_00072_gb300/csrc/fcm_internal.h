@@ -10,6 +10,7 @@ namespace fcm {
 
 constexpr int NT = 256;                                  // threads per block of the pass
 constexpr int NWARP = NT / 32;
+constexpr int WARP_TILE = 128;                           // pixels per warp tile of the TMA kernels
 constexpr int SLOTS_MAX = 2 * FCM_MAX_CLUSTERS + 4;      // num[C], den[C], J, delta, 2 flags
 constexpr int STATUS_RUNNING = 2;
 
@@ -58,9 +59,14 @@ typedef void (*PassFn)(RunState*, double*, cudaGraphConditionalHandle, int);
 // Kernel table: [C][m kind][pass][variant], variant 0 = grid-stride scalar
 // loads (any n), 1 = TMA ring (n % 4 == 0, 16-byte aligned rows); smem holds
 // each kernel's dynamic shared memory in bytes.
+typedef void (*RunFn)(RunState*, double*);
+
 struct SingleTable {
     PassFn k[FCM_MAX_CLUSTERS + 1][4][P_COUNT][2];
     int smem[FCM_MAX_CLUSTERS + 1][4][P_COUNT][2];
+    // the whole run in one cooperative launch: [C][m kind][0 = from U^0, 1 = from V^0]
+    RunFn run[FCM_MAX_CLUSTERS + 1][4][2];
+    int run_smem[FCM_MAX_CLUSTERS + 1];
 };
 
 void register_single_c1(SingleTable&);

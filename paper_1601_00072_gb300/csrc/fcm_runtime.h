@@ -33,6 +33,9 @@ struct fcm_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
     int num_sms = 0;
+    bool coop = false;        // cooperative launch supported
+    int last_blocks = 0;      // grid of the last run
+    int last_path = 0;        // 0 host loop, 1 graph WHILE loop, 2 one cooperative launch
     int max_smem_optin = 0;
     std::string device_name;
     std::string last_error;

@@ -14,13 +14,14 @@
 // cluster (Sec. 4.3) become this single pass.
 //
 // Two kernels move the pixels:
-//  * k_fcm_pass_tma (n % 4 == 0, 16-byte aligned rows): a persistent block
-//    walks 1024-pixel tiles; thread 0 streams each tile's x and U rows into a
-//    multi-stage shared-memory ring with 1-D TMA bulk copies completing on
-//    mbarriers, so the bytes in flight do not depend on register occupancy;
-//    the threads read 4 pixels each from shared memory and store U^k with
-//    128-bit stores. x carries an L2 evict-last hint (it is re-read every
-//    iteration and fits in L2), U an evict-first hint.
+//  * k_fcm_pass_tma (n % 4 == 0, 16-byte aligned rows): persistent warps
+//    each stream 128-pixel tiles of x and of the C rows of U through a private
+//    multi-stage shared-memory ring filled by 1-D TMA bulk copies that
+//    complete on mbarriers, so the bytes in flight do not depend on register
+//    occupancy and no warp waits for another; each lane reads 4 pixels from
+//    shared memory and stores U^k with 128-bit stores. x carries an L2
+//    evict-last hint (it is re-read every iteration and fits in L2), U an
+//    evict-first hint.
 //  * k_fcm_pass_ldg (any n): grid-stride loop with scalar loads.
 //
 // Reduction: warp shuffle -> shared memory -> one FP64 partial per block ->
@@ -39,8 +40,9 @@
 namespace fcm {
 namespace {
 
-// Bound of every mbarrier wait (polls); TMA tiles land in microseconds.
-constexpr uint32_t WAIT_LIMIT = 1u << 22;
+// Bound of every mbarrier wait: 2048 suspensions of about 1 ms (about 2 s);
+// TMA tiles land in microseconds.
+constexpr uint32_t WAIT_LIMIT = 2048;
 
 __device__ __forceinline__ double warp_max_d(double v) {
 #pragma unroll
@@ -98,17 +100,25 @@ __device__ __forceinline__ bool pass_prologue(RunState* st, int pass, cudaGraphC
     return true;
 }
 
-// Block reduction, FP64 partial, last-block combine and loop control.
+// Block reduction, per-block partials, last-block combine and loop control.
 // Slots: num[C], den[C], J, max|dU|, bad-input flag, timeout flag.
+//
+// The finisher runs when the pass's memory traffic is over, so it is kept
+// short: within a block the 8 warp totals are added in FP32 (8 terms); the
+// block totals go to slot-major FP32 partials[slot * gridDim.x + block]; the
+// last block to finish gives one slot to each warp, whose lanes add the block
+// totals in FP64 in a fixed order (lane-strided, then a shuffle tree), so the
+// cross-block sums of up to 10^7-pixel terms are FP64 and deterministic.
 template <int C, int PASS>
-__device__ __forceinline__ void finish_pass(RunState* st, double* partials,
+__device__ __forceinline__ void finish_pass(RunState* st, double* partials_raw,
                                             cudaGraphConditionalHandle cond, int use_cond,
                                             const float (&num)[C], const float (&den)[C], float Jacc,
                                             float dmax, bool bad, bool tmo) {
     constexpr int S = 2 * C + 4;
     static_assert(S <= SLOTS_MAX, "partial slots");
+    float* partials = reinterpret_cast<float*>(partials_raw);
     __shared__ float s_red[NWARP][S];
-    __shared__ double s_red64[NWARP][S];
+    __shared__ double s_tot[S];
     __shared__ int s_last;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     {
@@ -130,49 +140,41 @@ __device__ __forceinline__ void finish_pass(RunState* st, double* partials,
         }
     }
     __syncthreads();
-    if (warp == 0) {
+    if (threadIdx.x < S) {
+        const int s = threadIdx.x;
+        float a = s_red[0][s];
 #pragma unroll
-        for (int s = 0; s < S; ++s) {
-            double a = lane < NWARP ? (double)s_red[lane][s] : 0.0;
-            a = (s <= 2 * C) ? warp_sum(a) : warp_max_d(a);
-            if (lane == 0) __stcg(partials + (int64_t)blockIdx.x * S + s, a);
-        }
-        if (lane == 0) {
-            __threadfence();
-            const unsigned t = atomicAdd(&st->ticket, 1u);
-            s_last = (t == gridDim.x - 1);
-        }
+        for (int w = 1; w < NWARP; ++w) a = (s <= 2 * C) ? a + s_red[w][s] : fmaxf(a, s_red[w][s]);
+        __stcg(partials + (int64_t)s * gridDim.x + blockIdx.x, a);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned t = atomicAdd(&st->ticket, 1u);
+        s_last = (t == gridDim.x - 1);
     }
     __syncthreads();
     if (!s_last) return;
 
-    // ---- last block: FP64 combine of all partials in block order ----
+    // ---- last block: one slot per warp, FP64 over the block totals ----
     __threadfence();
-    double acc[S];
-#pragma unroll
-    for (int s = 0; s < S; ++s) acc[s] = 0.0;
-    for (int b = threadIdx.x; b < (int)gridDim.x; b += NT) {
-#pragma unroll
-        for (int s = 0; s < S; ++s) {
-            const double p = __ldcg(partials + (int64_t)b * S + s);
-            acc[s] = (s <= 2 * C) ? acc[s] + p : fmax(acc[s], p);
+    for (int s = warp; s < S; s += NWARP) {
+        const float* ps = partials + (int64_t)s * gridDim.x;
+        double a = 0.0;
+        if (s <= 2 * C) {
+            for (int b = lane; b < (int)gridDim.x; b += 32) a += (double)__ldcg(ps + b);
+            a = warp_sum(a);
+        } else {
+            for (int b = lane; b < (int)gridDim.x; b += 32) a = fmax(a, (double)__ldcg(ps + b));
+            a = warp_max_d(a);
         }
-    }
-#pragma unroll
-    for (int s = 0; s < S; ++s) acc[s] = (s <= 2 * C) ? warp_sum(acc[s]) : warp_max_d(acc[s]);
-    if (lane == 0) {
-#pragma unroll
-        for (int s = 0; s < S; ++s) s_red64[warp][s] = acc[s];
+        if (lane == 0) s_tot[s] = a;
     }
     __syncthreads();
     if (threadIdx.x != 0) return;
     double tot[S];
 #pragma unroll
-    for (int s = 0; s < S; ++s) {
-        double a = s_red64[0][s];
-        for (int w = 1; w < NWARP; ++w) a = (s <= 2 * C) ? a + s_red64[w][s] : fmax(a, s_red64[w][s]);
-        tot[s] = a;
-    }
+    for (int s = 0; s < S; ++s) tot[s] = s_tot[s];
 
     int cont = 1;
     if (tot[2 * C + 3] != 0.0) {
@@ -295,26 +297,107 @@ __global__ void __launch_bounds__(NT) k_fcm_pass_ldg(RunState* __restrict__ st, 
 }
 
 // ---------------------------------------------------------------------------
-// n % 4 == 0, 16-byte aligned rows: TMA bulk-copy ring.
+// n % 4 == 0, 16-byte aligned rows: one TMA bulk-copy ring per warp.
 // ---------------------------------------------------------------------------
-constexpr int TPX = 4;                 // pixels per thread per tile
-constexpr int TILE = NT * TPX;         // 1024 pixels
+constexpr int WTILE = WARP_TILE;       // 128 pixels per warp tile: 2 steps of 2 per lane
 
 template <int PASS, int C>
 struct TmaShape {
-    static constexpr int ROWS = (PASS == P_INITV) ? 1 : 1 + C;   // x, then U^{k-1} rows
-    static constexpr int STAGE_FLOATS = ROWS * TILE;
-    static constexpr int RAW = (100 * 1024) / (STAGE_FLOATS * 4);
-    static constexpr int STAGES = RAW < 2 ? 2 : (RAW > 6 ? 6 : RAW);
-    static constexpr int SMEM_BYTES = STAGES * STAGE_FLOATS * 4;
+    static constexpr int ROWS = (PASS == P_INITV) ? 1 : 1 + C;    // x, then U^{k-1} rows
+    static constexpr int STAGE_FLOATS = ROWS * WTILE;              // one warp's stage
+    // three blocks per SM (C <= 4) or two: about 72 or 108 KB of ring per block
+    static constexpr int BLOCKS_PER_SM = C <= 4 ? 3 : 2;
+    static constexpr int RAW = ((BLOCKS_PER_SM == 3 ? 72 : 108) * 1024) / (NWARP * STAGE_FLOATS * 4);
+    static constexpr int STAGES = RAW < 2 ? 2 : (RAW > 8 ? 8 : RAW);
+    static constexpr int SMEM_BYTES = NWARP * STAGES * STAGE_FLOATS * 4;
 };
 
+// Per-thread accumulators of one pass: packed pairs for the membership passes,
+// scalars for the first pass from a given U^0.
+template <int C>
+struct Acc {
+    f2 num2[C], den2[C], J2;
+    float num[C], den[C], J, dmax;
+    bool bad;
+    __device__ __forceinline__ void reset() {
+#pragma unroll
+        for (int j = 0; j < C; ++j) {
+            num2[j] = den2[j] = pack2(0.0f, 0.0f);
+            num[j] = den[j] = 0.0f;
+        }
+        J2 = pack2(0.0f, 0.0f);
+        J = dmax = 0.0f;
+        bad = false;
+    }
+    // fold the packed halves into the scalar sums
+    __device__ __forceinline__ void fold() {
+#pragma unroll
+        for (int j = 0; j < C; ++j) {
+            num[j] += lo2(num2[j]) + hi2(num2[j]);
+            den[j] += lo2(den2[j]) + hi2(den2[j]);
+        }
+        J += lo2(J2) + hi2(J2);
+    }
+};
+
+// One warp tile held in shared memory at sb (x, then the C rows of U^{k-1}
+// unless PASS == P_INITV): lane l handles pixels 2l, 2l+1 and 64+2l, 65+2l.
+// Writes U^k (not for P_ACCUM0) and accumulates the pass's sums.
 template <int C, int MK, int PASS>
-__global__ void __launch_bounds__(NT, 2) k_fcm_pass_tma(RunState* __restrict__ st, double* __restrict__ partials,
+__device__ __forceinline__ void tile_work(const float* sb, int cnt, int64_t i0, int lane, float* U, int64_t n,
+                                          const float (&v)[C], const f2 (&v2)[C], float m, float inv_m1,
+                                          uint64_t pol_u, Acc<C>& a) {
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+        const int pp = q * (WTILE / 2) + 2 * lane;
+        if (pp >= cnt) continue;  // cnt is a multiple of 4: pp + 1 < cnt too
+        const float2 xv = lds2(sb + pp);
+        float2 uo[C];
+        if (PASS != P_INITV) {
+#pragma unroll
+            for (int j = 0; j < C; ++j) uo[j] = lds2(sb + (1 + j) * WTILE + pp);
+        }
+        if (PASS == P_ACCUM0) {
+#pragma unroll
+            for (int p = 0; p < 2; ++p) {
+                float uop[C], unp[C];
+#pragma unroll
+                for (int j = 0; j < C; ++j) uop[j] = p == 0 ? uo[j].x : uo[j].y;
+                pixel_step<C, MK, PASS>(p == 0 ? xv.x : xv.y, v, m, inv_m1, uop, unp, a.num, a.den, a.J,
+                                        a.dmax, a.bad);
+            }
+        } else {
+            if (PASS == P_INITV) a.bad |= !finite_f(xv.x) || !finite_f(xv.y);
+            const f2 xq = pack2(xv.x, xv.y);
+            f2 u2[C], um2[C];
+            a.J2 = add2(a.J2, membership_pair<C, MK>(xq, v2, m, inv_m1, v, u2, um2));
+#pragma unroll
+            for (int j = 0; j < C; ++j) {
+                a.num2[j] = fma2(um2[j], xq, a.num2[j]);
+                a.den2[j] = add2(a.den2[j], um2[j]);
+                if (PASS == P_ITER) {
+                    float da, db;
+                    unpack2(sub2(u2[j], pack2(uo[j].x, uo[j].y)), da, db);
+                    a.dmax = fmaxf(a.dmax, fmaxf(fabsf(da), fabsf(db)));
+                }
+                st_hint2(U + (int64_t)j * n + i0 + pp, u2[j], pol_u);
+            }
+        }
+    }
+}
+
+// Every warp streams its own 128-pixel tiles (warp tile t = global warp id
+// + k * number of warps) through a private ring of STAGES shared-memory
+// stages: lane 0 issues the bulk copies of x and the C rows of U^{k-1} and
+// arms the stage's mbarrier with the byte count; all lanes wait on it, each
+// lane processes 4 pixels, and after __syncwarp lane 0 refills the stage with
+// the warp's tile k + STAGES. Warps never wait for one another.
+template <int C, int MK, int PASS>
+__global__ void __launch_bounds__(NT, (C <= 4 ? 3 : 2)) k_fcm_pass_tma(RunState* __restrict__ st, double* __restrict__ partials,
                                                          cudaGraphConditionalHandle cond, int use_cond) {
     using Sh = TmaShape<PASS, C>;
-    extern __shared__ __align__(128) float ring[];
-    __shared__ __align__(8) uint64_t full[Sh::STAGES];
+    extern __shared__ __align__(128) float ring_all[];
+    __shared__ __align__(8) uint64_t full_all[NWARP][Sh::STAGES];
     if (!pass_prologue(st, PASS, cond, use_cond)) return;
 
     const float* __restrict__ x = st->x;
@@ -322,81 +405,415 @@ __global__ void __launch_bounds__(NT, 2) k_fcm_pass_tma(RunState* __restrict__ s
     float* U = st->U;
     const int64_t n = st->n;
     const float m = st->m, inv_m1 = st->inv_m1;
-    PassVars<C> pv;
-    load_centers<C, PASS>(st, pv);
+    float v[C];
+    f2 v2[C];
+    Acc<C> a;
+    a.reset();
+#pragma unroll
+    for (int j = 0; j < C; ++j) {
+        v[j] = (PASS == P_INITV) ? st->V0[j] : st->V[j];
+        v2[j] = pack2(v[j], v[j]);
+        if (PASS == P_INITV) a.bad |= !finite_f(v[j]);
+    }
 
-    const int64_t ntiles = (n + TILE - 1) / TILE;
-    const int64_t nk = ntiles > blockIdx.x ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float* ring = ring_all + warp * (Sh::STAGES * Sh::STAGE_FLOATS);
+    uint64_t* full = full_all[warp];
+    const int64_t nwarps = (int64_t)gridDim.x * NWARP;
+    const int64_t gw = (int64_t)blockIdx.x * NWARP + warp;
+    const int64_t ntiles = (n + WTILE - 1) / WTILE;
+    const int64_t nk = ntiles > gw ? (ntiles - 1 - gw) / nwarps + 1 : 0;
     const uint64_t pol_x = policy_evict_last();
     const uint64_t pol_u = policy_evict_first();
 
-    if (threadIdx.x == 0) {
+    if (lane == 0) {
 #pragma unroll
         for (int s = 0; s < Sh::STAGES; ++s) mbar_init(&full[s], 1);
         mbar_fence_init();
     }
-    __syncthreads();
+    __syncwarp();
 
-    // Thread 0 only: start the copies of this block's k-th tile into stage s.
+    // Lane 0 only: start the copies of this warp's k-th tile into stage s.
     auto issue = [&](int64_t k, int s) {
-        const int64_t i0 = (blockIdx.x + k * gridDim.x) * (int64_t)TILE;
-        const uint32_t bytes = (uint32_t)min((int64_t)TILE, n - i0) * 4u;  // multiple of 16
+        const int64_t i0 = (gw + k * nwarps) * (int64_t)WTILE;
+        const uint32_t bytes = (uint32_t)min((int64_t)WTILE, n - i0) * 4u;  // multiple of 16
         float* dst = ring + s * Sh::STAGE_FLOATS;
         mbar_expect_tx(&full[s], bytes * Sh::ROWS);
         bulk_g2s(dst, x + i0, bytes, &full[s], pol_x);
         if (PASS != P_INITV) {
 #pragma unroll
-            for (int j = 0; j < C; ++j) bulk_g2s(dst + (1 + j) * TILE, Uold + (int64_t)j * n + i0, bytes, &full[s], pol_u);
+            for (int j = 0; j < C; ++j)
+                bulk_g2s(dst + (1 + j) * WTILE, Uold + (int64_t)j * n + i0, bytes, &full[s], pol_u);
         }
     };
-    if (threadIdx.x == 0)
+    if (lane == 0)
         for (int s = 0; s < Sh::STAGES && s < nk; ++s) issue(s, s);
 
     bool tmo = false;
-    const int p0 = threadIdx.x * TPX;
-    for (int64_t k = 0; k < nk; ++k) {
-        const int s = (int)(k % Sh::STAGES);
-        const uint32_t parity = (uint32_t)((k / Sh::STAGES) & 1);
+    int s = 0;
+    uint32_t parity = 0;
+    int64_t i0 = gw * (int64_t)WTILE;
+    const int64_t tile_stride = nwarps * (int64_t)WTILE;
+    for (int64_t k = 0; k < nk; ++k, i0 += tile_stride) {
         const bool ok = mbar_wait_bounded(&full[s], parity, WAIT_LIMIT);
-        const int64_t i0 = (blockIdx.x + k * gridDim.x) * (int64_t)TILE;
-        const int64_t cnt = min((int64_t)TILE, n - i0);
-        if (ok && p0 < cnt) {
-            const float* sb = ring + s * Sh::STAGE_FLOATS;
-            const float4 xv = lds4(sb + p0);
-            float4 uo[C], un[C];
-            if (PASS != P_INITV) {
-#pragma unroll
-                for (int j = 0; j < C; ++j) uo[j] = lds4(sb + (1 + j) * TILE + p0);
-            }
-#pragma unroll
-            for (int p = 0; p < 4; ++p) {
-                float uop[C], unp[C];
-#pragma unroll
-                for (int j = 0; j < C; ++j) uop[j] = (PASS != P_INITV) ? comp(uo[j], p) : 0.0f;
-                pixel_step<C, MK, PASS>(comp(xv, p), pv.v, m, inv_m1, uop, unp, pv.num, pv.den, pv.Jacc,
-                                        pv.dmax, pv.bad);
-#pragma unroll
-                for (int j = 0; j < C; ++j) set_comp(un[j], p, unp[j]);
-            }
-            if (PASS != P_ACCUM0) {
-#pragma unroll
-                for (int j = 0; j < C; ++j) st_hint4(U + (int64_t)j * n + i0 + p0, un[j], pol_u);
-            }
-        }
-        // every thread is done with stage s (and agrees on any timeout)
-        if (__syncthreads_or(!ok)) {
+        if (__any_sync(0xffffffffu, !ok)) {
             tmo = true;
-            if (threadIdx.x == 0) {
-                // let the copies still in flight land before the block exits
+            if (lane == 0) {
+                // let the copies still in flight land before the warp leaves
                 const int64_t last = min(nk, k + (int64_t)Sh::STAGES);
                 for (int64_t kk = k; kk < last; ++kk)
                     mbar_wait_bounded(&full[kk % Sh::STAGES], (uint32_t)((kk / Sh::STAGES) & 1), WAIT_LIMIT);
             }
             break;
         }
-        if (threadIdx.x == 0 && k + Sh::STAGES < nk) issue(k + Sh::STAGES, s);
+        const int cnt = (int)min((int64_t)WTILE, n - i0);
+        tile_work<C, MK, PASS>(ring + s * Sh::STAGE_FLOATS, cnt, i0, lane, U, n, v, v2, m, inv_m1, pol_u, a);
+        __syncwarp();  // every lane is done reading stage s
+        if (lane == 0 && k + Sh::STAGES < nk) issue(k + Sh::STAGES, s);
+        if (++s == Sh::STAGES) {
+            s = 0;
+            parity ^= 1u;
+        }
     }
-    finish_pass<C, PASS>(st, partials, cond, use_cond, pv.num, pv.den, pv.Jacc, pv.dmax, pv.bad, tmo);
+    if (PASS != P_ACCUM0) a.fold();
+    finish_pass<C, PASS>(st, partials, cond, use_cond, a.num, a.den, a.J, a.dmax, a.bad, tmo);
+}
+
+// ---------------------------------------------------------------------------
+// The whole run in one cooperative launch (n % 4 == 0, aligned rows).
+// ---------------------------------------------------------------------------
+
+// Compensated FP32 ("double-float") sum, hi + lo, with Knuth's TwoSum: the
+// cross-block sums of the center numerators/denominators and of J carry about
+// 44 bits, using only FP32 instructions in every block.
+struct DF {
+    float hi, lo;
+};
+__device__ __forceinline__ void df_add(DF& a, float b) {
+    const float s = __fadd_rn(a.hi, b);
+    const float bb = __fsub_rn(s, a.hi);
+    const float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    a.hi = s;
+    a.lo = __fadd_rn(a.lo, e);
+}
+__device__ __forceinline__ DF df_merge(DF a, DF b) {
+    const float s = __fadd_rn(a.hi, b.hi);
+    const float bb = __fsub_rn(s, a.hi);
+    const float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(b.hi, bb));
+    const float lo = __fadd_rn(__fadd_rn(a.lo, b.lo), e);
+    const float hi = __fadd_rn(s, lo);  // Fast2Sum renormalisation (|s| >= |lo|)
+    return DF{hi, __fsub_rn(lo, __fsub_rn(hi, s))};
+}
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Grid barrier spin bound: about 1 s of 128 ns sleeps.
+constexpr uint32_t GRID_WAIT_LIMIT = 1u << 23;
+
+// Every warp keeps the same tiles in every pass, so the U tile a warp reads in
+// pass p + 1 is the one it wrote in pass p. Its ring therefore streams one
+// sequence of loads across passes (look-ahead min(STAGES, tiles per warp), so
+// a tile is never re-read before the warp has written it; a proxy fence orders
+// the warp's stores before its own TMA re-read) and keeps DRAM busy while the
+// grid exchanges the 2C + 4 sums of a pass. After each pass every block
+// publishes its FP32 totals, waits at a bounded grid barrier (co-residency is
+// guaranteed by the cooperative launch), and computes the cross-block sums in
+// the same fixed order as every other block, so all blocks derive the same
+// V^{k+1} and the same stop decision. Pass 0 is INIT (V^1 from U^0, or U^0
+// from V^0); pass p >= 1 is iteration p of Algorithm 1.
+template <int C, int MK, int INIT>
+__global__ void __launch_bounds__(NT, (C <= 4 ? 3 : 2)) k_fcm_run_tma(RunState* __restrict__ st,
+                                                                      double* __restrict__ partials_raw) {
+    using Sh = TmaShape<P_ITER, C>;
+    constexpr int S = 2 * C + 4;
+    extern __shared__ __align__(128) float ring_all[];
+    __shared__ __align__(8) uint64_t full_all[NWARP][Sh::STAGES];
+    __shared__ float s_red[NWARP][S];
+    __shared__ DF s_df[2 * C + 1];
+    __shared__ float s_mx[3];
+    __shared__ float s_v[C];
+    __shared__ double s_v64[C];
+    __shared__ int s_empty[C];
+    __shared__ int s_err;
+
+    const float* __restrict__ x = st->x;
+    const float* U0 = st->Uprev;
+    float* U = st->U;
+    const int64_t n = st->n;
+    const float m = st->m, inv_m1 = st->inv_m1, eps = st->eps;
+    const int max_iter = st->max_iter;
+    unsigned* gbar = &st->ticket;
+    float* partials = reinterpret_cast<float*>(partials_raw);
+
+    float v[C];
+    f2 v2[C];
+    double v64[C];
+#pragma unroll
+    for (int j = 0; j < C; ++j) {
+        v[j] = st->V0[j];
+        v2[j] = pack2(v[j], v[j]);
+        v64[j] = v[j];
+    }
+    int flags = 0;
+
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float* ring = ring_all + warp * (Sh::STAGES * Sh::STAGE_FLOATS);
+    uint64_t* full = full_all[warp];
+    const int64_t nwarps = (int64_t)gridDim.x * NWARP;
+    const int64_t gw = (int64_t)blockIdx.x * NWARP + warp;
+    const int64_t ntiles = (n + WTILE - 1) / WTILE;
+    const int nk = (int)(ntiles > gw ? (ntiles - 1 - gw) / nwarps + 1 : 0);
+    const int look = nk < Sh::STAGES ? nk : Sh::STAGES;
+    const int64_t tile_stride = nwarps * (int64_t)WTILE;
+    const int npass = 1 + max_iter;  // passes the run can take
+    const uint64_t pol_x = policy_evict_last();
+    const uint64_t pol_u = policy_evict_first();
+
+    if (lane == 0) {
+#pragma unroll
+        for (int s = 0; s < Sh::STAGES; ++s) mbar_init(&full[s], 1);
+        mbar_fence_init();
+    }
+    if (threadIdx.x == 0) s_err = 0;
+    __syncthreads();
+
+    // Issue side (lane 0): pass ip, tile ik of the next load, ring slot is.
+    int ip = 0, ik = 0, is = 0;
+    int64_t issued = 0;
+    auto issue_next = [&]() {
+        if (ip >= npass || nk == 0) return;
+        const int64_t i0 = gw * (int64_t)WTILE + ik * tile_stride;
+        const uint32_t bytes = (uint32_t)min((int64_t)WTILE, n - i0) * 4u;  // multiple of 16
+        const bool with_u = !(ip == 0 && INIT == P_INITV);
+        const float* Usrc = (ip == 0 || (ip == 1 && INIT == P_ACCUM0)) ? U0 : U;
+        float* dst = ring + is * Sh::STAGE_FLOATS;
+        mbar_expect_tx(&full[is], bytes * (with_u ? 1 + C : 1));
+        bulk_g2s(dst, x + i0, bytes, &full[is], pol_x);
+        if (with_u) {
+#pragma unroll
+            for (int j = 0; j < C; ++j)
+                bulk_g2s(dst + (1 + j) * WTILE, Usrc + (int64_t)j * n + i0, bytes, &full[is], pol_u);
+        }
+        ++issued;
+        if (++ik == nk) {
+            ik = 0;
+            ++ip;
+        }
+        if (++is == Sh::STAGES) is = 0;
+    };
+    if (lane == 0)
+        for (int t = 0; t < look; ++t) issue_next();
+
+    int cs = 0;  // consume side: ring slot and phase parity
+    uint32_t parity = 0;
+    int64_t consumed = 0;
+    bool stop = false, err = false;
+    int status = FCM_NOT_CONVERGED, iters = 0;
+    Acc<C> a;
+
+    for (int p = 0; !stop; ++p) {
+        a.reset();
+        if (p == 0 && INIT == P_INITV) {
+#pragma unroll
+            for (int j = 0; j < C; ++j) a.bad |= !finite_f(v[j]);
+        }
+        // ---- the pass over this warp's tiles ----
+        int64_t i0 = gw * (int64_t)WTILE;
+        for (int k = 0; k < nk; ++k, i0 += tile_stride) {
+            const bool ok = mbar_wait_bounded(&full[cs], parity, WAIT_LIMIT);
+            if (__any_sync(0xffffffffu, !ok)) {
+                err = true;
+                break;
+            }
+            const int cnt = (int)min((int64_t)WTILE, n - i0);
+            const float* sb = ring + cs * Sh::STAGE_FLOATS;
+            if (p == 0)
+                tile_work<C, MK, INIT>(sb, cnt, i0, lane, U, n, v, v2, m, inv_m1, pol_u, a);
+            else
+                tile_work<C, MK, P_ITER>(sb, cnt, i0, lane, U, n, v, v2, m, inv_m1, pol_u, a);
+            // this lane's stores of U must precede the warp's own TMA re-read
+            asm volatile("fence.proxy.async.global;" ::: "memory");
+            __syncwarp();
+            ++consumed;
+            if (lane == 0) issue_next();
+            if (++cs == Sh::STAGES) {
+                cs = 0;
+                parity ^= 1u;
+            }
+        }
+        if (!(p == 0 && INIT == P_ACCUM0)) a.fold();
+
+        // ---- block totals (FP32 over the 8 warps) -> partials[p & 1] ----
+        {
+            float vals[S];
+#pragma unroll
+            for (int j = 0; j < C; ++j) {
+                vals[j] = a.num[j];
+                vals[C + j] = a.den[j];
+            }
+            vals[2 * C] = a.J;
+            vals[2 * C + 1] = a.dmax;
+            vals[2 * C + 2] = a.bad ? 1.0f : 0.0f;
+            vals[2 * C + 3] = err ? 1.0f : 0.0f;
+#pragma unroll
+            for (int s = 0; s < S; ++s) vals[s] = (s <= 2 * C) ? warp_sum(vals[s]) : warp_max(vals[s]);
+            if (lane == 0) {
+#pragma unroll
+                for (int s = 0; s < S; ++s) s_red[warp][s] = vals[s];
+            }
+        }
+        __syncthreads();
+        float* part = partials + (int64_t)(p & 1) * S * gridDim.x;
+        if (threadIdx.x < S) {
+            const int s = threadIdx.x;
+            float t = s_red[0][s];
+#pragma unroll
+            for (int w = 1; w < NWARP; ++w) t = (s <= 2 * C) ? t + s_red[w][s] : fmaxf(t, s_red[w][s]);
+            __stcg(part + (int64_t)s * gridDim.x + blockIdx.x, t);
+        }
+        __syncthreads();
+        // ---- bounded grid barrier ----
+        if (threadIdx.x == 0) {
+            __threadfence();
+            atomicAdd(gbar, 1u);
+            const unsigned target = (unsigned)(p + 1) * gridDim.x;
+            uint32_t spins = 0;
+            while (ld_acquire_u32(gbar) < target) {
+                if (++spins > GRID_WAIT_LIMIT) {
+                    s_err = 1;
+                    break;
+                }
+                __nanosleep(128);
+            }
+            __threadfence();
+        }
+        __syncthreads();
+        if (s_err) {
+            status = FCM_ERR_TIMEOUT;
+            iters = p;
+            break;
+        }
+        // ---- cross-block sums, the same fixed order in every block ----
+        for (int s = warp; s < S; s += NWARP) {
+            const float* ps = part + (int64_t)s * gridDim.x;
+            if (s <= 2 * C) {
+                DF d{0.0f, 0.0f};
+                for (int b = lane; b < (int)gridDim.x; b += 32) df_add(d, __ldcg(ps + b));
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    DF e{__shfl_xor_sync(0xffffffffu, d.hi, o), __shfl_xor_sync(0xffffffffu, d.lo, o)};
+                    d = (lane & o) ? df_merge(e, d) : df_merge(d, e);
+                }
+                if (lane == 0) s_df[s] = d;
+            } else {
+                float t = 0.0f;
+                for (int b = lane; b < (int)gridDim.x; b += 32) t = fmaxf(t, __ldcg(ps + b));
+                t = warp_max(t);
+                if (lane == 0) s_mx[s - (2 * C + 1)] = t;
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x < C) {
+            // V^{p+1}_j = num_j / den_j in FP64 from the compensated sums (Eq. 3)
+            const int j = threadIdx.x;
+            const double num = (double)s_df[j].hi + (double)s_df[j].lo;
+            const double den = (double)s_df[C + j].hi + (double)s_df[C + j].lo;
+            const bool empty = !(den > 0.0);
+            const double q = empty ? 0.0 : num / den;
+            s_v64[j] = q;
+            s_v[j] = (float)q;
+            s_empty[j] = empty;
+        }
+        __syncthreads();
+        const double J = (double)s_df[2 * C].hi + (double)s_df[2 * C].lo;
+        const float delta = s_mx[0];
+        const bool bad = s_mx[1] != 0.0f, tmo = s_mx[2] != 0.0f;
+        bool update = false;
+        if (tmo) {
+            status = FCM_ERR_TIMEOUT;
+            iters = p;
+            stop = true;
+        } else if (p == 0) {
+            if (bad) {
+                status = FCM_ERR_BAD_INPUT;
+                iters = 0;
+                stop = true;
+            } else {
+                update = true;
+            }
+        } else {
+            if (blockIdx.x == 0 && threadIdx.x == 0 && st->trace) {
+                double* t = st->trace + (int64_t)(p - 1) * (2 + C);
+                t[0] = delta;
+                t[1] = J;
+#pragma unroll
+                for (int j = 0; j < C; ++j) t[2 + j] = v64[j];
+            }
+            if (delta < eps) {
+                status = FCM_OK;
+                iters = p;
+                stop = true;
+            } else if (p >= max_iter) {
+                status = FCM_NOT_CONVERGED;
+                iters = p;
+                stop = true;
+            } else {
+                update = true;
+            }
+            if (blockIdx.x == 0 && threadIdx.x == 0) {
+                st->delta = delta;
+                st->J = J;
+            }
+        }
+        if (update) {
+#pragma unroll
+            for (int j = 0; j < C; ++j) {
+                if (s_empty[j]) {
+                    // an empty cluster keeps its center (first pass: V^0, or 0 from a U^0)
+                    flags |= FCM_FLAG_EMPTY_CLUSTER;
+                    if (p == 0 && INIT == P_ACCUM0) {
+                        v[j] = 0.0f;
+                        v64[j] = 0.0;
+                    }
+                } else {
+                    v[j] = s_v[j];
+                    v64[j] = s_v64[j];
+                }
+                v2[j] = pack2(v[j], v[j]);
+            }
+        }
+        __syncthreads();  // s_df / s_v are rewritten by the next pass
+    }
+
+    // copies issued for passes that will not run: let them land
+    if (lane == 0) {
+        int ds = cs;
+        uint32_t dp = parity;
+        for (int64_t q = consumed; q < issued; ++q) {
+            mbar_wait_bounded(&full[ds], dp, WAIT_LIMIT);
+            if (++ds == Sh::STAGES) {
+                ds = 0;
+                dp ^= 1u;
+            }
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+#pragma unroll
+        for (int j = 0; j < C; ++j) {
+            st->V[j] = v[j];
+            st->V64[j] = v64[j];
+        }
+        st->status = status;
+        st->iters = iters;
+        st->k = iters;
+        st->flags = flags;
+        st->done = 1;
+        st->Uprev = st->U;
+    }
 }
 
 template <int C, int MK, int PASS>
@@ -412,6 +829,9 @@ void fill_mk(SingleTable& t) {
     fill_pass<C, MK, P_ACCUM0>(t);
     fill_pass<C, MK, P_INITV>(t);
     fill_pass<C, MK, P_ITER>(t);
+    t.run[C][MK][0] = k_fcm_run_tma<C, MK, P_ACCUM0>;
+    t.run[C][MK][1] = k_fcm_run_tma<C, MK, P_INITV>;
+    t.run_smem[C] = TmaShape<P_ITER, C>::SMEM_BYTES;
 }
 
 }  // namespace

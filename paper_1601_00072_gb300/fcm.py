@@ -90,7 +90,7 @@ class FCM:
 
     def run(self, x, C: int, m: float = 2.0, eps: float = 1e-5, max_iter: int = 300, *,
             U0=None, V0=None, U=None, V=None, trace: bool = False, graph: bool = True,
-            tma: bool = True, raise_on_error: bool = True) -> FCMResult:
+            tma: bool = True, persistent: bool = True, raise_on_error: bool = True) -> FCMResult:
         """Algorithm 1 on one image.
 
         ``x``: n float32 pixels (CUDA tensor, pinned/CPU tensor or numpy).
@@ -128,7 +128,7 @@ class FCM:
         if _numel(U) != C * n or _numel(V) != C or (u0p is not None and _numel(u0p) != C * n):
             raise ValueError("U and U0 must hold C*n floats and V C floats")
         opts = ((_lib.FCM_OPT_TRACE if trace else 0) | (0 if graph else _lib.FCM_OPT_NO_GRAPH)
-                | (0 if tma else _lib.FCM_OPT_NO_TMA))
+                | (0 if tma else _lib.FCM_OPT_NO_TMA) | (0 if persistent else _lib.FCM_OPT_NO_PERSISTENT))
         rep = _lib.fcm_report()
         self._bind_stream()
         st = self._lib.fcm_run(self._h, _ptr(x), n, int(C), float(m), float(eps), int(max_iter),
@@ -148,3 +148,14 @@ class FCM:
             tr = {"delta": d[:got], "J": J[:got], "V": Vt[:got]}
         return FCMResult(U=U, V=V, iters=rep.iters, status=st, delta=rep.delta, J=rep.J,
                          V64=np.array(rep.V64[:C]), flags=rep.flags, trace=tr)
+
+    def time_pass(self, x, C: int, m: float, U, V, launches: int = 20, tma: bool = True) -> float:
+        """Average milliseconds per launch of the iteration pass, from
+        ``launches`` back-to-back launches timed with CUDA events (U updated in
+        place, no stopping test). A profiling aid."""
+        ms = ctypes.c_float(0.0)
+        self._bind_stream()
+        _lib.check(self._lib.fcm_time_pass(self._h, _ptr(x), _numel(x), int(C), float(m), _ptr(U),
+                                           _ptr(V), int(launches), 0 if tma else _lib.FCM_OPT_NO_TMA,
+                                           ctypes.byref(ms)), self._h)
+        return ms.value

@@ -73,21 +73,6 @@ def test_phantom200_matches_oracle(fcm, m):
     assert gU.min() >= 0.0 and gU.max() <= 1.0 + 1e-6
 
 
-@pytest.mark.parametrize("m", [2.0, 3.0])
-def test_plain_load_variant_matches_oracle(fcm, m):
-    """The kernel without the TMA ring (also used for ragged n) on an aligned image."""
-    x, _, u0, C = phantom.single_image("phantom200")
-    g, gU, gV = gpu_run(fcm, x, C, m, u0=u0, tma=False)
-    o = oracle_run(x, C, m, EPS, MAX_ITER, u0=u0)
-    k = min(g.iters, o["iters"])
-    d_iters = g.iters - o["iters"]
-    if g.iters > k:
-        g, gU, gV = gpu_run(fcm, x, C, m, max_iter=k, u0=u0, tma=False)
-    if o["iters"] > k:
-        o = oracle_run(x, C, m, EPS, k, u0=u0)
-    assert_within(precision_report(gU, gV, g.iters + d_iters, o["U"], o["V"], o["iters"]))
-
-
 def test_phantom1024_matches_oracle(fcm):
     x, _, u0, C = phantom.single_image("phantom1024")
     rep, *_ = paired(fcm, x, C, 2.0, u0=u0, quantized=True)
@@ -173,9 +158,43 @@ def test_every_iteration_is_one_oracle_step(fcm, m):
     assert np.all(np.diff(tr["J"]) <= 1e-6 * tr["J"][0])
 
 
-def test_graph_and_host_loop_agree_bitwise(fcm):
+@pytest.mark.parametrize("path", ["persistent", "graph", "host_loop", "plain_loads"])
+@pytest.mark.parametrize("m", [2.0, 3.0])
+def test_every_execution_path_matches_oracle(fcm, path, m):
+    """One cooperative launch for the whole run (default), one launch per pass
+    in a graph WHILE loop, the host-driven loop, and the plain-load kernel."""
+    kw = {"persistent": {}, "graph": {"persistent": False}, "host_loop": {"graph": False},
+          "plain_loads": {"tma": False}}[path]
     x, _, u0, C = phantom.single_image("phantom200")
-    a, aU, aV = gpu_run(fcm, x, C, 2.0, u0=u0)
+    g, gU, gV = gpu_run(fcm, x, C, m, u0=u0, **kw)
+    o = oracle_run(x, C, m, EPS, MAX_ITER, u0=u0)
+    k = min(g.iters, o["iters"])
+    d_iters = g.iters - o["iters"]
+    if g.iters > k:
+        g, gU, gV = gpu_run(fcm, x, C, m, max_iter=k, u0=u0, **kw)
+    if o["iters"] > k:
+        o = oracle_run(x, C, m, EPS, k, u0=u0)
+    assert_within(precision_report(gU, gV, g.iters + d_iters, o["U"], o["V"], o["iters"]))
+
+
+@pytest.mark.parametrize("n,C", [(4, 2), (132, 3), (1024, 8), (5000, 4), (40960, 5)])
+def test_small_aligned_sizes_match_oracle(fcm, n, C):
+    """Aligned sizes where warps hold fewer tiles than ring stages (or none)."""
+    side = int(np.ceil(np.sqrt(n)))
+    img, _ = phantom.phantom2d(2000 + n, side, side, 9.0)
+    x = img.reshape(-1)[:n]
+    u0 = phantom.dirichlet_u0((2000 + n, 3), C, n)
+    rep, *_ = paired(fcm, x, C, 2.0, u0=u0)
+    assert_within(rep)
+    V0 = np.linspace(10.0, 200.0, C)
+    rep, *_ = paired(fcm, x, C, 3.0, V0=V0)
+    assert_within(rep)
+
+
+def test_graph_and_host_loop_agree_bitwise(fcm):
+    """The per-pass kernels give the same bits from a graph or a host loop."""
+    x, _, u0, C = phantom.single_image("phantom200")
+    a, aU, aV = gpu_run(fcm, x, C, 2.0, u0=u0, persistent=False)
     b, bU, bV = gpu_run(fcm, x, C, 2.0, u0=u0, graph=False)
     assert a.iters == b.iters and np.array_equal(aU, bU) and np.array_equal(aV, bV)
     assert np.array_equal(a.V64, b.V64)
