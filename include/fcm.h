@@ -59,6 +59,7 @@ extern "C" {
 #define FCM_ERR_OOM (-3)         /* workspace allocation failed              */
 #define FCM_ERR_BAD_INPUT (-4)   /* NaN/Inf in x or V0, or NaN/Inf/negative U0 */
 #define FCM_ERR_TIMEOUT (-5)     /* a bounded device-side wait gave up       */
+#define FCM_ERR_TOO_LARGE (-6)   /* beyond a fixed limit of fcm_run_noalloc  */
 
 /* Report flags. */
 #define FCM_FLAG_EMPTY_CLUSTER 1 /* some sum_i u_ij^m underflowed to 0: v_j kept */
@@ -145,6 +146,45 @@ int fcm_run(fcm_handle h, const float* x, int64_t n, int C, float m,
  */
 int fcm_time_pass(fcm_handle h, const float* x, int64_t n, int C, float m, float* U,
                   const float* V, int launches, int options, float* ms_per_launch);
+
+/*
+ * fcm_run_noalloc — the same run as fcm_run for aligned inputs, for callers
+ * that must not allocate memory while they run. The paper has no counterpart;
+ * this is a deployment variant of the library's own whole-run kernel.
+ *
+ * Some callers cannot call cudaMalloc: code whose device memory is owned by a
+ * pool or framework allocator it may not bypass, plugins that receive only
+ * pre-allocated buffers, and latency-critical services where an allocation
+ * (which may synchronise the device or fail under memory pressure) is not
+ * acceptable. fcm_run keeps its scratch in a handle that allocates on first
+ * use; this entry point needs no handle and allocates nothing (no cudaMalloc,
+ * cudaFree or allocating library call). Its scratch — the device-side run
+ * state and the per-block partial sums — lives in one fixed array inside the
+ * library image (about 80 KB plus the state) that every GPU which loads the
+ * library holds until the process exits.
+ *
+ *   x, n, C, m, eps, max_iter, init_mode, U0, U, V: as for fcm_run, except
+ *             that x, U and U0 must be device memory, 16-byte aligned, and
+ *             n % 4 == 0 (host memory cannot be staged without allocating).
+ *             V may be device or host memory.
+ *   cuda_stream  the cudaStream_t to run on (NULL = legacy default stream),
+ *             on the current device. The call synchronises that stream.
+ *   rep       nullable; filled on return.
+ *
+ * Limit: the scratch holds partial sums for at most FCM_NOALLOC_MAX_BLOCKS
+ * thread blocks; a device that would need more (more SMs than any current
+ * GPU) gets FCM_ERR_TOO_LARGE. Other bad arguments give FCM_ERR_INVALID_ARG.
+ *
+ * The first call on each device looks up the scratch address and the kernels'
+ * launch limits on that device; make that first call before capturing any
+ * stream into a CUDA graph. Every call shares the one scratch array and
+ * resets it as needed, so calls must not overlap on the GPU: calls from
+ * several host threads, or on streams not ordered with one another, race.
+ */
+#define FCM_NOALLOC_MAX_BLOCKS 512
+int fcm_run_noalloc(const float* x, int64_t n, int C, float m, float eps, int max_iter,
+                    int init_mode, const float* U0, float* U, float* V, void* cuda_stream,
+                    fcm_report* rep);
 
 /* Copy the trace of the last run made with FCM_OPT_TRACE into host arrays
  * (each nullable): delta[k-1], J[k-1] and V[(k-1)*C + j] for k = 1..iters.

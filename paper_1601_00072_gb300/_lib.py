@@ -18,6 +18,8 @@ FCM_ERR_CUDA = -2
 FCM_ERR_OOM = -3
 FCM_ERR_BAD_INPUT = -4
 FCM_ERR_TIMEOUT = -5
+FCM_ERR_TOO_LARGE = -6
+FCM_NOALLOC_MAX_BLOCKS = 512
 FCM_FLAG_EMPTY_CLUSTER = 1
 FCM_INIT_U = 0
 FCM_INIT_V = 1
@@ -46,6 +48,8 @@ SIGNATURES = [
     ("fcm_destroy", None, [_vp]),
     ("fcm_run", _i, [_vp, _vp, _i64, _i, _f, _f, _i, _i, _vp, _vp, _vp, _i,
                      ctypes.POINTER(fcm_report)]),
+    ("fcm_run_noalloc", _i, [_vp, _i64, _i, _f, _f, _i, _i, _vp, _vp, _vp, _vp,
+                             ctypes.POINTER(fcm_report)]),
     ("fcm_time_pass", _i, [_vp, _vp, _i64, _i, _f, _vp, _vp, _i, _i, ctypes.POINTER(_f)]),
     ("fcm_get_trace", _i, [_vp, _dp, _dp, _dp, _i]),
     ("fcm_last_error", ctypes.c_char_p, [_vp]),

@@ -60,6 +60,11 @@ bool is_device_pointer(const void* p) {
 
 namespace fcm {
 
+const SingleTable& single_table() {
+    std::call_once(g_table_once, init_table);
+    return g_table;
+}
+
 int ctx_fail(fcm_ctx* h, cudaError_t e, const char* what) {
     if (h) {
         char buf[256];
@@ -310,6 +315,7 @@ const char* fcm_status_string(int s) {
         case FCM_ERR_OOM: return "FCM_ERR_OOM";
         case FCM_ERR_BAD_INPUT: return "FCM_ERR_BAD_INPUT";
         case FCM_ERR_TIMEOUT: return "FCM_ERR_TIMEOUT";
+        case FCM_ERR_TOO_LARGE: return "FCM_ERR_TOO_LARGE";
         default: return "FCM_UNKNOWN_STATUS";
     }
 }

@@ -69,6 +69,9 @@ struct SingleTable {
     int run_smem[FCM_MAX_CLUSTERS + 1];
 };
 
+// The kernel table, filled on first use.
+const SingleTable& single_table();
+
 void register_single_c1(SingleTable&);
 void register_single_c2(SingleTable&);
 void register_single_c3(SingleTable&);
