@@ -45,6 +45,7 @@ UNIT = "pixel-iter/s"
 PROFILE = os.path.join(ROOT, "profiles", "fcm_pass_volume256.md")
 KERNEL_SOURCES = ["paper_1601_00072_gb300/csrc/fcm_single_inst.cu",
                   "paper_1601_00072_gb300/csrc/fcm_device.cuh",
+                  "paper_1601_00072_gb300/csrc/fcm_tma.cuh",
                   "paper_1601_00072_gb300/csrc/fcm_internal.h"]
 
 
@@ -73,7 +74,7 @@ def profiled_traffic():
     except OSError:
         return None
     mh = re.search(r"kernel source hash:\s*`?([0-9a-f]{16})", text)
-    mt = re.search(r"dram bytes per launch \(scaled to volume256\):\s*([0-9.eE+]+)", text)
+    mt = re.search(r"dram bytes per launch:\s*([0-9.eE+]+)", text)
     if not mh or not mt or mh.group(1) != kernel_hash():
         return None
     return float(mt.group(1))
@@ -264,9 +265,11 @@ def bench_ours(args):
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     iters = []
+    launches = 0
     for _ in range(args.steps):
         r = step()
         iters.append(r.iters)
+        launches += r.launches
     e1.record(stream)
     torch.cuda.synchronize(dev)
     barrier(world)
@@ -280,7 +283,6 @@ def bench_ours(args):
     # roofline of the pass kernels over the timed region (algorithmic bytes:
     # pass 0 reads x and U^0; each iteration reads x and U^{k-1}, writes U^k)
     bytes_local = sum((4 * n + 4 * C * n) + it * (4 * n + 8 * C * n) for it in iters)
-    launches = sum(1 + it for it in iters)
     achieved = bytes_local / (ms_local / 1e3) / 1e9
     peak, peak_kind = measured_peak()
     traffic = profiled_traffic()
@@ -330,8 +332,12 @@ def bench_ours(args):
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
                      "peak_source": f"{peak_kind} copy bandwidth",
-                     "kernel": "k_fcm_pass (all passes of the step, algorithmic bytes "
-                               "36 B/pixel-iteration at C=4)"},
+                     "kernel": ("k_fcm_run_tma: one cooperative launch per step (pass 0 reads "
+                                "x and U0, 20 B/pixel; each iteration 36 B/pixel at C=4)"
+                                if r.launches == 1 else
+                                "k_fcm_pass_*: one launch per pass (pass 0 20 B/pixel, "
+                                "each iteration 36 B/pixel at C=4)"),
+                     "algorithmic_bytes_per_step": bytes_local / args.steps},
         "clocks": clocks,
         "e2e": e2e,
     }

@@ -87,6 +87,8 @@ typedef struct {
     double delta;   /* delta_k of the last iteration (L-infinity)            */
     double J;       /* J_m(U^k, V^k), Eq. 1                                  */
     double V64[FCM_MAX_CLUSTERS];
+    int launches;   /* kernel launches the run used                          */
+    int reserved;
 } fcm_report;
 
 /* Create a handle on CUDA device `device`, issuing work on `cuda_stream`

@@ -32,7 +32,8 @@ FCM_OPT_NO_PERSISTENT = 8
 class fcm_report(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int), ("status", ctypes.c_int), ("flags", ctypes.c_int),
                 ("C", ctypes.c_int), ("delta", ctypes.c_double), ("J", ctypes.c_double),
-                ("V64", ctypes.c_double * FCM_MAX_CLUSTERS)]
+                ("V64", ctypes.c_double * FCM_MAX_CLUSTERS), ("launches", ctypes.c_int),
+                ("reserved", ctypes.c_int)]
 
 
 _vp = ctypes.c_void_p

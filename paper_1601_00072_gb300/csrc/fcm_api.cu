@@ -239,6 +239,7 @@ int run_host_loop(fcm_ctx* h, PassFn kfirst, int smem_first, PassFn kiter, int s
             kiter<<<nblocks, NT, smem_iter, h->stream>>>(h->d_st, h->d_partials, none, 0);
         CK(cudaGetLastError());
         launched += todo;
+        h->last_launches = 1 + launched;
         CK(cudaMemcpyAsync(done_host, &h->d_st->done, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
         CK(cudaStreamSynchronize(h->stream));
         if (*done_host || launched >= max_iter) break;
@@ -449,6 +450,7 @@ int fcm_run(fcm_handle h, const float* x, int64_t n, int C, float m, float eps, 
         rep->delta = hs->delta;
         rep->J = hs->J;
         for (int j = 0; j < C; ++j) rep->V64[j] = hs->V64[j];
+        rep->launches = h->last_path == 2 ? 1 : h->last_path == 1 ? 1 + hs->iters : h->last_launches;
     }
     if (hs->status == STATUS_RUNNING) {
         h->last_error = "run ended without a status";

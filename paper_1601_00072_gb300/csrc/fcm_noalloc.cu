@@ -179,6 +179,7 @@ extern "C" int fcm_run_noalloc(const float* x, int64_t n, int C, float m, float 
         rep->delta = out.delta;
         rep->J = out.J;
         for (int j = 0; j < C; ++j) rep->V64[j] = out.V64[j];
+        rep->launches = 1;
     }
     return out.status == STATUS_RUNNING ? FCM_ERR_CUDA : out.status;
 }

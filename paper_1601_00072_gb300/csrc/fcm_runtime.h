@@ -36,6 +36,7 @@ struct fcm_ctx {
     bool coop = false;        // cooperative launch supported
     int last_blocks = 0;      // grid of the last run
     int last_path = 0;        // 0 host loop, 1 graph WHILE loop, 2 one cooperative launch
+    int last_launches = 0;    // kernel launches of the last host-loop run
     int max_smem_optin = 0;
     std::string device_name;
     std::string last_error;

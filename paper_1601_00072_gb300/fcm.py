@@ -42,6 +42,7 @@ class FCMResult:
     J: float
     V64: np.ndarray
     flags: int
+    launches: int = 0
     trace: dict | None = field(default=None)
 
     @property
@@ -147,7 +148,7 @@ class FCM:
             _lib.check(got, self._h)
             tr = {"delta": d[:got], "J": J[:got], "V": Vt[:got]}
         return FCMResult(U=U, V=V, iters=rep.iters, status=st, delta=rep.delta, J=rep.J,
-                         V64=np.array(rep.V64[:C]), flags=rep.flags, trace=tr)
+                         V64=np.array(rep.V64[:C]), flags=rep.flags, launches=rep.launches, trace=tr)
 
     def time_pass(self, x, C: int, m: float, U, V, launches: int = 20, tma: bool = True) -> float:
         """Average milliseconds per launch of the iteration pass, from
