@@ -138,6 +138,86 @@ int fcm_run(fcm_handle h, const float* x, int64_t n, int C, float m,
             float* V, int options, fcm_report* rep);
 
 /*
+ * Batched runs: many independent images ("slices") of different sizes, cluster
+ * counts and fuzzifiers in one persistent launch (not in the paper, which
+ * segments one image at a time; each slice follows Algorithm 1 exactly as
+ * fcm_run does).
+ *
+ * fcm_slice — one slice. Pointers are device memory.
+ *   x         n floats, 16-byte aligned.
+ *   n, C, m, eps, max_iter   as for fcm_run.
+ *   init_mode FCM_INIT_U (U^0 in U0, or in U when U0 is NULL) or FCM_INIT_V
+ *             (initial centers in V0[], host values inside the struct).
+ *   U0        C*n floats, cluster-major, read only; nullable.
+ *   U         C*n floats, cluster-major: receives U^k.
+ *   V         C floats: receives V^k.
+ *   iters, status, flags, delta, J, V64: outputs, written on return.
+ */
+typedef struct {
+    const float* x;
+    int64_t n;
+    int C;
+    float m;
+    float eps;
+    int max_iter;
+    int init_mode;
+    int reserved0;
+    const float* U0;
+    float* U;
+    float* V;
+    float V0[FCM_MAX_CLUSTERS];
+    int iters;
+    int status;
+    int flags;
+    int reserved1;
+    double delta;
+    double J;
+    double V64[FCM_MAX_CLUSTERS];
+} fcm_slice;
+
+/* Launch shape of the batched kernel (see fcm_run_batched). */
+typedef struct {
+    int block;      /* threads per CTA: 256 or 512                           */
+    int cluster;    /* CTAs per thread-block cluster: 1, 2, 4 or 8            */
+    int64_t big;    /* slices with n >= big are shared by a whole cluster     */
+    double ms;      /* measured batch time when the autotuner chose it, or 0  */
+} fcm_batch_plan;
+
+/* Batch options (bit flags). */
+#define FCM_BATCH_RETUNE 16  /* run the autotuner even if a plan is cached        */
+#define FCM_BATCH_NO_TUNE 32 /* use the cached or default plan, never tune        */
+#define FCM_BATCH_NO_GRAPH 64 /* launch directly instead of replaying a CUDA graph */
+
+/*
+ * fcm_run_batched — Algorithm 1 on each of n_slices slices, in one persistent
+ * launch captured in a CUDA graph. Slices are taken from a work queue in
+ * order of decreasing size; slices with n >= plan.big are shared by the CTAs
+ * of a thread-block cluster (per-iteration sums exchanged through distributed
+ * shared memory), smaller ones run one per CTA. Memberships U^{k-1} are
+ * recomputed from V^{k-1} rather than stored, so each iteration reads only x.
+ *
+ * The launch shape comes from an autotuner: on the first batch of a new
+ * "bucket" (device, set of C values, and the powers of two of the slice
+ * count, total pixels and largest slice), it times each candidate shape on
+ * the batch itself and keeps the fastest, in memory and, when the environment
+ * variable FCM_AUTOTUNE_CACHE names a file, in that JSON file. Tuning runs the
+ * batch several times, so it is skipped (default plan) when a slice updates
+ * its initial memberships in place (FCM_INIT_U with U0 NULL or equal to U).
+ *
+ * Returns FCM_OK if every slice converged, FCM_NOT_CONVERGED if some slice
+ * stopped at max_iter, the first negative status of a failed slice, or an
+ * error of the whole call (FCM_ERR_INVALID_ARG names no slice then). Per-slice
+ * results are in the structs.
+ */
+int fcm_run_batched(fcm_handle h, fcm_slice* slices, int n_slices, int options);
+
+/* The plan the last batched run used. */
+int fcm_batched_plan(fcm_handle h, fcm_batch_plan* plan);
+
+/* Force a plan for later batched runs (NULL returns to the autotuner). */
+int fcm_batched_set_plan(fcm_handle h, const fcm_batch_plan* plan);
+
+/*
  * fcm_time_pass — profiling aid: time `launches` back-to-back launches of the
  * iteration pass (one Algorithm 1 iteration each: Eq. 4, Eq. 1, Eq. 3) on the
  * handle's stream with CUDA events, starting from centers V (device or host,

@@ -2,7 +2,8 @@
 
 Every translation unit is compiled by its own ``nvcc -c`` process, in
 parallel, then linked with ``nvcc -shared``. The single-image pass source is
-compiled eight times, once per cluster count (``-DFCM_INST_C=1..8``).
+compiled eight times, once per cluster count (``-DFCM_INST_C=1..8``), and the
+batched kernel twice, once per block size (``-DFCM_BATCH_NT=256, 512``).
 Nothing is rebuilt when the library is newer than every source.
 """
 from __future__ import annotations
@@ -39,6 +40,9 @@ def _units():
         if base == "fcm_single_inst":
             for c in range(1, 9):
                 units.append((src, os.path.join(BUILD, f"{base}_c{c}.o"), [f"-DFCM_INST_C={c}"]))
+        elif base == "fcm_batched_inst":
+            for nt in (256, 512):
+                units.append((src, os.path.join(BUILD, f"{base}_nt{nt}.o"), [f"-DFCM_BATCH_NT={nt}"]))
         else:
             units.append((src, os.path.join(BUILD, base + ".o"), []))
     return units

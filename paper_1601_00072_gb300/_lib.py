@@ -36,6 +36,26 @@ class fcm_report(ctypes.Structure):
                 ("reserved", ctypes.c_int)]
 
 
+class fcm_slice(ctypes.Structure):
+    _fields_ = [("x", ctypes.c_void_p), ("n", ctypes.c_int64), ("C", ctypes.c_int),
+                ("m", ctypes.c_float), ("eps", ctypes.c_float), ("max_iter", ctypes.c_int),
+                ("init_mode", ctypes.c_int), ("reserved0", ctypes.c_int),
+                ("U0", ctypes.c_void_p), ("U", ctypes.c_void_p), ("V", ctypes.c_void_p),
+                ("V0", ctypes.c_float * FCM_MAX_CLUSTERS),
+                ("iters", ctypes.c_int), ("status", ctypes.c_int), ("flags", ctypes.c_int),
+                ("reserved1", ctypes.c_int), ("delta", ctypes.c_double), ("J", ctypes.c_double),
+                ("V64", ctypes.c_double * FCM_MAX_CLUSTERS)]
+
+
+class fcm_batch_plan(ctypes.Structure):
+    _fields_ = [("block", ctypes.c_int), ("cluster", ctypes.c_int), ("big", ctypes.c_int64),
+                ("ms", ctypes.c_double)]
+
+
+FCM_BATCH_RETUNE = 16
+FCM_BATCH_NO_TUNE = 32
+FCM_BATCH_NO_GRAPH = 64
+
 _vp = ctypes.c_void_p
 _i = ctypes.c_int
 _f = ctypes.c_float
@@ -49,6 +69,9 @@ SIGNATURES = [
     ("fcm_destroy", None, [_vp]),
     ("fcm_run", _i, [_vp, _vp, _i64, _i, _f, _f, _i, _i, _vp, _vp, _vp, _i,
                      ctypes.POINTER(fcm_report)]),
+    ("fcm_run_batched", _i, [_vp, ctypes.POINTER(fcm_slice), _i, _i]),
+    ("fcm_batched_plan", _i, [_vp, ctypes.POINTER(fcm_batch_plan)]),
+    ("fcm_batched_set_plan", _i, [_vp, ctypes.POINTER(fcm_batch_plan)]),
     ("fcm_run_noalloc", _i, [_vp, _i64, _i, _f, _f, _i, _i, _vp, _vp, _vp, _vp,
                              ctypes.POINTER(fcm_report)]),
     ("fcm_time_pass", _i, [_vp, _vp, _i64, _i, _f, _vp, _vp, _i, _i, ctypes.POINTER(_f)]),

@@ -103,18 +103,6 @@ int ctx_grow(fcm_ctx* h, void** p, size_t* cap, size_t bytes, const char* what) 
 
 namespace {
 
-struct DeviceGuard {
-    int prev = -1;
-    explicit DeviceGuard(int dev) {
-        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
-        if (prev != dev) cudaSetDevice(dev);
-    }
-    ~DeviceGuard() {
-        int cur;
-        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
-    }
-};
-
 int ensure_single_workspace(fcm_ctx* h) {
     if (h->d_st) return 0;
     CK(cudaMalloc(&h->d_st, sizeof(RunState)));

@@ -1,4 +1,470 @@
-// Batched FCM over many independent slices (filled in by the batched path).
+// Host runtime of the batched FCM path: argument checks, LPT work order,
+// launch-shape autotuner with its cache, and the CUDA graph of a batch.
+//
+// A batch is one persistent kernel launch. Its graph holds, in order: the
+// upload of the slice descriptors and of the work order (from pinned host
+// buffers the handle refills before each launch), the reset of the work-queue
+// head, the kernel (a thread-block-cluster launch), and the download of the
+// per-slice results. The graph is instantiated once per (slice count, plan).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <numeric>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "fcm.h"
+#include "fcm_batched.h"
+#include "fcm_device.cuh"
 #include "fcm_runtime.h"
 
-void fcm_release_batched(fcm_ctx* h) { (void)h; }
+using namespace fcm;
+
+namespace fcm {
+
+struct BatchedWorkspace {
+    int cap = 0;
+    SliceDesc* d_desc = nullptr;
+    SliceResult* d_res = nullptr;
+    int* d_order = nullptr;
+    BatchCtl* d_ctl = nullptr;
+    SliceDesc* h_desc = nullptr;   // pinned
+    SliceResult* h_res = nullptr;  // pinned
+    int* h_order = nullptr;        // pinned
+    cudaStream_t cap_stream = nullptr;
+    std::map<std::tuple<int, int, int, int64_t>, GraphEntry> graphs;
+    std::map<std::string, fcm_batch_plan> plans;
+    bool cache_loaded = false;
+    bool forced = false;
+    fcm_batch_plan forced_plan{};
+    fcm_batch_plan last{};
+    std::map<std::pair<int, int>, int> grid;  // (block, cluster) -> CTAs of a full persistent grid
+};
+
+}  // namespace fcm
+
+#define CK(call)                                              \
+    do {                                                      \
+        cudaError_t e_ = (call);                              \
+        if (e_ != cudaSuccess) return ctx_fail(h, e_, #call); \
+    } while (0)
+
+namespace {
+
+BatchKernel kernel_for(int block) { return block == 256 ? batched_kernel_256() : batched_kernel_512(); }
+
+void free_graphs(BatchedWorkspace* w) {
+    for (auto& kv : w->graphs) {
+        if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+        if (kv.second.graph) cudaGraphDestroy(kv.second.graph);
+    }
+    w->graphs.clear();
+}
+
+int ensure_batched(fcm_ctx* h, int n) {
+    if (!h->batched) h->batched = new BatchedWorkspace();
+    BatchedWorkspace* w = h->batched;
+    if (!w->cap_stream) CK(cudaStreamCreateWithFlags(&w->cap_stream, cudaStreamNonBlocking));
+    if (!w->d_ctl) CK(cudaMalloc(&w->d_ctl, sizeof(BatchCtl)));
+    if (w->cap >= n) return 0;
+    free_graphs(w);  // graphs point at the old buffers
+    cudaFree(w->d_desc);
+    cudaFree(w->d_res);
+    cudaFree(w->d_order);
+    cudaFreeHost(w->h_desc);
+    cudaFreeHost(w->h_res);
+    cudaFreeHost(w->h_order);
+    w->d_desc = nullptr;
+    w->d_res = nullptr;
+    w->d_order = nullptr;
+    w->h_desc = nullptr;
+    w->h_res = nullptr;
+    w->h_order = nullptr;
+    w->cap = 0;
+    const int cap = std::max(n, 64);
+    CK(cudaMalloc(&w->d_desc, sizeof(SliceDesc) * cap));
+    CK(cudaMalloc(&w->d_res, sizeof(SliceResult) * cap));
+    CK(cudaMalloc(&w->d_order, sizeof(int) * cap));
+    CK(cudaMallocHost(&w->h_desc, sizeof(SliceDesc) * cap));
+    CK(cudaMallocHost(&w->h_res, sizeof(SliceResult) * cap));
+    CK(cudaMallocHost(&w->h_order, sizeof(int) * cap));
+    w->cap = cap;
+    return 0;
+}
+
+// CTAs of a full persistent grid for this shape (0 if it cannot run).
+int grid_ctas(fcm_ctx* h, int block, int cluster) {
+    BatchedWorkspace* w = h->batched;
+    auto it = w->grid.find({block, cluster});
+    if (it != w->grid.end()) return it->second;
+    const BatchKernel k = kernel_for(block);
+    int ctas = 0;
+    if (cudaFuncSetAttribute((const void*)k.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, k.smem) ==
+        cudaSuccess) {
+        if (cluster == 1) {
+            int nb = 0;
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, (const void*)k.fn, block, k.smem) == cudaSuccess)
+                ctas = nb * h->num_sms;
+        } else {
+            cudaLaunchConfig_t cfg;
+            std::memset(&cfg, 0, sizeof(cfg));
+            cudaLaunchAttribute attr[1];
+            attr[0].id = cudaLaunchAttributeClusterDimension;
+            attr[0].val.clusterDim.x = cluster;
+            attr[0].val.clusterDim.y = 1;
+            attr[0].val.clusterDim.z = 1;
+            cfg.gridDim = dim3(cluster * h->num_sms);
+            cfg.blockDim = dim3(block);
+            cfg.dynamicSmemBytes = k.smem;
+            cfg.attrs = attr;
+            cfg.numAttrs = 1;
+            int nc = 0;
+            if (cudaOccupancyMaxActiveClusters(&nc, (const void*)k.fn, &cfg) == cudaSuccess) ctas = nc * cluster;
+        }
+    }
+    cudaGetLastError();
+    w->grid[{block, cluster}] = ctas;
+    return ctas;
+}
+
+int launch_kernel(fcm_ctx* h, cudaStream_t s, const fcm_batch_plan& p, int n_slices) {
+    BatchedWorkspace* w = h->batched;
+    const BatchKernel k = kernel_for(p.block);
+    const int ctas = grid_ctas(h, p.block, p.cluster);
+    if (ctas < p.cluster) {
+        h->last_error = "batched launch shape does not fit on this device";
+        return FCM_ERR_CUDA;
+    }
+    cudaLaunchConfig_t cfg;
+    std::memset(&cfg, 0, sizeof(cfg));
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = p.cluster;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(ctas);
+    cfg.blockDim = dim3(p.block);
+    cfg.dynamicSmemBytes = k.smem;
+    cfg.stream = s;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    CK(cudaMemsetAsync(w->d_ctl, 0, sizeof(BatchCtl), s));
+    const SliceDesc* d = w->d_desc;
+    const int* o = w->d_order;
+    SliceResult* r = w->d_res;
+    BatchCtl* c = w->d_ctl;
+    int64_t big = p.big;
+    CK(cudaLaunchKernelEx(&cfg, k.fn, d, o, n_slices, r, c, big));
+    return 0;
+}
+
+// ---- autotune cache ------------------------------------------------------
+
+std::string cache_path() {
+    const char* p = std::getenv("FCM_AUTOTUNE_CACHE");
+    return p ? std::string(p) : std::string();
+}
+
+void load_cache(BatchedWorkspace* w) {
+    w->cache_loaded = true;
+    const std::string path = cache_path();
+    if (path.empty()) return;
+    FILE* f = std::fopen(path.c_str(), "r");
+    if (!f) return;
+    // One entry per line: "<key>": {"block": B, "cluster": K, "big": G, "ms": T},
+    char line[1024];
+    while (std::fgets(line, sizeof(line), f)) {
+        char key[512];
+        int block = 0, cluster = 0;
+        long long big = 0;
+        double ms = 0;
+        if (std::sscanf(line, " \"%511[^\"]\": {\"block\": %d, \"cluster\": %d, \"big\": %lld, \"ms\": %lf",
+                        key, &block, &cluster, &big, &ms) == 5 &&
+            (block == 256 || block == 512) && (cluster == 1 || cluster == 2 || cluster == 4 || cluster == 8))
+            w->plans[key] = fcm_batch_plan{block, cluster, (int64_t)big, ms};
+    }
+    std::fclose(f);
+}
+
+void save_cache(BatchedWorkspace* w) {
+    const std::string path = cache_path();
+    if (path.empty()) return;
+    const std::string tmp = path + ".tmp";
+    FILE* f = std::fopen(tmp.c_str(), "w");
+    if (!f) return;
+    std::fprintf(f, "{\n");
+    size_t i = 0;
+    for (auto& kv : w->plans) {
+        std::fprintf(f, "  \"%s\": {\"block\": %d, \"cluster\": %d, \"big\": %lld, \"ms\": %.4f}%s\n",
+                     kv.first.c_str(), kv.second.block, kv.second.cluster, (long long)kv.second.big,
+                     kv.second.ms, ++i < w->plans.size() ? "," : "");
+    }
+    std::fprintf(f, "}\n");
+    std::fclose(f);
+    std::rename(tmp.c_str(), path.c_str());
+}
+
+int ilog2(int64_t v) {
+    int l = 0;
+    while (v > 1) {
+        v >>= 1;
+        ++l;
+    }
+    return l;
+}
+
+std::string bucket_key(fcm_ctx* h, const fcm_slice* s, int n) {
+    int64_t total = 0, largest = 0;
+    unsigned cset = 0;
+    for (int i = 0; i < n; ++i) {
+        total += s[i].n;
+        largest = std::max(largest, s[i].n);
+        cset |= 1u << s[i].C;
+    }
+    char buf[512];
+    std::snprintf(buf, sizeof(buf), "%s|C%x|s%d|p%d|l%d", h->device_name.c_str(), cset, ilog2(n), ilog2(total),
+                  ilog2(largest));
+    return buf;
+}
+
+fcm_batch_plan default_plan() { return fcm_batch_plan{512, 4, 65536, 0.0}; }
+
+}  // namespace
+
+void fcm_release_batched(fcm_ctx* h) {
+    if (!h || !h->batched) return;
+    BatchedWorkspace* w = h->batched;
+    free_graphs(w);
+    cudaFree(w->d_desc);
+    cudaFree(w->d_res);
+    cudaFree(w->d_order);
+    cudaFree(w->d_ctl);
+    cudaFreeHost(w->h_desc);
+    cudaFreeHost(w->h_res);
+    cudaFreeHost(w->h_order);
+    if (w->cap_stream) cudaStreamDestroy(w->cap_stream);
+    delete w;
+    h->batched = nullptr;
+}
+
+namespace {
+
+bool device_ptr(const void* p) {
+    cudaPointerAttributes a;
+    if (!p || cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// One batch, synchronously: descriptors and order are already in the pinned
+// host buffers; results land in w->h_res.
+int run_once(fcm_ctx* h, const fcm_batch_plan& p, int n, bool use_graph) {
+    BatchedWorkspace* w = h->batched;
+    int rc;
+    if (!use_graph) {
+        CK(cudaMemcpyAsync(w->d_desc, w->h_desc, sizeof(SliceDesc) * n, cudaMemcpyHostToDevice, h->stream));
+        CK(cudaMemcpyAsync(w->d_order, w->h_order, sizeof(int) * n, cudaMemcpyHostToDevice, h->stream));
+        if ((rc = launch_kernel(h, h->stream, p, n))) return rc;
+        CK(cudaMemcpyAsync(w->h_res, w->d_res, sizeof(SliceResult) * n, cudaMemcpyDeviceToHost, h->stream));
+        CK(cudaStreamSynchronize(h->stream));
+        return 0;
+    }
+    const auto key = std::make_tuple(n, p.block, p.cluster, p.big);
+    auto it = w->graphs.find(key);
+    if (it == w->graphs.end()) {
+        cudaStream_t s = w->cap_stream;
+        CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+        cudaError_t e = cudaMemcpyAsync(w->d_desc, w->h_desc, sizeof(SliceDesc) * n, cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(w->d_order, w->h_order, sizeof(int) * n, cudaMemcpyHostToDevice, s);
+        int lrc = e == cudaSuccess ? launch_kernel(h, s, p, n) : 0;
+        if (e == cudaSuccess && lrc == 0)
+            e = cudaMemcpyAsync(w->h_res, w->d_res, sizeof(SliceResult) * n, cudaMemcpyDeviceToHost, s);
+        cudaGraph_t g = nullptr;
+        cudaError_t e2 = cudaStreamEndCapture(s, &g);
+        if (e != cudaSuccess || lrc != 0 || e2 != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            cudaGetLastError();
+            return lrc ? lrc : ctx_fail(h, e != cudaSuccess ? e : e2, "capturing the batch graph");
+        }
+        GraphEntry ge;
+        ge.graph = g;
+        e = cudaGraphInstantiate(&ge.exec, g, 0);
+        if (e != cudaSuccess) {
+            cudaGraphDestroy(g);
+            return ctx_fail(h, e, "instantiating the batch graph");
+        }
+        it = w->graphs.emplace(key, ge).first;
+    }
+    CK(cudaGraphLaunch(it->second.exec, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return 0;
+}
+
+// Time one plan on the batch: best of `reps` launches after one warm-up.
+int time_plan(fcm_ctx* h, const fcm_batch_plan& p, int n, int reps, double* ms_out) {
+    int rc = launch_kernel(h, h->stream, p, n);
+    if (rc) return rc;
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    double best = 1e30;
+    for (int r = 0; r < reps && rc == 0; ++r) {
+        cudaEventRecord(e0, h->stream);
+        rc = launch_kernel(h, h->stream, p, n);
+        cudaEventRecord(e1, h->stream);
+        if (cudaEventSynchronize(e1) != cudaSuccess) rc = FCM_ERR_CUDA;
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        best = std::min(best, (double)ms);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    *ms_out = best;
+    return rc;
+}
+
+}  // namespace
+
+extern "C" {
+
+int fcm_run_batched(fcm_handle h, fcm_slice* slices, int n_slices, int options) {
+    if (!h) return FCM_ERR_INVALID_ARG;
+    if (!slices || n_slices < 1) return ctx_invalid(h, "no slices");
+    bool in_place = false;
+    for (int i = 0; i < n_slices; ++i) {
+        const fcm_slice& s = slices[i];
+        const bool ok = s.n >= 1 && s.n < ((int64_t)1 << 40) && s.C >= 1 && s.C <= FCM_MAX_CLUSTERS &&
+                        s.m > 1.0f && std::isfinite(s.m) && s.eps >= 0.0f && std::isfinite(s.eps) &&
+                        s.max_iter >= 1 && (s.init_mode == FCM_INIT_U || s.init_mode == FCM_INIT_V) &&
+                        s.x && s.U && s.V && ((uintptr_t)s.x % 16 == 0);
+        if (!ok) {
+            char buf[96];
+            std::snprintf(buf, sizeof(buf), "slice %d: bad size, C, m, eps, max_iter, mode or pointer", i);
+            return ctx_invalid(h, buf);
+        }
+        if (s.init_mode == FCM_INIT_U && (!s.U0 || s.U0 == s.U)) in_place = true;
+    }
+    DeviceGuard g(h->device);
+    int rc = ensure_batched(h, n_slices);
+    if (rc) return rc;
+    BatchedWorkspace* w = h->batched;
+    for (int i = 0; i < n_slices; ++i) {
+        const fcm_slice& s = slices[i];
+        const float* U0 = s.init_mode == FCM_INIT_U ? (s.U0 ? s.U0 : s.U) : s.U;
+        if (!device_ptr(s.x) || !device_ptr(s.U) || !device_ptr(s.V) || !device_ptr(U0)) {
+            char buf[96];
+            std::snprintf(buf, sizeof(buf), "slice %d: x, U, U0 and V must be device memory", i);
+            return ctx_invalid(h, buf);
+        }
+        SliceDesc& d = w->h_desc[i];
+        std::memset(&d, 0, sizeof(d));
+        d.x = s.x;
+        d.U0 = U0;
+        d.U = s.U;
+        d.V = s.V;
+        d.n = s.n;
+        d.C = s.C;
+        d.mk = mkind_of(s.m);
+        d.m = s.m;
+        d.inv_m1 = (float)(1.0 / ((double)s.m - 1.0));
+        d.eps = s.eps;
+        d.max_iter = s.max_iter;
+        d.init = s.init_mode;
+        for (int j = 0; j < s.C; ++j) d.V0[j] = s.init_mode == FCM_INIT_V ? s.V0[j] : 0.0f;
+    }
+    // LPT: the largest slices first (ties by index, so the order is stable)
+    std::iota(w->h_order, w->h_order + n_slices, 0);
+    std::stable_sort(w->h_order, w->h_order + n_slices,
+                     [&](int a, int b) { return slices[a].n > slices[b].n; });
+
+    fcm_batch_plan plan;
+    if (w->forced) {
+        plan = w->forced_plan;
+    } else {
+        if (!w->cache_loaded) load_cache(w);
+        const std::string key = bucket_key(h, slices, n_slices);
+        auto it = w->plans.find(key);
+        const bool may_tune = !(options & FCM_BATCH_NO_TUNE) && !in_place;
+        if (it != w->plans.end() && !(options & FCM_BATCH_RETUNE)) {
+            plan = it->second;
+        } else if (may_tune) {
+            // upload the batch once, then time every candidate shape on it
+            CK(cudaMemcpyAsync(w->d_desc, w->h_desc, sizeof(SliceDesc) * n_slices, cudaMemcpyHostToDevice,
+                               h->stream));
+            CK(cudaMemcpyAsync(w->d_order, w->h_order, sizeof(int) * n_slices, cudaMemcpyHostToDevice,
+                               h->stream));
+            fcm_batch_plan best = default_plan();
+            best.ms = 1e30;
+            const int blocks[2] = {256, 512};
+            const int clusters[4] = {1, 2, 4, 8};
+            const int64_t bigs[3] = {16384, 65536, 131072};
+            for (int b : blocks)
+                for (int k : clusters)
+                    for (int gi = 0; gi < (k == 1 ? 1 : 3); ++gi) {
+                        fcm_batch_plan p{b, k, k == 1 ? ((int64_t)1 << 62) : bigs[gi], 0.0};
+                        if (grid_ctas(h, b, k) < k) continue;
+                        double ms = 0;
+                        if ((rc = time_plan(h, p, n_slices, 2, &ms))) return rc;
+                        if (ms < best.ms) {
+                            best = p;
+                            best.ms = ms;
+                        }
+                    }
+            plan = best;
+            w->plans[key] = best;
+            save_cache(w);
+        } else {
+            plan = default_plan();
+        }
+    }
+    if ((rc = run_once(h, plan, n_slices, !(options & FCM_BATCH_NO_GRAPH)))) return rc;
+    w->last = plan;
+
+    int worst = FCM_OK;
+    for (int i = 0; i < n_slices; ++i) {
+        const SliceResult& r = w->h_res[i];
+        fcm_slice& s = slices[i];
+        s.iters = r.iters;
+        s.status = r.status;
+        s.flags = r.flags;
+        s.delta = r.delta;
+        s.J = r.J;
+        for (int j = 0; j < FCM_MAX_CLUSTERS; ++j) s.V64[j] = j < s.C ? r.V64[j] : 0.0;
+        if (r.status < 0 && worst >= 0) worst = r.status;
+        if (r.status == FCM_NOT_CONVERGED && worst == FCM_OK) worst = FCM_NOT_CONVERGED;
+    }
+    return worst;
+}
+
+int fcm_batched_plan(fcm_handle h, fcm_batch_plan* plan) {
+    if (!h || !plan) return FCM_ERR_INVALID_ARG;
+    if (!h->batched) return ctx_invalid(h, "no batched run yet");
+    *plan = h->batched->last;
+    return FCM_OK;
+}
+
+int fcm_batched_set_plan(fcm_handle h, const fcm_batch_plan* plan) {
+    if (!h) return FCM_ERR_INVALID_ARG;
+    if (!h->batched) h->batched = new BatchedWorkspace();
+    if (!plan) {
+        h->batched->forced = false;
+        return FCM_OK;
+    }
+    if ((plan->block != 256 && plan->block != 512) ||
+        (plan->cluster != 1 && plan->cluster != 2 && plan->cluster != 4 && plan->cluster != 8) || plan->big < 1)
+        return ctx_invalid(h, "plan: block 256|512, cluster 1|2|4|8, big >= 1");
+    h->batched->forced = true;
+    h->batched->forced_plan = *plan;
+    return FCM_OK;
+}
+
+}  // extern "C"

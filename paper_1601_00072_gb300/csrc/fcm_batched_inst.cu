@@ -1,0 +1,470 @@
+// Batched FCM: many independent slices in one persistent launch.
+//
+// Compiled once per block size with -DFCM_BATCH_NT=256 or 512.
+//
+// Each slice is one run of Algorithm 1 (arXiv:1601.00072, Sec. 2.1) with its
+// own n, C, m, eps and max_iter. The grid is persistent: CTAs (or thread-block
+// clusters) take slices from a work queue ordered by decreasing size (LPT),
+// so the largest slices start first and the small ones fill the tail.
+//
+//  * Big slices (n >= plan.big) are shared by all K CTAs of a cluster: each
+//    CTA takes a contiguous 1/K of the pixels; after every pass the CTAs
+//    exchange their block totals through distributed shared memory at a
+//    hardware cluster barrier and add them in rank order, so every rank
+//    derives the same centers and the same stop decision.
+//  * Once the queue reaches small slices, every CTA works alone.
+//
+// No U is stored between iterations: U^{k-1} is recomputed from V^{k-1} with
+// the same code that produced it (bit-identical), so an iteration reads only
+// x, which sits in shared memory when the CTA's share fits. U^0 (when given)
+// is read in the first two passes; U^k is written once, after the last
+// iteration. All per-pixel arithmetic is the single-image pass's (Eq. 4 in
+// packed FP32x2 pairs); sums run in FP32 over chunks of a few pixels, then in
+// compensated FP32 per thread and warp, and in FP64 across warps and CTAs.
+#include "fcm_batched.h"
+#include "fcm_device.cuh"
+
+#ifndef FCM_BATCH_NT
+#error "compile with -DFCM_BATCH_NT=<threads per CTA>"
+#endif
+
+namespace fcm {
+namespace {
+
+constexpr int NTB = FCM_BATCH_NT;
+constexpr int NWB = NTB / 32;
+// Up to 128 registers per thread (the recompute loop keeps two center sets
+// and packed accumulators live): one 512-thread CTA or two 256-thread CTAs
+// per SM, with 192 KB or 96 KB of x staging each.
+constexpr int XCAP = NTB == 512 ? 49152 : 24576;
+constexpr int MIN_BLOCKS = NTB == 512 ? 1 : 2;
+constexpr int SBMAX = 2 * FCM_MAX_CLUSTERS + 3;  // num[C], den[C], J, max|dU|, bad
+
+__device__ __forceinline__ unsigned cluster_rank() {
+    unsigned r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ unsigned cluster_size() {
+    unsigned k;
+    asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(k));
+    return k;
+}
+// Hardware barrier of all threads of all CTAs of the cluster, with release /
+// acquire ordering of their shared-memory writes.
+__device__ __forceinline__ void cluster_sync() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+__device__ __forceinline__ uint32_t dsmem_addr(const void* local, unsigned rank) {
+    uint32_t a = static_cast<uint32_t>(__cvta_generic_to_shared(local)), r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+    return r;
+}
+__device__ __forceinline__ double ld_dsmem_f64(const double* local, unsigned rank) {
+    double v;
+    asm volatile("ld.shared::cluster.f64 %0, [%1];" : "=d"(v) : "r"(dsmem_addr(local, rank)) : "memory");
+    return v;
+}
+__device__ __forceinline__ int ld_dsmem_s32(const int* local, unsigned rank) {
+    int v;
+    asm volatile("ld.shared::cluster.s32 %0, [%1];" : "=r"(v) : "r"(dsmem_addr(local, rank)) : "memory");
+    return v;
+}
+
+struct BatchShared {
+    float w[NWB][2 * SBMAX];  // warp totals: (hi, lo) of each sum, then the maxima
+    double red[2][SBMAX];     // block totals, double-buffered for the cluster exchange
+    double tot[SBMAX];        // slice totals (the same on every rank)
+    double vq[FCM_MAX_CLUSTERS];  // next centers, FP64 quotients
+    float vcur[FCM_MAX_CLUSTERS], vprev[FCM_MAX_CLUSTERS];  // centers, for the scalar path
+    int idx;
+};
+
+// Per-thread pass sums: compensated (double-float) num, den and J, plus the
+// maxima. Threads add pixels in FP32 over chunks of CHUNK pairs and fold each
+// chunk into these, so the rounding of a thread's sum does not grow with the
+// size of its share of the slice.
+constexpr int CHUNK = 8;
+
+template <int C>
+struct SliceAcc {
+    DF s[2 * C + 1];
+    float dmax;
+    bool bad;
+    __device__ __forceinline__ void reset() {
+#pragma unroll
+        for (int t = 0; t < 2 * C + 1; ++t) s[t] = DF{0.0f, 0.0f};
+        dmax = 0.0f;
+        bad = false;
+    }
+};
+
+// Totals of one pass over the slice: double-float warp sums, the CTA's warps
+// in FP64, then (K > 1) the K CTAs in rank order through distributed shared
+// memory. Leaves sh.tot and the FP64 quotients sh.vq = num / den.
+template <int C>
+__device__ __forceinline__ void slice_reduce(BatchShared& sh, SliceAcc<C>& a, unsigned K, int& parity) {
+    constexpr int S = 2 * C + 3;
+    constexpr int NS = 2 * C + 1;  // compensated sums
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int t = 0; t < NS; ++t) {
+        const DF d = warp_sum_df(a.s[t]);
+        if (lane == 0) {
+            sh.w[warp][2 * t] = d.hi;
+            sh.w[warp][2 * t + 1] = d.lo;
+        }
+    }
+    const float dm = warp_max(a.dmax), bd = warp_max(a.bad ? 1.0f : 0.0f);
+    if (lane == 0) {
+        sh.w[warp][2 * NS] = dm;
+        sh.w[warp][2 * NS + 1] = bd;
+    }
+    __syncthreads();
+    if (threadIdx.x < S) {
+        const int s = threadIdx.x;
+        double t = 0.0;
+        if (s < NS) {
+            for (int w = 0; w < NWB; ++w) t += (double)sh.w[w][2 * s] + (double)sh.w[w][2 * s + 1];
+        } else {
+            for (int w = 0; w < NWB; ++w) t = fmax(t, (double)sh.w[w][2 * NS + (s - NS)]);
+        }
+        sh.red[parity][s] = t;
+    }
+    if (K > 1) {
+        cluster_sync();
+        if (threadIdx.x < S) {
+            const int s = threadIdx.x;
+            double t = ld_dsmem_f64(&sh.red[parity][s], 0);
+            for (unsigned q = 1; q < K; ++q) {
+                const double u = ld_dsmem_f64(&sh.red[parity][s], q);
+                t = (s < NS) ? t + u : fmax(t, u);
+            }
+            sh.tot[s] = t;
+        }
+    } else {
+        __syncthreads();
+        if (threadIdx.x < S) sh.tot[threadIdx.x] = sh.red[parity][threadIdx.x];
+    }
+    parity ^= 1;
+    __syncthreads();
+    if (threadIdx.x < C) {
+        const double den = sh.tot[C + threadIdx.x];
+        sh.vq[threadIdx.x] = den > 0.0 ? sh.tot[threadIdx.x] / den : 0.0;
+    }
+    __syncthreads();
+}
+
+template <int C, int MK>
+__device__ __noinline__ void process_slice(const SliceDesc& d, SliceResult& res, unsigned r, unsigned K, float* xs,
+                                           BatchShared& sh) {
+    const int64_t n = d.n;
+    int64_t share = (n + K - 1) / K;
+    share += share & 1;  // even, so only the last pixel of the slice can be unpaired
+    const int64_t lo = min(n, (int64_t)r * share), hi = min(n, lo + share);
+    const int cnt = (int)(hi - lo);
+    const bool staged = cnt <= XCAP;
+    if (threadIdx.x < C) sh.vcur[threadIdx.x] = sh.vprev[threadIdx.x] = d.V0[threadIdx.x];
+    if (staged)
+        for (int i = threadIdx.x; i < cnt; i += NTB) xs[i] = __ldg(d.x + lo + i);
+    __syncthreads();
+    const float* xl = staged ? xs : d.x + lo;
+    const int npair = cnt >> 1;
+    const bool odd_tail = (cnt & 1) && threadIdx.x == 0;  // the slice's last pixel, alone
+    const float m = d.m, inv_m1 = d.inv_m1;
+    const bool from_u = d.init == FCM_INIT_U;
+    const float* U0 = d.U0;
+    float (&v)[C] = *reinterpret_cast<float(*)[C]>(sh.vcur);
+    float (&vp)[C] = *reinterpret_cast<float(*)[C]>(sh.vprev);
+
+    f2 v2[C], vp2[C];
+#pragma unroll
+    for (int j = 0; j < C; ++j) v2[j] = vp2[j] = pack2(d.V0[j], d.V0[j]);
+    int parity = 0, flags = 0;
+    SliceAcc<C> a;
+
+    // ---- pass 0: V^1 from U^0 (Eq. 3), or U^0 = membership(V^0) (Eq. 4) ----
+    a.reset();
+    if (!from_u) {
+#pragma unroll
+        for (int j = 0; j < C; ++j) a.bad |= !finite_f(d.V0[j]);
+    }
+    for (int p0 = threadIdx.x; p0 < npair; p0 += NTB * CHUNK) {
+        float num[C], den[C];
+#pragma unroll
+        for (int j = 0; j < C; ++j) num[j] = den[j] = 0.0f;
+        for (int q = 0, p = p0; q < CHUNK && p < npair; ++q, p += NTB) {
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int i = 2 * p + h;
+                const float xi = xl[i];
+                a.bad |= !finite_f(xi);
+                if (from_u) {
+#pragma unroll
+                    for (int j = 0; j < C; ++j) {
+                        const float u0 = __ldg(U0 + (int64_t)j * n + lo + i);
+                        a.bad |= !(u0 >= 0.0f) || !finite_f(u0);
+                        const float w = pow_m<MK>(u0, m);
+                        num[j] = fmaf(w, xi, num[j]);
+                        den[j] += w;
+                    }
+                } else {
+                    float u[C], um[C];
+                    membership<C, MK>(xi, v, m, inv_m1, u, um);
+#pragma unroll
+                    for (int j = 0; j < C; ++j) {
+                        num[j] = fmaf(um[j], xi, num[j]);
+                        den[j] += um[j];
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < C; ++j) {
+            df_add(a.s[j], num[j]);
+            df_add(a.s[C + j], den[j]);
+        }
+    }
+    if (odd_tail) {
+        const float xi = xl[cnt - 1];
+        a.bad |= !finite_f(xi);
+#pragma unroll
+        for (int j = 0; j < C; ++j) {
+            float w;
+            if (from_u) {
+                const float u0 = __ldg(U0 + (int64_t)j * n + lo + cnt - 1);
+                a.bad |= !(u0 >= 0.0f) || !finite_f(u0);
+                w = pow_m<MK>(u0, m);
+            } else {
+                float u[C], um[C];
+                membership<C, MK>(xi, v, m, inv_m1, u, um);
+                w = um[j];
+            }
+            df_add(a.s[j], w * xi);
+            df_add(a.s[C + j], w);
+        }
+    }
+    slice_reduce<C>(sh, a, K, parity);
+
+    int status = FCM_NOT_CONVERGED, iters = 0;
+    double delta = 0.0, Jk = 0.0;
+    double v64[C];
+#pragma unroll
+    for (int j = 0; j < C; ++j) v64[j] = d.V0[j];
+    if (sh.tot[2 * C + 2] != 0.0) {
+        status = FCM_ERR_BAD_INPUT;
+    } else {
+        float vn[C];
+#pragma unroll
+        for (int j = 0; j < C; ++j) {
+            if (sh.tot[C + j] > 0.0) {
+                v64[j] = sh.vq[j];
+                vn[j] = (float)sh.vq[j];
+            } else {
+                flags |= FCM_FLAG_EMPTY_CLUSTER;  // V^0 kept, or 0 from a U^0
+                vn[j] = from_u ? 0.0f : d.V0[j];
+                v64[j] = vn[j];
+            }
+            v2[j] = pack2(vn[j], vn[j]);
+        }
+        __syncthreads();
+        if (threadIdx.x < C) sh.vcur[threadIdx.x] = vn[threadIdx.x];
+        __syncthreads();
+        // ---- iterations: U^k from V^k, U^{k-1} recomputed from V^{k-1} ----
+        for (int k = 1;; ++k) {
+            a.reset();
+            const bool prev_given = from_u && k == 1;
+            for (int p0 = threadIdx.x; p0 < npair; p0 += NTB * CHUNK) {
+                f2 num2[C], den2[C], J2 = pack2(0.0f, 0.0f);
+#pragma unroll
+                for (int j = 0; j < C; ++j) num2[j] = den2[j] = pack2(0.0f, 0.0f);
+                for (int q = 0, p = p0; q < CHUNK && p < npair; ++q, p += NTB) {
+                    const float2 xv = *reinterpret_cast<const float2*>(xl + 2 * p);
+                    const f2 xq = pack2(xv.x, xv.y);
+                    f2 u2[C], um2[C];
+                    J2 = add2(J2, membership_pair<C, MK>(xq, v2, m, inv_m1, v, u2, um2));
+                    f2 uo2[C];
+                    if (prev_given) {
+#pragma unroll
+                        for (int j = 0; j < C; ++j) {
+                            const float* r0 = U0 + (int64_t)j * n + lo + 2 * p;
+                            uo2[j] = pack2(__ldg(r0), __ldg(r0 + 1));
+                        }
+                    } else {
+                        f2 tmp[C];
+                        membership_pair<C, MK>(xq, vp2, m, inv_m1, vp, uo2, tmp);
+                    }
+#pragma unroll
+                    for (int j = 0; j < C; ++j) {
+                        num2[j] = fma2(um2[j], xq, num2[j]);
+                        den2[j] = add2(den2[j], um2[j]);
+                        float da, db;
+                        unpack2(sub2(u2[j], uo2[j]), da, db);
+                        a.dmax = fmaxf(a.dmax, fmaxf(fabsf(da), fabsf(db)));
+                    }
+                }
+#pragma unroll
+                for (int j = 0; j < C; ++j) {
+                    df_add(a.s[j], lo2(num2[j]) + hi2(num2[j]));
+                    df_add(a.s[C + j], lo2(den2[j]) + hi2(den2[j]));
+                }
+                df_add(a.s[2 * C], lo2(J2) + hi2(J2));
+            }
+            if (odd_tail) {
+                const float xi = xl[cnt - 1];
+                float u[C], um[C], uo[C], umo[C];
+                df_add(a.s[2 * C], membership<C, MK>(xi, v, m, inv_m1, u, um));
+                if (prev_given) {
+#pragma unroll
+                    for (int j = 0; j < C; ++j) uo[j] = __ldg(U0 + (int64_t)j * n + lo + cnt - 1);
+                } else {
+                    membership<C, MK>(xi, vp, m, inv_m1, uo, umo);
+                }
+#pragma unroll
+                for (int j = 0; j < C; ++j) {
+                    df_add(a.s[j], um[j] * xi);
+                    df_add(a.s[C + j], um[j]);
+                    a.dmax = fmaxf(a.dmax, fabsf(u[j] - uo[j]));
+                }
+            }
+            slice_reduce<C>(sh, a, K, parity);
+            delta = sh.tot[2 * C + 1];
+            Jk = sh.tot[2 * C];
+            iters = k;
+            if (delta < d.eps) {
+                status = FCM_OK;
+                break;
+            }
+            if (k >= d.max_iter) {
+                status = FCM_NOT_CONVERGED;
+                break;
+            }
+#pragma unroll
+            for (int j = 0; j < C; ++j) {
+                vp2[j] = v2[j];
+                vn[j] = v[j];
+                if (sh.tot[C + j] > 0.0) {
+                    v64[j] = sh.vq[j];
+                    vn[j] = (float)sh.vq[j];
+                    v2[j] = pack2(vn[j], vn[j]);
+                } else {
+                    flags |= FCM_FLAG_EMPTY_CLUSTER;  // keep v_j
+                }
+            }
+            __syncthreads();  // every thread has read sh.vcur
+            if (threadIdx.x < C) {
+                sh.vprev[threadIdx.x] = sh.vcur[threadIdx.x];
+                sh.vcur[threadIdx.x] = vn[threadIdx.x];
+            }
+            __syncthreads();
+        }
+        // ---- U^k, written once ----
+        float* U = d.U;
+        for (int p = threadIdx.x; p < npair; p += NTB) {
+            const float2 xv = *reinterpret_cast<const float2*>(xl + 2 * p);
+            f2 u2[C], um2[C];
+            membership_pair<C, MK>(pack2(xv.x, xv.y), v2, m, inv_m1, v, u2, um2);
+#pragma unroll
+            for (int j = 0; j < C; ++j) {
+                float a0, b0;
+                unpack2(u2[j], a0, b0);
+                float* row = U + (int64_t)j * n + lo + 2 * p;
+                __stcs(row, a0);
+                __stcs(row + 1, b0);
+            }
+        }
+        if (odd_tail) {
+            float u[C], um[C];
+            membership<C, MK>(xl[cnt - 1], v, m, inv_m1, u, um);
+#pragma unroll
+            for (int j = 0; j < C; ++j) __stcs(U + (int64_t)j * n + lo + cnt - 1, u[j]);
+        }
+    }
+    if (r == 0 && threadIdx.x == 0) {
+        res.iters = iters;
+        res.status = status;
+        res.flags = flags;
+        res.delta = delta;
+        res.J = Jk;
+#pragma unroll
+        for (int j = 0; j < C; ++j) {
+            res.V64[j] = v64[j];
+            d.V[j] = v[j];
+        }
+    }
+    // no rank leaves the slice (and reuses its shared memory) while another
+    // may still read it
+    if (K > 1) cluster_sync();
+    __syncthreads();
+}
+
+__device__ __forceinline__ void run_slice(const SliceDesc& d, SliceResult& res, unsigned r, unsigned K, float* xs,
+                                          BatchShared& sh) {
+#define FCM_BATCH_CASE(CC)                                                                  \
+    case CC:                                                                                \
+        switch (d.mk) {                                                                     \
+            case M_TWO: process_slice<CC, M_TWO>(d, res, r, K, xs, sh); break;              \
+            case M_THREE: process_slice<CC, M_THREE>(d, res, r, K, xs, sh); break;          \
+            case M_ONE_HALF: process_slice<CC, M_ONE_HALF>(d, res, r, K, xs, sh); break;    \
+            default: process_slice<CC, M_GENERIC>(d, res, r, K, xs, sh); break;             \
+        }                                                                                   \
+        break;
+    switch (d.C) {
+        FCM_BATCH_CASE(1)
+        FCM_BATCH_CASE(2)
+        FCM_BATCH_CASE(3)
+        FCM_BATCH_CASE(4)
+        FCM_BATCH_CASE(5)
+        FCM_BATCH_CASE(6)
+        FCM_BATCH_CASE(7)
+        FCM_BATCH_CASE(8)
+        default: break;
+    }
+#undef FCM_BATCH_CASE
+}
+
+__global__ void __launch_bounds__(NTB, MIN_BLOCKS)
+    k_fcm_batched(const SliceDesc* __restrict__ descs, const int* __restrict__ order, int n_slices,
+                  SliceResult* __restrict__ results, BatchCtl* __restrict__ ctl, int64_t big) {
+    extern __shared__ __align__(16) float xs[];
+    __shared__ BatchShared sh;
+    const unsigned K = cluster_size(), r = cluster_rank();
+    bool solo = K == 1;
+    int first_solo = -1;
+    // ---- the cluster shares the big slices ----
+    while (!solo) {
+        if (r == 0 && threadIdx.x == 0) sh.idx = (int)atomicAdd(&ctl->next, 1u);
+        cluster_sync();
+        const int idx = ld_dsmem_s32(&sh.idx, 0);
+        cluster_sync();  // every rank has read the index before rank 0 takes another
+        if (idx >= n_slices) return;
+        const int s = order[idx];
+        if (descs[s].n >= big) {
+            run_slice(descs[s], results[s], r, K, xs, sh);
+            continue;
+        }
+        // the queue has reached the small slices: every CTA works alone now
+        solo = true;
+        if (r == 0) first_solo = s;
+    }
+    if (first_solo >= 0) run_slice(descs[first_solo], results[first_solo], 0, 1, xs, sh);
+    for (;;) {
+        if (threadIdx.x == 0) sh.idx = (int)atomicAdd(&ctl->next, 1u);
+        __syncthreads();
+        const int idx = sh.idx;
+        __syncthreads();
+        if (idx >= n_slices) return;
+        const int s = order[idx];
+        run_slice(descs[s], results[s], 0, 1, xs, sh);
+    }
+}
+
+}  // namespace
+
+#define FCM_CAT2(a, b) a##b
+#define FCM_CAT(a, b) FCM_CAT2(a, b)
+BatchKernel FCM_CAT(batched_kernel_, FCM_BATCH_NT)() {
+    return BatchKernel{k_fcm_batched, XCAP * (int)sizeof(float), XCAP};
+}
+
+}  // namespace fcm

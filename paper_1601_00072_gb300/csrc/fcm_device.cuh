@@ -227,6 +227,39 @@ __device__ __forceinline__ f2 membership_pair(f2 x2, const f2 (&v2)[C], float m,
     return pack2(ja, jb);
 }
 
+// Compensated FP32 ("double-float") sum, hi + lo, with Knuth's TwoSum: long
+// sums of the center numerators/denominators and of J carry about 44 bits
+// while using only FP32 instructions.
+struct DF {
+    float hi, lo;
+};
+__device__ __forceinline__ void df_add(DF& a, float b) {
+    const float s = __fadd_rn(a.hi, b);
+    const float bb = __fsub_rn(s, a.hi);
+    const float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    a.hi = s;
+    a.lo = __fadd_rn(a.lo, e);
+}
+__device__ __forceinline__ DF df_merge(DF a, DF b) {
+    const float s = __fadd_rn(a.hi, b.hi);
+    const float bb = __fsub_rn(s, a.hi);
+    const float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(b.hi, bb));
+    const float lo = __fadd_rn(__fadd_rn(a.lo, b.lo), e);
+    const float hi = __fadd_rn(s, lo);  // Fast2Sum renormalisation (|s| >= |lo|)
+    return DF{hi, __fsub_rn(lo, __fsub_rn(hi, s))};
+}
+
+// Warp-wide double-float sum (xor tree, fixed order).
+__device__ __forceinline__ DF warp_sum_df(DF d) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        DF e{__shfl_xor_sync(0xffffffffu, d.hi, o), __shfl_xor_sync(0xffffffffu, d.lo, o)};
+        d = (lane & o) ? df_merge(e, d) : df_merge(d, e);
+    }
+    return d;
+}
+
 __device__ __forceinline__ float warp_sum(float v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);

@@ -64,6 +64,20 @@ struct fcm_ctx {
 };
 
 namespace fcm {
+
+// Makes a device current for a scope and restores the caller's afterwards.
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
 int ctx_fail(fcm_ctx* h, cudaError_t e, const char* what);
 int ctx_invalid(fcm_ctx* h, const char* what);
 int ctx_grow(fcm_ctx* h, void** p, size_t* cap, size_t bytes, const char* what);

@@ -483,28 +483,6 @@ __global__ void __launch_bounds__(NT, (C <= 4 ? 3 : 2)) k_fcm_pass_tma(RunState*
 // The whole run in one cooperative launch (n % 4 == 0, aligned rows).
 // ---------------------------------------------------------------------------
 
-// Compensated FP32 ("double-float") sum, hi + lo, with Knuth's TwoSum: the
-// cross-block sums of the center numerators/denominators and of J carry about
-// 44 bits, using only FP32 instructions in every block.
-struct DF {
-    float hi, lo;
-};
-__device__ __forceinline__ void df_add(DF& a, float b) {
-    const float s = __fadd_rn(a.hi, b);
-    const float bb = __fsub_rn(s, a.hi);
-    const float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(b, bb));
-    a.hi = s;
-    a.lo = __fadd_rn(a.lo, e);
-}
-__device__ __forceinline__ DF df_merge(DF a, DF b) {
-    const float s = __fadd_rn(a.hi, b.hi);
-    const float bb = __fsub_rn(s, a.hi);
-    const float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(b.hi, bb));
-    const float lo = __fadd_rn(__fadd_rn(a.lo, b.lo), e);
-    const float hi = __fadd_rn(s, lo);  // Fast2Sum renormalisation (|s| >= |lo|)
-    return DF{hi, __fsub_rn(lo, __fsub_rn(hi, s))};
-}
-
 __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
     unsigned v;
     asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");

@@ -50,6 +50,29 @@ class FCMResult:
         return self.status == _lib.FCM_OK
 
 
+@dataclass
+class Slice:
+    """One image of a batch. ``x`` is a CUDA float32 tensor of n pixels; give
+    ``U0`` [C, n] (read only) or ``V0`` (C initial centers). ``U`` and ``V``
+    receive the results (allocated when None). After the run the result
+    fields are filled."""
+    x: object
+    C: int
+    m: float = 2.0
+    eps: float = 1e-5
+    max_iter: int = 300
+    U0: object = None
+    V0: object = None
+    U: object = None
+    V: object = None
+    iters: int = 0
+    status: int = 0
+    flags: int = 0
+    delta: float = 0.0
+    J: float = 0.0
+    V64: np.ndarray | None = None
+
+
 class FCM:
     """A handle of the CUDA FCM library bound to one device.
 
@@ -160,3 +183,52 @@ class FCM:
                                            _ptr(V), int(launches), 0 if tma else _lib.FCM_OPT_NO_TMA,
                                            ctypes.byref(ms)), self._h)
         return ms.value
+
+    def run_batched(self, slices, tune: bool = True, retune: bool = False, graph: bool = True,
+                    raise_on_error: bool = False) -> int:
+        """Algorithm 1 on every slice in one persistent launch (see
+        ``fcm_run_batched``). Fills each Slice's U, V and result fields and
+        returns the aggregate status."""
+        import torch
+        arr = (_lib.fcm_slice * len(slices))()
+        for i, s in enumerate(slices):
+            n = _numel(s.x)
+            if s.U is None:
+                s.U = torch.empty((s.C, n), dtype=torch.float32, device=s.x.device)
+            if s.V is None:
+                s.V = torch.empty(s.C, dtype=torch.float32, device=s.x.device)
+            a = arr[i]
+            a.x, a.n, a.C, a.m, a.eps, a.max_iter = _ptr(s.x), n, s.C, s.m, s.eps, s.max_iter
+            a.U, a.V = _ptr(s.U), _ptr(s.V)
+            if s.V0 is not None:
+                a.init_mode = _lib.FCM_INIT_V
+                for j, vj in enumerate(np.asarray(s.V0, dtype=np.float64).reshape(-1)[:s.C]):
+                    a.V0[j] = float(vj)
+            else:
+                a.init_mode = _lib.FCM_INIT_U
+                a.U0 = None if s.U0 is None else _ptr(s.U0)
+        opts = ((0 if tune else _lib.FCM_BATCH_NO_TUNE) | (_lib.FCM_BATCH_RETUNE if retune else 0)
+                | (0 if graph else _lib.FCM_BATCH_NO_GRAPH))
+        self._bind_stream()
+        st = self._lib.fcm_run_batched(self._h, arr, len(slices), opts)
+        if st == _lib.FCM_ERR_INVALID_ARG or st == _lib.FCM_ERR_CUDA or st == _lib.FCM_ERR_OOM or raise_on_error:
+            _lib.check(st, self._h)
+        for i, s in enumerate(slices):
+            a = arr[i]
+            s.iters, s.status, s.flags, s.delta, s.J = a.iters, a.status, a.flags, a.delta, a.J
+            s.V64 = np.array(a.V64[:s.C])
+        return st
+
+    def batched_plan(self) -> dict:
+        p = _lib.fcm_batch_plan()
+        _lib.check(self._lib.fcm_batched_plan(self._h, ctypes.byref(p)), self._h)
+        return {"block": p.block, "cluster": p.cluster, "big": p.big, "ms": p.ms}
+
+    def set_batched_plan(self, block=None, cluster=None, big=None):
+        """Force a launch shape for later batched runs; no arguments returns
+        to the autotuner."""
+        if block is None:
+            _lib.check(self._lib.fcm_batched_set_plan(self._h, None), self._h)
+            return
+        p = _lib.fcm_batch_plan(int(block), int(cluster), int(big), 0.0)
+        _lib.check(self._lib.fcm_batched_set_plan(self._h, ctypes.byref(p)), self._h)

@@ -61,3 +61,72 @@ def assert_within(rep, iters_checked=True):
     if iters_checked and abs(rep["d_iters"]) > ITER_TOL:
         msgs.append(f"iteration count differs by {rep['d_iters']}")
     assert not msgs, "; ".join(msgs) + f"  ({rep})"
+
+
+def sensitivity(orc, x_u8, C, m, eps, max_iter, U0=None, V0=None, rel=1e-6, trials=4):
+    """The FP64 oracle's own spread at the FP32 rounding scale.
+
+    The oracle is restarted from its first centers V^1 and from copies of V^1
+    perturbed by +-rel (relative, systematic — the scale of FP32 rounding),
+    and the perturbed runs are compared with the unperturbed restart: largest
+    change of the iteration count, whether the clusters got relabelled, and
+    (after matching clusters by sorted centers) the largest change of the
+    final centers and memberships. Oracle only, CPU only."""
+    x_u8 = np.asarray(x_u8, dtype=np.uint8)
+    bins = np.arange(256.0)
+    if U0 is not None:
+        um = np.asarray(U0, dtype=np.float64) ** m
+        V1 = (um @ x_u8.astype(np.float64)) / um.sum(1)
+    else:
+        Ux = orc.memberships(bins, V0, m)[:, x_u8] ** m
+        V1 = (Ux @ x_u8.astype(np.float64)) / Ux.sum(1)
+    ref = orc.fcm_quantized(x_u8, C, m, eps32(eps), max_iter, V0=V1)
+    Uref = orc.memberships(bins, ref["V"], m)[:, x_u8]
+    env = {"iters": 0, "relabel": False, "center_rel_err": 0.0, "max_abs_dU": 0.0}
+    g = np.random.default_rng(12345)
+    for _ in range(trials):
+        Vp = V1 * (1.0 + rel * g.choice([-1.0, 1.0], size=C))
+        r = orc.fcm_quantized(x_u8, C, m, eps32(eps), max_iter, V0=Vp)
+        rep = permuted_report(orc.memberships(bins, r["V"], m)[:, x_u8], r["V"], Uref, ref["V"])
+        env["iters"] = max(env["iters"], abs(r["iters"] - ref["iters"]))
+        env["relabel"] |= center_err(r["V"], ref["V"]) > CENTER_TOL
+        env["center_rel_err"] = max(env["center_rel_err"], rep["center_rel_err"])
+        env["max_abs_dU"] = max(env["max_abs_dU"], rep["max_abs_dU"])
+    return env
+
+
+def trajectory_sensitive(env):
+    """FP32-scale perturbations change when the oracle converges (by more than
+    one iteration) or which cluster ends where: an FP32 run follows its own,
+    equally valid path, so it is judged on its converged result."""
+    return env["iters"] > ITER_TOL or env["relabel"]
+
+
+def assert_converged_within(rep, env):
+    """Converged results of a trajectory-sensitive input: the stated
+    tolerances, or twice the oracle's own spread where that is larger."""
+    c_tol = max(CENTER_TOL, 2 * env["center_rel_err"])
+    u_tol = max(U_TOL, 2 * env["max_abs_dU"])
+    msgs = []
+    if rep["center_rel_err"] > c_tol:
+        msgs.append(f"center rel err {rep['center_rel_err']:.3g} > {c_tol:.3g}")
+    if rep["max_abs_dU"] > u_tol:
+        msgs.append(f"max|dU| {rep['max_abs_dU']:.3g} > {u_tol:.3g}")
+    if rep["label_agreement"] < LABEL_AGREE:
+        msgs.append(f"label agreement {rep['label_agreement']:.6f} < {LABEL_AGREE}")
+    assert not msgs, "; ".join(msgs) + f"  ({rep}, oracle spread {env})"
+
+
+def permuted_report(gpu_U, gpu_V, ref_U, ref_V):
+    """Errors after matching the CUDA clusters to the oracle's by sorting the
+    centers (for inputs whose clusters may be relabelled)."""
+    gV, rV = np.asarray(gpu_V, np.float64), np.asarray(ref_V, np.float64)
+    pg, pr = np.argsort(gV), np.argsort(rV)
+    gU = np.asarray(gpu_U, np.float64)[pg]
+    rU = np.asarray(ref_U, np.float64)[pr]
+    return {
+        "center_rel_err": center_err(gV[pg], rV[pr]),
+        "max_abs_dU": float(np.max(np.abs(gU - rU))),
+        "label_agreement": float(np.mean(labels_of(gU) == labels_of(rU))),
+        "d_iters": 0,
+    }
