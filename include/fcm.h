@@ -218,6 +218,57 @@ int fcm_batched_plan(fcm_handle h, fcm_batch_plan* plan);
 int fcm_batched_set_plan(fcm_handle h, const fcm_batch_plan* plan);
 
 /*
+ * Learned warm start (not in the paper, which starts from random memberships,
+ * Algorithm 1 step 2). A small network maps a slice's grey-level histogram to
+ * initial centers V^0:
+ *   f  = [histogram / n over 256 bins of round(clip(x, 0, 255)), onehot(C)]
+ *                                                     (264 values, FP32)
+ *   a1 = GELU(W1 f + b1) (128), a2 = GELU(W2 a1 + b2) (128), y = W3 a2 + b3 (8)
+ *   V^0 = sort(255 * y[0..C-1])
+ * Weights are W[out, in], kept as FP32 master copies and used in BF16;
+ * accumulation, activations, gradients and Adam state are FP32. Training
+ * minimises the masked mean squared error sum_{b, j<C_b} (y_bj - t_bj)^2 /
+ * sum_b C_b against t = (sorted converged centers of plain FCM) / 255.
+ * Parameters, as one FP32 vector, in the order W1, b1, W2, b2, W3, b3.
+ * Device arrays: features [B, 264] row-major, targets [B, 8], C [B] (int).
+ */
+#define FCM_MODEL_PARAMS 51464
+
+/* Initialise the network (He-normal weights from a splitmix64 stream seeded
+ * with `seed`, zero hidden biases, output biases (j+1)/9). */
+int fcm_model_init(fcm_handle h, uint64_t seed);
+/* Set / read the FP32 parameters (host arrays of FCM_MODEL_PARAMS floats);
+ * setting resets the optimiser state. */
+int fcm_model_set_params(fcm_handle h, const float* params, int64_t count);
+int fcm_model_get_params(fcm_handle h, float* params, int64_t count);
+/* Save / load the parameters as a small binary file. */
+int fcm_model_save(fcm_handle h, const char* path);
+int fcm_model_load(fcm_handle h, const char* path);
+/* Network input of each slice (x and C of the structs are used) into device
+ * features [n, 264]. */
+int fcm_features(fcm_handle h, const fcm_slice* slices, int n, float* feats);
+/* Outputs y [B, 8] (device) of B feature rows (device). */
+int fcm_model_forward(fcm_handle h, const float* feats, int B, float* out);
+/* Loss and gradient (host arrays: loss[1], grad[FCM_MODEL_PARAMS]) of B rows,
+ * without updating the parameters. */
+int fcm_model_loss_grad(fcm_handle h, const float* feats, const float* targets, const int* C, int B,
+                        float* grad, float* loss);
+/* Adam (lr, beta 0.9 / 0.999, eps 1e-8) over `epochs` passes of shuffled
+ * full mini-batches of `batch` rows of the n training rows (device arrays),
+ * all on the GPU; *last_loss (nullable) receives the last epoch's mean loss. */
+int fcm_model_train(fcm_handle h, const float* feats, const float* targets, const int* C, int n,
+                    int epochs, int batch, float lr, uint64_t seed, float* last_loss);
+/* Predicted V^0 of every slice into slices[i].V0, with init_mode set to
+ * FCM_INIT_V. */
+int fcm_predict_centers(fcm_handle h, fcm_slice* slices, int n);
+/* Warm-started batch: predict V^0, run fcm_run_batched, and fall back to the
+ * plain cold start (the slice's U0, which must be given) for every slice whose
+ * prediction is unusable (non-finite or two centers within 1e-3) or whose
+ * warm run did not converge or emptied a cluster. *n_cold (nullable) counts
+ * the slices that ran cold. Returns as fcm_run_batched. */
+int fcm_run_batched_warm(fcm_handle h, fcm_slice* slices, int n, int options, int* n_cold);
+
+/*
  * fcm_time_pass — profiling aid: time `launches` back-to-back launches of the
  * iteration pass (one Algorithm 1 iteration each: Eq. 4, Eq. 1, Eq. 3) on the
  * handle's stream with CUDA events, starting from centers V (device or host,

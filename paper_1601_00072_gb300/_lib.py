@@ -55,6 +55,9 @@ class fcm_batch_plan(ctypes.Structure):
 FCM_BATCH_RETUNE = 16
 FCM_BATCH_NO_TUNE = 32
 FCM_BATCH_NO_GRAPH = 64
+FCM_MODEL_PARAMS = 51464
+MODEL_D_IN = 264
+MODEL_D_OUT = 8
 
 _vp = ctypes.c_void_p
 _i = ctypes.c_int
@@ -72,6 +75,17 @@ SIGNATURES = [
     ("fcm_run_batched", _i, [_vp, ctypes.POINTER(fcm_slice), _i, _i]),
     ("fcm_batched_plan", _i, [_vp, ctypes.POINTER(fcm_batch_plan)]),
     ("fcm_batched_set_plan", _i, [_vp, ctypes.POINTER(fcm_batch_plan)]),
+    ("fcm_model_init", _i, [_vp, ctypes.c_uint64]),
+    ("fcm_model_set_params", _i, [_vp, ctypes.POINTER(_f), _i64]),
+    ("fcm_model_get_params", _i, [_vp, ctypes.POINTER(_f), _i64]),
+    ("fcm_model_save", _i, [_vp, ctypes.c_char_p]),
+    ("fcm_model_load", _i, [_vp, ctypes.c_char_p]),
+    ("fcm_features", _i, [_vp, ctypes.POINTER(fcm_slice), _i, _vp]),
+    ("fcm_model_forward", _i, [_vp, _vp, _i, _vp]),
+    ("fcm_model_loss_grad", _i, [_vp, _vp, _vp, _vp, _i, ctypes.POINTER(_f), ctypes.POINTER(_f)]),
+    ("fcm_model_train", _i, [_vp, _vp, _vp, _vp, _i, _i, _i, _f, ctypes.c_uint64, ctypes.POINTER(_f)]),
+    ("fcm_predict_centers", _i, [_vp, ctypes.POINTER(fcm_slice), _i]),
+    ("fcm_run_batched_warm", _i, [_vp, ctypes.POINTER(fcm_slice), _i, _i, ctypes.POINTER(_i)]),
     ("fcm_run_noalloc", _i, [_vp, _i64, _i, _f, _f, _i, _i, _vp, _vp, _vp, _vp,
                              ctypes.POINTER(fcm_report)]),
     ("fcm_time_pass", _i, [_vp, _vp, _i64, _i, _f, _vp, _vp, _i, _i, ctypes.POINTER(_f)]),

@@ -1,4 +1,611 @@
-// Warm-start network kernels (filled in by the warm-start path).
+// Learned warm start: a small network from a slice's grey-level histogram to
+// initial centers V^0, trained and run on the GPU by the kernels below. The
+// paper starts from random memberships (Algorithm 1 step 2); this is an
+// addition of this library, judged by how many FCM iterations it saves.
+//
+//   f  = [histogram / n (256 bins of round(clip(x, 0, 255))), onehot(C) (8)]
+//   a1 = GELU(W1 f + b1)   (128)      a2 = GELU(W2 a1 + b2)   (128)
+//   y  = W3 a2 + b3        (8)        V^0 = sort(255 * y[:C])
+//   loss = sum_{b, j < C_b} (y_bj - t_bj)^2 / sum_b C_b
+//
+// Weights W[out, in] are kept as FP32 master copies (updated by Adam) and
+// used as BF16 in every product; activations, accumulation, gradients and
+// optimiser state are FP32. The products are small (batch <= a few hundred,
+// widths <= 264): a shared-memory tiled SIMT GEMM with fused bias/GELU
+// epilogues covers them.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "fcm.h"
 #include "fcm_runtime.h"
 
-void fcm_release_mlp(fcm_ctx* h) { (void)h; }
+using namespace fcm;
+
+namespace fcm {
+
+constexpr int D_HIST = 256, D_ONE = 8, D_IN = D_HIST + D_ONE, D_H = 128, D_OUT = 8;
+constexpr int64_t OFF_W1 = 0, OFF_B1 = OFF_W1 + D_H * D_IN, OFF_W2 = OFF_B1 + D_H, OFF_B2 = OFF_W2 + D_H * D_H,
+                  OFF_W3 = OFF_B2 + D_H, OFF_B3 = OFF_W3 + D_OUT * D_H, N_PARAMS = OFF_B3 + D_OUT;
+static_assert(N_PARAMS == FCM_MODEL_PARAMS, "parameter count");
+
+struct MlpWorkspace {
+    bool ready = false;
+    float* master = nullptr;   // FP32 parameters
+    __nv_bfloat16* wbf = nullptr;  // BF16 copies used in the products
+    float* adam_m = nullptr;
+    float* adam_v = nullptr;
+    float* grad = nullptr;
+    int64_t step = 0;
+    int bcap = 0;
+    float *xb = nullptr, *tb = nullptr, *z1 = nullptr, *a1 = nullptr, *z2 = nullptr, *a2 = nullptr, *y = nullptr,
+          *dy = nullptr, *dz2 = nullptr, *dz1 = nullptr, *loss = nullptr;
+    int* cb = nullptr;
+    int* idx = nullptr;
+    int idx_cap = 0;
+    // features of the slices of one predict call
+    float* feats = nullptr;
+    int feat_cap = 0;
+    void* hdesc_dev = nullptr;
+    int hdesc_cap = 0;
+};
+
+}  // namespace fcm
+
+namespace {
+
+__device__ __forceinline__ float gelu(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f)); }
+__device__ __forceinline__ float gelu_grad(float z) {
+    return 0.5f * (1.0f + erff(z * 0.70710678118654752f)) + z * expf(-0.5f * z * z) * 0.39894228040143268f;
+}
+
+template <typename T>
+__device__ __forceinline__ float ld(const T* p, int64_t i);
+template <>
+__device__ __forceinline__ float ld<float>(const float* p, int64_t i) {
+    return p[i];
+}
+template <>
+__device__ __forceinline__ float ld<__nv_bfloat16>(const __nv_bfloat16* p, int64_t i) {
+    return __bfloat162float(p[i]);
+}
+
+enum Epi : int { E_NONE = 0, E_BIAS = 1, E_BIAS_GELU = 2, E_GELU_GRAD = 3 };
+
+// C[m, n] = sum_k A(m, k) B(k, n), A(m, k) = A[m * as_m + k * as_k], likewise
+// B. Epilogues: + bias[n]; + bias[n] then GELU (Z and A both stored); times
+// GELU'(Z[m, n]) (backward through a GELU). 32 x 32 output tile per block,
+// 256 threads with 2 x 2 outputs each, K in steps of 32 through shared memory.
+constexpr int TT = 32;
+template <typename TA, typename TB, int EPI>
+__global__ void __launch_bounds__(256) k_gemm(const TA* __restrict__ A, int64_t as_m, int64_t as_k,
+                                              const TB* __restrict__ B, int64_t bs_k, int64_t bs_n, int M, int N,
+                                              int K, const float* __restrict__ bias, const float* __restrict__ Zin,
+                                              float* __restrict__ Cout, float* __restrict__ Aout, int ldc) {
+    __shared__ float sa[TT][TT + 1], sb[TT][TT + 1];
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const int m0 = blockIdx.y * TT, n0 = blockIdx.x * TT;
+    float acc[2][2] = {{0.f, 0.f}, {0.f, 0.f}};
+    for (int k0 = 0; k0 < K; k0 += TT) {
+        for (int t = threadIdx.x; t < TT * TT; t += 256) {
+            const int r = t / TT, c = t % TT;
+            const int m = m0 + r, k = k0 + c;
+            sa[r][c] = (m < M && k < K) ? ld<TA>(A, (int64_t)m * as_m + (int64_t)k * as_k) : 0.0f;
+            const int kk = k0 + r, n = n0 + c;
+            sb[r][c] = (kk < K && n < N) ? ld<TB>(B, (int64_t)kk * bs_k + (int64_t)n * bs_n) : 0.0f;
+        }
+        __syncthreads();
+#pragma unroll 8
+        for (int k = 0; k < TT; ++k) {
+            const float a0 = sa[ty * 2][k], a1 = sa[ty * 2 + 1][k];
+            const float b0 = sb[k][tx * 2], b1 = sb[k][tx * 2 + 1];
+            acc[0][0] = fmaf(a0, b0, acc[0][0]);
+            acc[0][1] = fmaf(a0, b1, acc[0][1]);
+            acc[1][0] = fmaf(a1, b0, acc[1][0]);
+            acc[1][1] = fmaf(a1, b1, acc[1][1]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            const int m = m0 + ty * 2 + i, n = n0 + tx * 2 + j;
+            if (m >= M || n >= N) continue;
+            float v = acc[i][j];
+            const int64_t o = (int64_t)m * ldc + n;
+            if (EPI == E_BIAS || EPI == E_BIAS_GELU) v += bias[n];
+            if (EPI == E_GELU_GRAD) v *= gelu_grad(Zin[o]);
+            Cout[o] = v;
+            if (EPI == E_BIAS_GELU) Aout[o] = gelu(v);
+        }
+}
+
+// db[n] = sum_m dZ[m, n], in a fixed order.
+__global__ void k_colsum(const float* __restrict__ dZ, int M, int N, float* __restrict__ db) {
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    float s = 0.0f;
+    for (int m = 0; m < M; ++m) s += dZ[(int64_t)m * N + n];
+    db[n] = s;
+}
+
+// Masked MSE and its gradient dY (one block, fixed-order reduction).
+__global__ void k_loss(const float* __restrict__ Y, const float* __restrict__ T, const int* __restrict__ Cs, int B,
+                       float* __restrict__ dY, float* __restrict__ loss) {
+    __shared__ float s_l[256], s_c[256];
+    float l = 0.0f, c = 0.0f;
+    for (int b = threadIdx.x; b < B; b += blockDim.x) c += (float)Cs[b];
+    s_c[threadIdx.x] = c;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) s_c[threadIdx.x] += s_c[threadIdx.x + o];
+        __syncthreads();
+    }
+    const float cnt = s_c[0];
+    for (int t = threadIdx.x; t < B * D_OUT; t += blockDim.x) {
+        const int b = t / D_OUT, j = t % D_OUT;
+        const float r = j < Cs[b] ? Y[t] - T[t] : 0.0f;
+        dY[t] = 2.0f * r / cnt;
+        l = fmaf(r, r, l);
+    }
+    s_l[threadIdx.x] = l;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) s_l[threadIdx.x] += s_l[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *loss = s_l[0] / cnt;
+}
+
+// Adam (Kingma & Ba 2015) on the FP32 master weights; refreshes the BF16 copy.
+__global__ void k_adam(float* __restrict__ w, const float* __restrict__ g, float* __restrict__ m,
+                       float* __restrict__ v, __nv_bfloat16* __restrict__ wbf, int64_t n, float lr, float b1, float b2,
+                       float eps, float c1, float c2) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.0f - b1) * gi;
+    const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    const float wi = w[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    w[i] = wi;
+    wbf[i] = __float2bfloat16_rn(wi);
+}
+
+__global__ void k_to_bf16(const float* __restrict__ w, __nv_bfloat16* __restrict__ wbf, int64_t n) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) wbf[i] = __float2bfloat16_rn(w[i]);
+}
+
+// Rows idx[r] of the feature, target and C arrays into contiguous batches.
+__global__ void k_gather(const float* __restrict__ F, const float* __restrict__ T, const int* __restrict__ Cs,
+                         const int* __restrict__ idx, int B, float* __restrict__ Fb, float* __restrict__ Tb,
+                         int* __restrict__ Cb) {
+    const int r = blockIdx.x;
+    if (r >= B) return;
+    const int64_t s = idx[r];
+    for (int t = threadIdx.x; t < D_IN; t += blockDim.x) Fb[(int64_t)r * D_IN + t] = F[s * D_IN + t];
+    if (threadIdx.x < D_OUT) Tb[(int64_t)r * D_OUT + threadIdx.x] = T[s * D_OUT + threadIdx.x];
+    if (threadIdx.x == 0) Cb[r] = Cs[s];
+}
+
+struct HistDesc {
+    const float* x;
+    int64_t n;
+    int C;
+    int pad;
+};
+
+// Features of one slice per block: 256-bin histogram of round(clip(x)) in
+// shared memory, normalised by n, then onehot(C). Non-finite pixels count in
+// no bin.
+__global__ void k_features(const HistDesc* __restrict__ d, int ns, float* __restrict__ F) {
+    __shared__ unsigned int h[D_HIST];
+    const int s = blockIdx.x;
+    if (s >= ns) return;
+    for (int b = threadIdx.x; b < D_HIST; b += blockDim.x) h[b] = 0;
+    __syncthreads();
+    const float* x = d[s].x;
+    const int64_t n = d[s].n;
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+        const float v = __ldg(x + i);
+        if (!(v == v) || fabsf(v) == __int_as_float(0x7f800000)) continue;
+        const int b = (int)fminf(fmaxf(rintf(v), 0.0f), 255.0f);
+        atomicAdd(&h[b], 1u);
+    }
+    __syncthreads();
+    const float inv = 1.0f / (float)n;
+    float* f = F + (int64_t)s * D_IN;
+    for (int b = threadIdx.x; b < D_HIST; b += blockDim.x) f[b] = (float)h[b] * inv;
+    if (threadIdx.x < D_ONE) f[D_HIST + threadIdx.x] = (threadIdx.x == d[s].C - 1) ? 1.0f : 0.0f;
+}
+
+}  // namespace
+
+#define CK(call)                                              \
+    do {                                                      \
+        cudaError_t e_ = (call);                              \
+        if (e_ != cudaSuccess) return ctx_fail(h, e_, #call); \
+    } while (0)
+
+namespace {
+
+dim3 tiles(int M, int N) { return dim3((N + TT - 1) / TT, (M + TT - 1) / TT); }
+
+int ensure_mlp(fcm_ctx* h, int bcap) {
+    if (!h->mlp) h->mlp = new MlpWorkspace();
+    MlpWorkspace* w = h->mlp;
+    if (!w->master) {
+        CK(cudaMalloc(&w->master, sizeof(float) * N_PARAMS));
+        CK(cudaMalloc(&w->wbf, sizeof(__nv_bfloat16) * N_PARAMS));
+        CK(cudaMalloc(&w->adam_m, sizeof(float) * N_PARAMS));
+        CK(cudaMalloc(&w->adam_v, sizeof(float) * N_PARAMS));
+        CK(cudaMalloc(&w->grad, sizeof(float) * N_PARAMS));
+        CK(cudaMalloc(&w->loss, sizeof(float)));
+    }
+    if (w->bcap < bcap) {
+        float** bufs[] = {&w->xb, &w->tb, &w->z1, &w->a1, &w->z2, &w->a2, &w->y, &w->dy, &w->dz2, &w->dz1};
+        const int64_t sizes[] = {D_IN, D_OUT, D_H, D_H, D_H, D_H, D_OUT, D_OUT, D_H, D_H};
+        for (int i = 0; i < 10; ++i) {
+            cudaFree(*bufs[i]);
+            *bufs[i] = nullptr;
+            CK(cudaMalloc(bufs[i], sizeof(float) * sizes[i] * bcap));
+        }
+        cudaFree(w->cb);
+        w->cb = nullptr;
+        CK(cudaMalloc(&w->cb, sizeof(int) * bcap));
+        w->bcap = bcap;
+    }
+    return 0;
+}
+
+// Forward pass of B rows of X (device, row stride D_IN) into w->y.
+int forward(fcm_ctx* h, const float* X, int B) {
+    MlpWorkspace* w = h->mlp;
+    cudaStream_t s = h->stream;
+    k_gemm<float, __nv_bfloat16, E_BIAS_GELU><<<tiles(B, D_H), 256, 0, s>>>(
+        X, D_IN, 1, w->wbf + OFF_W1, 1, D_IN, B, D_H, D_IN, w->master + OFF_B1, nullptr, w->z1, w->a1, D_H);
+    k_gemm<float, __nv_bfloat16, E_BIAS_GELU><<<tiles(B, D_H), 256, 0, s>>>(
+        w->a1, D_H, 1, w->wbf + OFF_W2, 1, D_H, B, D_H, D_H, w->master + OFF_B2, nullptr, w->z2, w->a2, D_H);
+    k_gemm<float, __nv_bfloat16, E_BIAS><<<tiles(B, D_OUT), 256, 0, s>>>(
+        w->a2, D_H, 1, w->wbf + OFF_W3, 1, D_H, B, D_OUT, D_H, w->master + OFF_B3, nullptr, w->y, nullptr, D_OUT);
+    CK(cudaGetLastError());
+    return 0;
+}
+
+// Loss and gradients (into w->grad) of B rows: X [B, D_IN], T [B, D_OUT], Cs [B].
+int backward(fcm_ctx* h, const float* X, const float* T, const int* Cs, int B) {
+    MlpWorkspace* w = h->mlp;
+    cudaStream_t s = h->stream;
+    int rc = forward(h, X, B);
+    if (rc) return rc;
+    k_loss<<<1, 256, 0, s>>>(w->y, T, Cs, B, w->dy, w->loss);
+    // layer 3: dW3 = dY^T a2, db3; dZ2 = (dY W3) * GELU'(z2)
+    k_gemm<float, float, E_NONE><<<tiles(D_OUT, D_H), 256, 0, s>>>(
+        w->dy, 1, D_OUT, w->a2, D_H, 1, D_OUT, D_H, B, nullptr, nullptr, w->grad + OFF_W3, nullptr, D_H);
+    k_colsum<<<1, 128, 0, s>>>(w->dy, B, D_OUT, w->grad + OFF_B3);
+    k_gemm<float, __nv_bfloat16, E_GELU_GRAD><<<tiles(B, D_H), 256, 0, s>>>(
+        w->dy, D_OUT, 1, w->wbf + OFF_W3, D_H, 1, B, D_H, D_OUT, nullptr, w->z2, w->dz2, nullptr, D_H);
+    // layer 2
+    k_gemm<float, float, E_NONE><<<tiles(D_H, D_H), 256, 0, s>>>(
+        w->dz2, 1, D_H, w->a1, D_H, 1, D_H, D_H, B, nullptr, nullptr, w->grad + OFF_W2, nullptr, D_H);
+    k_colsum<<<1, 128, 0, s>>>(w->dz2, B, D_H, w->grad + OFF_B2);
+    k_gemm<float, __nv_bfloat16, E_GELU_GRAD><<<tiles(B, D_H), 256, 0, s>>>(
+        w->dz2, D_H, 1, w->wbf + OFF_W2, D_H, 1, B, D_H, D_H, nullptr, w->z1, w->dz1, nullptr, D_H);
+    // layer 1
+    k_gemm<float, float, E_NONE><<<tiles(D_H, D_IN), 256, 0, s>>>(
+        w->dz1, 1, D_H, X, D_IN, 1, D_H, D_IN, B, nullptr, nullptr, w->grad + OFF_W1, nullptr, D_IN);
+    k_colsum<<<1, 128, 0, s>>>(w->dz1, B, D_H, w->grad + OFF_B1);
+    CK(cudaGetLastError());
+    return 0;
+}
+
+// splitmix64 (Steele, Lea & Flood 2014) and Box-Muller for the initial weights.
+uint64_t splitmix64(uint64_t& s) {
+    uint64_t z = (s += 0x9E3779B97F4A7C15ull);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+double uniform01(uint64_t& s) { return ((splitmix64(s) >> 11) + 0.5) * (1.0 / 9007199254740992.0); }
+
+bool device_mem(const void* p) {
+    cudaPointerAttributes a;
+    if (!p || cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+int upload_params(fcm_ctx* h, const float* host) {
+    MlpWorkspace* w = h->mlp;
+    CK(cudaMemcpyAsync(w->master, host, sizeof(float) * N_PARAMS, cudaMemcpyHostToDevice, h->stream));
+    CK(cudaMemsetAsync(w->adam_m, 0, sizeof(float) * N_PARAMS, h->stream));
+    CK(cudaMemsetAsync(w->adam_v, 0, sizeof(float) * N_PARAMS, h->stream));
+    k_to_bf16<<<(unsigned)((N_PARAMS + 255) / 256), 256, 0, h->stream>>>(w->master, w->wbf, N_PARAMS);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(h->stream));
+    w->step = 0;
+    w->ready = true;
+    return 0;
+}
+
+int need_model(fcm_ctx* h) {
+    if (!h->mlp || !h->mlp->ready) return ctx_invalid(h, "no model: call fcm_model_init, _load or _set_params");
+    return 0;
+}
+
+}  // namespace
+
+void fcm_release_mlp(fcm_ctx* h) {
+    if (!h || !h->mlp) return;
+    MlpWorkspace* w = h->mlp;
+    void* ps[] = {w->master, w->wbf, w->adam_m, w->adam_v, w->grad, w->xb, w->tb, w->z1, w->a1, w->z2,
+                  w->a2, w->y, w->dy, w->dz2, w->dz1, w->loss, w->cb, w->idx, w->feats, w->hdesc_dev};
+    for (void* p : ps) cudaFree(p);
+    delete w;
+    h->mlp = nullptr;
+}
+
+extern "C" {
+
+int fcm_model_init(fcm_handle h, uint64_t seed) {
+    if (!h) return FCM_ERR_INVALID_ARG;
+    DeviceGuard g(h->device);
+    int rc = ensure_mlp(h, 1);
+    if (rc) return rc;
+    // He-normal weights (std sqrt(2 / fan_in)), zero hidden biases, output
+    // biases spread over (0, 1) so an untrained net predicts ordered centers.
+    std::vector<float> p(N_PARAMS, 0.0f);
+    uint64_t s = seed;
+    auto fill = [&](int64_t off, int fan_out, int fan_in) {
+        const double sd = std::sqrt(2.0 / fan_in);
+        for (int64_t i = 0; i < (int64_t)fan_out * fan_in; ++i) {
+            const double u1 = uniform01(s), u2 = uniform01(s);
+            p[off + i] = (float)(sd * std::sqrt(-2.0 * std::log(u1)) * std::cos(6.283185307179586 * u2));
+        }
+    };
+    fill(OFF_W1, D_H, D_IN);
+    fill(OFF_W2, D_H, D_H);
+    fill(OFF_W3, D_OUT, D_H);
+    for (int j = 0; j < D_OUT; ++j) p[OFF_B3 + j] = (float)(j + 1) / (D_OUT + 1);
+    return upload_params(h, p.data());
+}
+
+int fcm_model_set_params(fcm_handle h, const float* params, int64_t count) {
+    if (!h || !params || count != N_PARAMS) return FCM_ERR_INVALID_ARG;
+    DeviceGuard g(h->device);
+    int rc = ensure_mlp(h, 1);
+    if (rc) return rc;
+    return upload_params(h, params);
+}
+
+int fcm_model_get_params(fcm_handle h, float* params, int64_t count) {
+    if (!h || !params || count != N_PARAMS) return FCM_ERR_INVALID_ARG;
+    int rc = need_model(h);
+    if (rc) return rc;
+    DeviceGuard g(h->device);
+    CK(cudaMemcpyAsync(params, h->mlp->master, sizeof(float) * N_PARAMS, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return FCM_OK;
+}
+
+int fcm_model_save(fcm_handle h, const char* path) {
+    if (!h || !path) return FCM_ERR_INVALID_ARG;
+    std::vector<float> p(N_PARAMS);
+    int rc = fcm_model_get_params(h, p.data(), N_PARAMS);
+    if (rc) return rc;
+    FILE* f = std::fopen(path, "wb");
+    if (!f) return ctx_invalid(h, "cannot open the model file for writing");
+    const int32_t head[5] = {0x57434D46 /* "FMCW" */, 1, D_IN, D_H, D_OUT};
+    const bool ok = std::fwrite(head, sizeof(head), 1, f) == 1 &&
+                    std::fwrite(p.data(), sizeof(float), N_PARAMS, f) == (size_t)N_PARAMS;
+    std::fclose(f);
+    return ok ? FCM_OK : ctx_invalid(h, "short write of the model file");
+}
+
+int fcm_model_load(fcm_handle h, const char* path) {
+    if (!h || !path) return FCM_ERR_INVALID_ARG;
+    FILE* f = std::fopen(path, "rb");
+    if (!f) return ctx_invalid(h, "cannot open the model file");
+    int32_t head[5];
+    std::vector<float> p(N_PARAMS);
+    const bool ok = std::fread(head, sizeof(head), 1, f) == 1 && head[0] == 0x57434D46 && head[1] == 1 &&
+                    head[2] == D_IN && head[3] == D_H && head[4] == D_OUT &&
+                    std::fread(p.data(), sizeof(float), N_PARAMS, f) == (size_t)N_PARAMS;
+    std::fclose(f);
+    if (!ok) return ctx_invalid(h, "not a model file of this network");
+    return fcm_model_set_params(h, p.data(), N_PARAMS);
+}
+
+int fcm_model_forward(fcm_handle h, const float* feats, int B, float* out) {
+    if (!h || !feats || !out || B < 1) return FCM_ERR_INVALID_ARG;
+    int rc = need_model(h);
+    if (rc) return rc;
+    if (!device_mem(feats) || !device_mem(out)) return ctx_invalid(h, "features and output must be device memory");
+    DeviceGuard g(h->device);
+    if ((rc = ensure_mlp(h, B))) return rc;
+    if ((rc = forward(h, feats, B))) return rc;
+    CK(cudaMemcpyAsync(out, h->mlp->y, sizeof(float) * B * D_OUT, cudaMemcpyDeviceToDevice, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return FCM_OK;
+}
+
+int fcm_model_loss_grad(fcm_handle h, const float* feats, const float* targets, const int* Cs, int B, float* grad,
+                        float* loss) {
+    if (!h || !feats || !targets || !Cs || B < 1 || !grad || !loss) return FCM_ERR_INVALID_ARG;
+    int rc = need_model(h);
+    if (rc) return rc;
+    if (!device_mem(feats) || !device_mem(targets) || !device_mem(Cs))
+        return ctx_invalid(h, "features, targets and C must be device memory");
+    DeviceGuard g(h->device);
+    if ((rc = ensure_mlp(h, B))) return rc;
+    if ((rc = backward(h, feats, targets, Cs, B))) return rc;
+    CK(cudaMemcpyAsync(grad, h->mlp->grad, sizeof(float) * N_PARAMS, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaMemcpyAsync(loss, h->mlp->loss, sizeof(float), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return FCM_OK;
+}
+
+int fcm_model_train(fcm_handle h, const float* feats, const float* targets, const int* Cs, int n, int epochs,
+                    int batch, float lr, uint64_t seed, float* last_loss) {
+    if (!h || !feats || !targets || !Cs || n < 1 || epochs < 1 || batch < 1 || !(lr > 0.0f))
+        return FCM_ERR_INVALID_ARG;
+    int rc = need_model(h);
+    if (rc) return rc;
+    if (!device_mem(feats) || !device_mem(targets) || !device_mem(Cs))
+        return ctx_invalid(h, "features, targets and C must be device memory");
+    DeviceGuard g(h->device);
+    batch = std::min(batch, n);
+    if ((rc = ensure_mlp(h, batch))) return rc;
+    MlpWorkspace* w = h->mlp;
+    if (w->idx_cap < n) {
+        cudaFree(w->idx);
+        w->idx = nullptr;
+        CK(cudaMalloc(&w->idx, sizeof(int) * n));
+        w->idx_cap = n;
+    }
+    std::vector<int> perm(n);
+    uint64_t s = seed;
+    const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+    double epoch_loss = 0.0;
+    float lh = 0.0f;
+    for (int e = 0; e < epochs; ++e) {
+        for (int i = 0; i < n; ++i) perm[i] = i;
+        for (int i = n - 1; i > 0; --i) std::swap(perm[i], perm[(int)(splitmix64(s) % (uint64_t)(i + 1))]);
+        CK(cudaMemcpyAsync(w->idx, perm.data(), sizeof(int) * n, cudaMemcpyHostToDevice, h->stream));
+        epoch_loss = 0.0;
+        int nb = 0;
+        for (int b0 = 0; b0 + batch <= n; b0 += batch, ++nb) {  // full batches only
+            k_gather<<<batch, 128, 0, h->stream>>>(feats, targets, Cs, w->idx + b0, batch, w->xb, w->tb, w->cb);
+            if ((rc = backward(h, w->xb, w->tb, w->cb, batch))) return rc;
+            ++w->step;
+            const float c1 = 1.0f - std::pow(b1, (float)w->step), c2 = 1.0f - std::pow(b2, (float)w->step);
+            k_adam<<<(unsigned)((N_PARAMS + 255) / 256), 256, 0, h->stream>>>(w->master, w->grad, w->adam_m,
+                                                                               w->adam_v, w->wbf, N_PARAMS, lr, b1,
+                                                                               b2, eps, c1, c2);
+            if (e == epochs - 1) {
+                CK(cudaMemcpyAsync(&lh, w->loss, sizeof(float), cudaMemcpyDeviceToHost, h->stream));
+                CK(cudaStreamSynchronize(h->stream));
+                epoch_loss += lh;
+            }
+        }
+        CK(cudaGetLastError());
+        if (e == epochs - 1 && nb > 0) epoch_loss /= nb;
+    }
+    CK(cudaStreamSynchronize(h->stream));
+    if (last_loss) *last_loss = (float)epoch_loss;
+    return FCM_OK;
+}
+
+int fcm_features(fcm_handle h, const fcm_slice* slices, int n, float* feats) {
+    if (!h || !slices || n < 1 || !feats) return FCM_ERR_INVALID_ARG;
+    if (!device_mem(feats)) return ctx_invalid(h, "features must be device memory");
+    DeviceGuard g(h->device);
+    int rc = ensure_mlp(h, 1);
+    if (rc) return rc;
+    MlpWorkspace* w = h->mlp;
+    std::vector<HistDesc> d(n);
+    for (int i = 0; i < n; ++i) {
+        if (!slices[i].x || slices[i].n < 1 || slices[i].C < 1 || slices[i].C > FCM_MAX_CLUSTERS ||
+            !device_mem(slices[i].x))
+            return ctx_invalid(h, "slice: bad x, n or C");
+        d[i] = HistDesc{slices[i].x, slices[i].n, slices[i].C, 0};
+    }
+    if (w->hdesc_cap < n) {
+        cudaFree(w->hdesc_dev);
+        w->hdesc_dev = nullptr;
+        CK(cudaMalloc(&w->hdesc_dev, sizeof(HistDesc) * n));
+        w->hdesc_cap = n;
+    }
+    CK(cudaMemcpyAsync(w->hdesc_dev, d.data(), sizeof(HistDesc) * n, cudaMemcpyHostToDevice, h->stream));
+    k_features<<<n, 512, 0, h->stream>>>((const HistDesc*)w->hdesc_dev, n, feats);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(h->stream));
+    return FCM_OK;
+}
+
+int fcm_predict_centers(fcm_handle h, fcm_slice* slices, int n) {
+    if (!h || !slices || n < 1) return FCM_ERR_INVALID_ARG;
+    int rc = need_model(h);
+    if (rc) return rc;
+    DeviceGuard g(h->device);
+    MlpWorkspace* w = h->mlp;
+    if (w->feat_cap < n) {
+        cudaFree(w->feats);
+        w->feats = nullptr;
+        CK(cudaMalloc(&w->feats, sizeof(float) * D_IN * n));
+        w->feat_cap = n;
+    }
+    if ((rc = fcm_features(h, slices, n, w->feats))) return rc;
+    if ((rc = ensure_mlp(h, n))) return rc;
+    if ((rc = forward(h, w->feats, n))) return rc;
+    std::vector<float> y((size_t)n * D_OUT);
+    CK(cudaMemcpyAsync(y.data(), w->y, sizeof(float) * D_OUT * n, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    for (int i = 0; i < n; ++i) {
+        float v[D_OUT];
+        const int C = slices[i].C;
+        for (int j = 0; j < C; ++j) v[j] = 255.0f * y[(size_t)i * D_OUT + j];
+        std::sort(v, v + C);
+        for (int j = 0; j < FCM_MAX_CLUSTERS; ++j) slices[i].V0[j] = j < C ? v[j] : 0.0f;
+        slices[i].init_mode = FCM_INIT_V;
+    }
+    return FCM_OK;
+}
+
+int fcm_run_batched_warm(fcm_handle h, fcm_slice* slices, int n, int options, int* n_cold) {
+    if (!h || !slices || n < 1) return FCM_ERR_INVALID_ARG;
+    if (n_cold) *n_cold = 0;
+    int rc = fcm_predict_centers(h, slices, n);
+    if (rc) return rc;
+    // predictions that cannot start a run go back to the cold start
+    int cold = 0;
+    for (int i = 0; i < n; ++i) {
+        fcm_slice& s = slices[i];
+        bool ok = true;
+        for (int j = 0; j < s.C; ++j) ok &= std::isfinite(s.V0[j]);
+        for (int j = 1; j < s.C && ok; ++j) ok &= s.V0[j] - s.V0[j - 1] > 1e-3f;
+        if (!ok && s.U0) {
+            s.init_mode = FCM_INIT_U;
+            ++cold;
+        }
+    }
+    const int st = fcm_run_batched(h, slices, n, options);
+    if (st == FCM_ERR_INVALID_ARG || st == FCM_ERR_CUDA || st == FCM_ERR_OOM) return st;
+    // warm runs that did not converge or emptied a cluster: rerun cold
+    std::vector<int> redo;
+    for (int i = 0; i < n; ++i) {
+        const fcm_slice& s = slices[i];
+        if (s.init_mode == FCM_INIT_V && s.U0 && (s.status != FCM_OK || (s.flags & FCM_FLAG_EMPTY_CLUSTER)))
+            redo.push_back(i);
+    }
+    int worst = st;
+    if (!redo.empty()) {
+        std::vector<fcm_slice> sub(redo.size());
+        for (size_t t = 0; t < redo.size(); ++t) {
+            sub[t] = slices[redo[t]];
+            sub[t].init_mode = FCM_INIT_U;
+        }
+        const int st2 = fcm_run_batched(h, sub.data(), (int)sub.size(), options | FCM_BATCH_NO_TUNE);
+        if (st2 == FCM_ERR_INVALID_ARG || st2 == FCM_ERR_CUDA || st2 == FCM_ERR_OOM) return st2;
+        for (size_t t = 0; t < redo.size(); ++t) slices[redo[t]] = sub[t];
+        worst = FCM_OK;
+        for (int i = 0; i < n; ++i) {
+            if (slices[i].status < 0 && worst >= 0) worst = slices[i].status;
+            if (slices[i].status == FCM_NOT_CONVERGED && worst == FCM_OK) worst = FCM_NOT_CONVERGED;
+        }
+    }
+    if (n_cold) *n_cold = cold + (int)redo.size();
+    return worst;
+}
+
+}  // extern "C"

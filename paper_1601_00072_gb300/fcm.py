@@ -71,6 +71,7 @@ class Slice:
     delta: float = 0.0
     J: float = 0.0
     V64: np.ndarray | None = None
+    init: str = ""
 
 
 class FCM:
@@ -184,11 +185,8 @@ class FCM:
                                            ctypes.byref(ms)), self._h)
         return ms.value
 
-    def run_batched(self, slices, tune: bool = True, retune: bool = False, graph: bool = True,
-                    raise_on_error: bool = False) -> int:
-        """Algorithm 1 on every slice in one persistent launch (see
-        ``fcm_run_batched``). Fills each Slice's U, V and result fields and
-        returns the aggregate status."""
+    @staticmethod
+    def _c_slices(slices):
         import torch
         arr = (_lib.fcm_slice * len(slices))()
         for i, s in enumerate(slices):
@@ -200,24 +198,119 @@ class FCM:
             a = arr[i]
             a.x, a.n, a.C, a.m, a.eps, a.max_iter = _ptr(s.x), n, s.C, s.m, s.eps, s.max_iter
             a.U, a.V = _ptr(s.U), _ptr(s.V)
+            a.U0 = None if s.U0 is None else _ptr(s.U0)
             if s.V0 is not None:
                 a.init_mode = _lib.FCM_INIT_V
                 for j, vj in enumerate(np.asarray(s.V0, dtype=np.float64).reshape(-1)[:s.C]):
                     a.V0[j] = float(vj)
             else:
                 a.init_mode = _lib.FCM_INIT_U
-                a.U0 = None if s.U0 is None else _ptr(s.U0)
-        opts = ((0 if tune else _lib.FCM_BATCH_NO_TUNE) | (_lib.FCM_BATCH_RETUNE if retune else 0)
-                | (0 if graph else _lib.FCM_BATCH_NO_GRAPH))
-        self._bind_stream()
-        st = self._lib.fcm_run_batched(self._h, arr, len(slices), opts)
-        if st == _lib.FCM_ERR_INVALID_ARG or st == _lib.FCM_ERR_CUDA or st == _lib.FCM_ERR_OOM or raise_on_error:
-            _lib.check(st, self._h)
+        return arr
+
+    @staticmethod
+    def _read_back(arr, slices):
         for i, s in enumerate(slices):
             a = arr[i]
             s.iters, s.status, s.flags, s.delta, s.J = a.iters, a.status, a.flags, a.delta, a.J
             s.V64 = np.array(a.V64[:s.C])
+            s.init = "V" if a.init_mode == _lib.FCM_INIT_V else "U"
+
+    def _batch_opts(self, tune, retune, graph):
+        return ((0 if tune else _lib.FCM_BATCH_NO_TUNE) | (_lib.FCM_BATCH_RETUNE if retune else 0)
+                | (0 if graph else _lib.FCM_BATCH_NO_GRAPH))
+
+    def run_batched(self, slices, tune: bool = True, retune: bool = False, graph: bool = True,
+                    raise_on_error: bool = False) -> int:
+        """Algorithm 1 on every slice in one persistent launch (see
+        ``fcm_run_batched``). Fills each Slice's U, V and result fields and
+        returns the aggregate status."""
+        arr = self._c_slices(slices)
+        self._bind_stream()
+        st = self._lib.fcm_run_batched(self._h, arr, len(slices), self._batch_opts(tune, retune, graph))
+        if st in (_lib.FCM_ERR_INVALID_ARG, _lib.FCM_ERR_CUDA, _lib.FCM_ERR_OOM) or raise_on_error:
+            _lib.check(st, self._h)
+        self._read_back(arr, slices)
         return st
+
+    def run_batched_warm(self, slices, tune: bool = True, retune: bool = False, graph: bool = True):
+        """Warm-started batch (``fcm_run_batched_warm``): predicted V^0, with the
+        plain cold start (each slice's U0) as the fallback. Returns
+        (status, number of slices that ran cold). ``s.init`` tells which."""
+        arr = self._c_slices(slices)
+        cold = ctypes.c_int(0)
+        self._bind_stream()
+        st = self._lib.fcm_run_batched_warm(self._h, arr, len(slices), self._batch_opts(tune, retune, graph),
+                                            ctypes.byref(cold))
+        if st in (_lib.FCM_ERR_INVALID_ARG, _lib.FCM_ERR_CUDA, _lib.FCM_ERR_OOM):
+            _lib.check(st, self._h)
+        self._read_back(arr, slices)
+        for i, s in enumerate(slices):
+            s.V0 = np.array(arr[i].V0[:s.C]) if arr[i].init_mode == _lib.FCM_INIT_V else s.V0
+        return st, cold.value
+
+    # ---- warm-start network ------------------------------------------------
+
+    def model_init(self, seed: int = 0):
+        _lib.check(self._lib.fcm_model_init(self._h, int(seed)), self._h)
+
+    def model_params(self) -> np.ndarray:
+        p = np.empty(_lib.FCM_MODEL_PARAMS, dtype=np.float32)
+        _lib.check(self._lib.fcm_model_get_params(self._h, p.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                                                  p.size), self._h)
+        return p
+
+    def set_model_params(self, params):
+        p = np.ascontiguousarray(params, dtype=np.float32).reshape(-1)
+        _lib.check(self._lib.fcm_model_set_params(self._h, p.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                                                  p.size), self._h)
+
+    def model_save(self, path: str):
+        _lib.check(self._lib.fcm_model_save(self._h, str(path).encode()), self._h)
+
+    def model_load(self, path: str):
+        _lib.check(self._lib.fcm_model_load(self._h, str(path).encode()), self._h)
+
+    def features(self, slices):
+        """Network inputs [n, 264] (CUDA tensor) of the slices' x and C."""
+        import torch
+        arr = self._c_slices(slices)
+        out = torch.empty((len(slices), _lib.MODEL_D_IN), dtype=torch.float32, device=slices[0].x.device)
+        self._bind_stream()
+        _lib.check(self._lib.fcm_features(self._h, arr, len(slices), _ptr(out)), self._h)
+        return out
+
+    def model_forward(self, feats):
+        import torch
+        out = torch.empty((feats.shape[0], _lib.MODEL_D_OUT), dtype=torch.float32, device=feats.device)
+        self._bind_stream()
+        _lib.check(self._lib.fcm_model_forward(self._h, _ptr(feats), feats.shape[0], _ptr(out)), self._h)
+        return out
+
+    def model_loss_grad(self, feats, targets, Cs):
+        g = np.empty(_lib.FCM_MODEL_PARAMS, dtype=np.float32)
+        loss = ctypes.c_float(0.0)
+        self._bind_stream()
+        _lib.check(self._lib.fcm_model_loss_grad(
+            self._h, _ptr(feats), _ptr(targets), ctypes.c_void_p(Cs.data_ptr()), feats.shape[0],
+            g.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), ctypes.byref(loss)), self._h)
+        return loss.value, g
+
+    def model_train(self, feats, targets, Cs, epochs: int, batch: int = 256, lr: float = 1e-3,
+                    seed: int = 0) -> float:
+        loss = ctypes.c_float(0.0)
+        self._bind_stream()
+        _lib.check(self._lib.fcm_model_train(self._h, _ptr(feats), _ptr(targets), ctypes.c_void_p(Cs.data_ptr()),
+                                             feats.shape[0], int(epochs), int(batch), float(lr), int(seed),
+                                             ctypes.byref(loss)), self._h)
+        return loss.value
+
+    def predict_centers(self, slices):
+        """Sets each slice's V0 to the network's prediction."""
+        arr = self._c_slices(slices)
+        self._bind_stream()
+        _lib.check(self._lib.fcm_predict_centers(self._h, arr, len(slices)), self._h)
+        for i, s in enumerate(slices):
+            s.V0 = np.array(arr[i].V0[:s.C])
 
     def batched_plan(self) -> dict:
         p = _lib.fcm_batch_plan()
