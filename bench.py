@@ -15,6 +15,13 @@ steps.
 With ``--gpus N`` under torchrun every rank runs its own copy of the workload
 (weak scaling; the pass has no cross-GPU exchange when images are independent).
 
+The line also carries ``batched``: images/s of the 512-slice batch (sides
+log-uniform 64..512, C in {3, 4, 5}, m = 2, eps = 1e-5) run cold (seeded
+Dirichlet U0, one persistent launch in a CUDA graph) and warm (the shipped
+network predicts V^0), each with inputs resident in HBM. A warm slice that
+fails the acceptance rule (centers within 1e-4 of the cold start's, or a final
+J no larger) is charged the time of its cold run on top.
+
 ``--impl reference`` times the FP64 CPU oracle instead, on a bounded sample of
 the same workload (rank 0 only).
 """
@@ -227,6 +234,75 @@ def cpu_baseline_leg(x, u0, m, gV, gU_sample, idx, g_iters, g_J):
     return base, prec
 
 
+def batch_inputs(dev, n=512):
+    """Device-resident x and U0 of the batch slices (generated in spawned
+    worker processes)."""
+    import torch
+    from paper_1601_00072_gb300 import warmstart
+    xs, u0s, Cs = [], [], []
+    for part in warmstart.slices_of(range(n), 1):
+        for _, Cj, x, u0 in part:
+            xs.append(torch.from_numpy(x.astype(np.float32)).to(dev))
+            u0s.append(torch.from_numpy(u0[0]).to(dev))
+            Cs.append(Cj)
+    return xs, u0s, Cs
+
+
+def bench_batched(h, dev, steps, warmup):
+    """Cold versus warm-started batch, timed with CUDA events on the launching
+    stream (each call returns after its results are read back)."""
+    import torch
+    from paper_1601_00072_gb300 import warmstart
+    from paper_1601_00072_gb300.fcm import Batch, Slice
+    xs, u0s, Cs = batch_inputs(dev)
+    n_img = len(xs)
+    px = sum(int(x.numel()) for x in xs)
+    cold = [Slice(x=x, C=c, U0=u) for x, c, u in zip(xs, Cs, u0s)]
+    h.model_load(warmstart.MODEL_PATH)
+    stream = torch.cuda.current_stream(dev)
+
+    def timed(fn, reps):
+        for _ in range(warmup):
+            fn()
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        return e0.elapsed_time(e1) / reps
+
+    cold = Batch(cold)
+    ms_cold = timed(lambda: h.run_batched(cold), steps)
+    warm = Batch([Slice(x=x, C=c, U0=u) for x, c, u in zip(xs, Cs, u0s)])
+    n_ran_cold = [0]
+
+    def run_warm():
+        n_ran_cold[0] = h.run_batched_warm(warm)[1]
+
+    ms_warm = timed(run_warm, steps)
+    ok = warmstart.accepted(cold.slices, warm.slices)
+    bad = Batch([Slice(x=xs[i], C=Cs[i], U0=u0s[i]) for i in np.flatnonzero(~ok)]) if not ok.all() else None
+    ms_charge = timed(lambda: h.run_batched(bad, tune=False), max(1, steps // 4)) if bad else 0.0
+    it_c = np.array([s.iters for s in cold.slices])
+    it_w = np.array([s.iters for s in warm.slices])
+    cold_ips = n_img / (ms_cold / 1e3)
+    warm_ips = n_img / ((ms_warm + ms_charge) / 1e3)
+    return {
+        "workload": "512 phantom slices, sides log-uniform 64..512, C in {3,4,5}, m=2, eps=1e-5, max_iter=300",
+        "pixels": px, "steps": steps,
+        "cold": {"images_per_s": cold_ips, "ms": ms_cold, "mean_iters": float(it_c.mean()),
+                 "max_iters": int(it_c.max()),
+                 "pixel_iter_per_s": sum(int(x.numel()) * int(i) for x, i in zip(xs, it_c)) / (ms_cold / 1e3)},
+        "warm": {"images_per_s": warm_ips, "ms": ms_warm, "charged_ms": ms_charge,
+                 "mean_iters": float(it_w.mean()), "max_iters": int(it_w.max()),
+                 "accepted": float(ok.mean()), "ran_cold_at_run_time": int(n_ran_cold[0])},
+        "warm_over_cold": warm_ips / cold_ips,
+        "plan": h.batched_plan(),
+    }
+
+
 def bench_ours(args):
     import torch
 
@@ -341,6 +417,8 @@ def bench_ours(args):
         "clocks": clocks,
         "e2e": e2e,
     }
+    if not args.no_batched:
+        out["batched"] = bench_batched(h, dev, max(3, min(args.steps, 20)), 3)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         idx = np.random.default_rng(0).choice(n, 100_000, replace=False)
         gU_sample = Ud[:, torch.from_numpy(idx).to(dev)].cpu().numpy().astype(np.float64)
@@ -401,6 +479,7 @@ def main():
     ap.add_argument("--m", type=float, default=2.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-batched", action="store_true", help="skip the cold versus warm batch measurement")
     ap.add_argument("--variant", choices=["tma", "ldg"], default="tma",
                     help="pass kernel: TMA-fed ring (default) or plain loads")
     ap.add_argument("--no-graph", action="store_true",

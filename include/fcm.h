@@ -175,12 +175,19 @@ typedef struct {
     double V64[FCM_MAX_CLUSTERS];
 } fcm_slice;
 
-/* Launch shape of the batched kernel (see fcm_run_batched). */
+/* Launch shape of the batched kernels (see fcm_run_batched). */
+#define FCM_SCHED_SLICES 0 /* slices from a queue, one CTA or one cluster each     */
+#define FCM_SCHED_ROUNDS 1 /* every slice steps each round; pixels tiled over the grid */
 typedef struct {
-    int block;      /* threads per CTA: 256 or 512                           */
-    int cluster;    /* CTAs per thread-block cluster: 1, 2, 4 or 8            */
-    int64_t big;    /* slices with n >= big are shared by a whole cluster     */
-    double ms;      /* measured batch time when the autotuner chose it, or 0  */
+    int block;      /* threads per CTA: 256 or 512                                   */
+    int cluster;    /* FCM_SCHED_SLICES: CTAs per thread-block cluster, 1, 2, 4 or 8; */
+                    /* FCM_SCHED_ROUNDS: 1                                            */
+    int64_t big;    /* FCM_SCHED_SLICES: slices with n >= big are shared by a whole  */
+                    /* cluster; FCM_SCHED_ROUNDS: unused (0)                          */
+    double ms;      /* measured batch time when the autotuner chose it, or 0          */
+    int schedule;   /* FCM_SCHED_SLICES or FCM_SCHED_ROUNDS                           */
+    int tile;       /* FCM_SCHED_ROUNDS: fewest pixels one CTA takes in a round,      */
+                    /* 1024 to 65536, a multiple of 1024; FCM_SCHED_SLICES: 0         */
 } fcm_batch_plan;
 
 /* Batch options (bit flags). */
@@ -190,24 +197,36 @@ typedef struct {
 
 /*
  * fcm_run_batched — Algorithm 1 on each of n_slices slices, in one persistent
- * launch captured in a CUDA graph. Slices are taken from a work queue in
- * order of decreasing size; slices with n >= plan.big are shared by the CTAs
- * of a thread-block cluster (per-iteration sums exchanged through distributed
- * shared memory), smaller ones run one per CTA. Memberships U^{k-1} are
- * recomputed from V^{k-1} rather than stored, so each iteration reads only x.
+ * launch captured in a CUDA graph. Memberships U^{k-1} are recomputed from
+ * V^{k-1} rather than stored, so each iteration reads only x; U^k is written
+ * once, after the last iteration. Two schedules:
+ *
+ *   FCM_SCHED_SLICES  slices are taken from a work queue in order of
+ *                     decreasing size; slices with n >= plan.big are shared by
+ *                     the CTAs of a thread-block cluster (per-iteration sums
+ *                     exchanged through distributed shared memory), smaller
+ *                     ones run one per CTA.
+ *   FCM_SCHED_ROUNDS  a cooperative launch; round k is iteration k of every
+ *                     slice still running, the pixels of those slices cut
+ *                     into one equal contiguous chunk per CTA (at least
+ *                     plan.tile pixels), with a grid barrier between rounds.
+ *                     Slices that need many iterations then use the whole GPU
+ *                     instead of a few SMs. At most 8192 slices.
  *
  * The launch shape comes from an autotuner: on the first batch of a new
  * "bucket" (device, set of C values, and the powers of two of the slice
- * count, total pixels and largest slice), it times each candidate shape on
- * the batch itself and keeps the fastest, in memory and, when the environment
- * variable FCM_AUTOTUNE_CACHE names a file, in that JSON file. Tuning runs the
- * batch several times, so it is skipped (default plan) when a slice updates
- * its initial memberships in place (FCM_INIT_U with U0 NULL or equal to U).
+ * count, total pixels and largest slice), it times each candidate shape of
+ * both schedules on the batch itself and keeps the fastest, in memory and,
+ * when the environment variable FCM_AUTOTUNE_CACHE names a file, in that JSON
+ * file. Tuning runs the batch several times, so it is skipped (default plan)
+ * when a slice updates its initial memberships in place (FCM_INIT_U with U0
+ * NULL or equal to U).
  *
  * Returns FCM_OK if every slice converged, FCM_NOT_CONVERGED if some slice
  * stopped at max_iter, the first negative status of a failed slice, or an
  * error of the whole call (FCM_ERR_INVALID_ARG names no slice then). Per-slice
- * results are in the structs.
+ * results are in the structs. A slice whose run was cut short by a bounded
+ * wait of the round schedule giving up reports FCM_ERR_TIMEOUT.
  */
 int fcm_run_batched(fcm_handle h, fcm_slice* slices, int n_slices, int options);
 

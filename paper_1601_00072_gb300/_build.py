@@ -3,7 +3,8 @@
 Every translation unit is compiled by its own ``nvcc -c`` process, in
 parallel, then linked with ``nvcc -shared``. The single-image pass source is
 compiled eight times, once per cluster count (``-DFCM_INST_C=1..8``), and the
-batched kernel twice, once per block size (``-DFCM_BATCH_NT=256, 512``).
+two batched kernels twice each, once per block size (``-DFCM_BATCH_NT`` and
+``-DFCM_ROUNDS_NT`` = 256, 512).
 Nothing is rebuilt when the library is newer than every source.
 """
 from __future__ import annotations
@@ -43,6 +44,9 @@ def _units():
         elif base == "fcm_batched_inst":
             for nt in (256, 512):
                 units.append((src, os.path.join(BUILD, f"{base}_nt{nt}.o"), [f"-DFCM_BATCH_NT={nt}"]))
+        elif base == "fcm_rounds_inst":
+            for nt in (256, 512):
+                units.append((src, os.path.join(BUILD, f"{base}_nt{nt}.o"), [f"-DFCM_ROUNDS_NT={nt}"]))
         else:
             units.append((src, os.path.join(BUILD, base + ".o"), []))
     return units

@@ -49,7 +49,11 @@ class fcm_slice(ctypes.Structure):
 
 class fcm_batch_plan(ctypes.Structure):
     _fields_ = [("block", ctypes.c_int), ("cluster", ctypes.c_int), ("big", ctypes.c_int64),
-                ("ms", ctypes.c_double)]
+                ("ms", ctypes.c_double), ("schedule", ctypes.c_int), ("tile", ctypes.c_int)]
+
+
+FCM_SCHED_SLICES = 0
+FCM_SCHED_ROUNDS = 1
 
 
 FCM_BATCH_RETUNE = 16

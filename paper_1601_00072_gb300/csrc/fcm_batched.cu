@@ -1,10 +1,12 @@
-// Host runtime of the batched FCM path: argument checks, LPT work order,
-// launch-shape autotuner with its cache, and the CUDA graph of a batch.
+// Host runtime of the batched FCM path: argument checks, LPT work order, the
+// tiling of the round schedule, the launch-shape autotuner with its cache, and
+// the CUDA graph of a batch.
 //
 // A batch is one persistent kernel launch. Its graph holds, in order: the
-// upload of the slice descriptors and of the work order (from pinned host
-// buffers the handle refills before each launch), the reset of the work-queue
-// head, the kernel (a thread-block-cluster launch), and the download of the
+// upload of the slice descriptors and of the work order or tiling (from pinned
+// host buffers the handle refills before each launch), the reset of the
+// kernel's control state, the kernel (a thread-block-cluster launch, or a
+// cooperative launch for the round schedule), and the download of the
 // per-slice results. The graph is instantiated once per (slice count, plan).
 #include <cuda_runtime.h>
 
@@ -17,6 +19,7 @@
 #include <numeric>
 #include <string>
 #include <tuple>
+#include <unordered_set>
 #include <vector>
 
 #include "fcm.h"
@@ -38,13 +41,27 @@ struct BatchedWorkspace {
     SliceResult* h_res = nullptr;  // pinned
     int* h_order = nullptr;        // pinned
     cudaStream_t cap_stream = nullptr;
-    std::map<std::tuple<int, int, int, int64_t>, GraphEntry> graphs;
+    // round schedule: per-slice state, control block, batch sizes, first slot
+    // of each slice, and the slot partials (capacity in slots)
+    RoundSlice* d_rstate = nullptr;
+    RoundCtl* d_rctl = nullptr;
+    RoundsHdr* d_rhdr = nullptr;
+    RoundsHdr* h_rhdr = nullptr;  // pinned
+    int* d_slot_base = nullptr;
+    int* h_slot_base = nullptr;   // pinned, cap + 1
+    int64_t slot_cap = 0;
+    double* d_rpart = nullptr;
+    std::map<std::tuple<int, int, int, int64_t, int, int>, GraphEntry> graphs;
     std::map<std::string, fcm_batch_plan> plans;
     bool cache_loaded = false;
     bool forced = false;
     fcm_batch_plan forced_plan{};
     fcm_batch_plan last{};
     std::map<std::pair<int, int>, int> grid;  // (block, cluster) -> CTAs of a full persistent grid
+    // device pointers already checked by this handle (the check is a driver
+    // call per pointer; repeated batches reuse their buffers)
+    std::unordered_set<const void*> known_device;
+    std::map<std::pair<int, int>, int> rgrid;  // (block, shared bytes) -> CTAs of a cooperative round grid
 };
 
 }  // namespace fcm
@@ -58,6 +75,14 @@ struct BatchedWorkspace {
 namespace {
 
 BatchKernel kernel_for(int block) { return block == 256 ? batched_kernel_256() : batched_kernel_512(); }
+RoundsKernel rounds_for(int block) { return block == 256 ? rounds_kernel_256() : rounds_kernel_512(); }
+
+bool plan_valid(const fcm_batch_plan& p) {
+    if (p.block != 256 && p.block != 512) return false;
+    if (p.schedule == FCM_SCHED_ROUNDS) return p.tile >= 1024 && p.tile <= 65536 && p.tile % 1024 == 0;
+    if (p.schedule != FCM_SCHED_SLICES) return false;
+    return (p.cluster == 1 || p.cluster == 2 || p.cluster == 4 || p.cluster == 8) && p.big >= 1;
+}
 
 void free_graphs(BatchedWorkspace* w) {
     for (auto& kv : w->graphs) {
@@ -72,29 +97,64 @@ int ensure_batched(fcm_ctx* h, int n) {
     BatchedWorkspace* w = h->batched;
     if (!w->cap_stream) CK(cudaStreamCreateWithFlags(&w->cap_stream, cudaStreamNonBlocking));
     if (!w->d_ctl) CK(cudaMalloc(&w->d_ctl, sizeof(BatchCtl)));
+    if (!w->d_rctl) CK(cudaMalloc(&w->d_rctl, sizeof(RoundCtl)));
+    if (!w->d_rhdr) CK(cudaMalloc(&w->d_rhdr, sizeof(RoundsHdr)));
+    if (!w->h_rhdr) CK(cudaMallocHost(&w->h_rhdr, sizeof(RoundsHdr)));
     if (w->cap >= n) return 0;
     free_graphs(w);  // graphs point at the old buffers
-    cudaFree(w->d_desc);
-    cudaFree(w->d_res);
-    cudaFree(w->d_order);
-    cudaFreeHost(w->h_desc);
-    cudaFreeHost(w->h_res);
-    cudaFreeHost(w->h_order);
+    void* dev[] = {w->d_desc, w->d_res, w->d_order, w->d_rstate, w->d_slot_base};
+    for (void* p : dev) cudaFree(p);
+    void* host[] = {w->h_desc, w->h_res, w->h_order, w->h_slot_base};
+    for (void* p : host) cudaFreeHost(p);
     w->d_desc = nullptr;
     w->d_res = nullptr;
     w->d_order = nullptr;
+    w->d_rstate = nullptr;
+    w->d_slot_base = nullptr;
     w->h_desc = nullptr;
     w->h_res = nullptr;
     w->h_order = nullptr;
+    w->h_slot_base = nullptr;
     w->cap = 0;
     const int cap = std::max(n, 64);
     CK(cudaMalloc(&w->d_desc, sizeof(SliceDesc) * cap));
     CK(cudaMalloc(&w->d_res, sizeof(SliceResult) * cap));
     CK(cudaMalloc(&w->d_order, sizeof(int) * cap));
+    CK(cudaMalloc(&w->d_rstate, sizeof(RoundSlice) * cap));
+    CK(cudaMalloc(&w->d_slot_base, sizeof(int) * (cap + 1)));
     CK(cudaMallocHost(&w->h_desc, sizeof(SliceDesc) * cap));
     CK(cudaMallocHost(&w->h_res, sizeof(SliceResult) * cap));
     CK(cudaMallocHost(&w->h_order, sizeof(int) * cap));
+    CK(cudaMallocHost(&w->h_slot_base, sizeof(int) * (cap + 1)));
     w->cap = cap;
+    return 0;
+}
+
+// First slot of every slice for a plan's minimum chunk, and the round bound,
+// into the pinned buffers; grows the slot partials when needed.
+int fill_slots(fcm_ctx* h, const fcm_slice* slices, int n, int min_chunk) {
+    BatchedWorkspace* w = h->batched;
+    if (n > ROUND_MAX_SLICES) return ctx_invalid(h, "the round schedule takes at most 8192 slices");
+    int64_t total = 0;
+    int max_iter = 1;
+    for (int i = 0; i < n; ++i) {
+        w->h_slot_base[i] = (int)total;
+        total += round_slots(slices[i].n, min_chunk);
+        if (total >= ((int64_t)1 << 31) / ROUND_SUMS) return ctx_invalid(h, "batch too large for the round schedule");
+        max_iter = std::max(max_iter, slices[i].max_iter);
+    }
+    w->h_slot_base[n] = (int)total;
+    w->h_rhdr->n_slices = n;
+    w->h_rhdr->max_rounds = max_iter + 1;
+    if (w->slot_cap < total) {
+        free_graphs(w);  // graphs point at the old buffer
+        cudaFree(w->d_rpart);
+        w->d_rpart = nullptr;
+        w->slot_cap = 0;
+        const int64_t cap = std::max<int64_t>(total + total / 4, 4096);
+        CK(cudaMalloc(&w->d_rpart, sizeof(double) * ROUND_SUMS * cap));
+        w->slot_cap = cap;
+    }
     return 0;
 }
 
@@ -133,7 +193,74 @@ int grid_ctas(fcm_ctx* h, int block, int cluster) {
     return ctas;
 }
 
+int round_smem(int n_slices) { return (int)sizeof(int64_t) * (n_slices + 1); }
+
+// CTAs of a full cooperative grid of the round kernel (0 if it cannot run).
+int round_ctas(fcm_ctx* h, int block, int smem) {
+    BatchedWorkspace* w = h->batched;
+    auto it = w->rgrid.find({block, smem});
+    if (it != w->rgrid.end()) return it->second;
+    const void* fn = (const void*)rounds_for(block).fn;
+    int nb = 0;
+    if (!h->coop || cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, block, smem) != cudaSuccess)
+        nb = 0;
+    cudaGetLastError();
+    w->rgrid[{block, smem}] = nb * h->num_sms;
+    return nb * h->num_sms;
+}
+
+int launch_rounds(fcm_ctx* h, cudaStream_t s, const fcm_batch_plan& p, int n_slices) {
+    BatchedWorkspace* w = h->batched;
+    const RoundsKernel k = rounds_for(p.block);
+    const int smem = round_smem(n_slices);
+    const int ctas = round_ctas(h, p.block, smem);
+    if (ctas < 1) {
+        h->last_error = "the round schedule needs cooperative launch support";
+        return FCM_ERR_CUDA;
+    }
+    k.init<<<(n_slices + 255) / 256, 256, 0, s>>>(w->d_rstate, w->d_res, w->d_rctl, n_slices);
+    CK(cudaGetLastError());
+    RoundsArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.descs = w->d_desc;
+    a.results = w->d_res;
+    a.state = w->d_rstate;
+    a.ctl = w->d_rctl;
+    a.hdr = w->d_rhdr;
+    a.slot_base = w->d_slot_base;
+    a.partials = w->d_rpart;
+    a.min_chunk = p.tile;
+    cudaLaunchConfig_t cfg;
+    std::memset(&cfg, 0, sizeof(cfg));
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.gridDim = dim3(ctas);
+    cfg.blockDim = dim3(p.block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    CK(cudaLaunchKernelEx(&cfg, k.fn, a));
+    return 0;
+}
+
+// Uploads of one batch's work description (descriptors, order or tiling).
+int upload_batch(fcm_ctx* h, cudaStream_t s, const fcm_batch_plan& p, int n) {
+    BatchedWorkspace* w = h->batched;
+    CK(cudaMemcpyAsync(w->d_desc, w->h_desc, sizeof(SliceDesc) * n, cudaMemcpyHostToDevice, s));
+    if (p.schedule == FCM_SCHED_ROUNDS) {
+        CK(cudaMemcpyAsync(w->d_rhdr, w->h_rhdr, sizeof(RoundsHdr), cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(w->d_slot_base, w->h_slot_base, sizeof(int) * (n + 1), cudaMemcpyHostToDevice, s));
+    } else {
+        CK(cudaMemcpyAsync(w->d_order, w->h_order, sizeof(int) * n, cudaMemcpyHostToDevice, s));
+    }
+    return 0;
+}
+
 int launch_kernel(fcm_ctx* h, cudaStream_t s, const fcm_batch_plan& p, int n_slices) {
+    if (p.schedule == FCM_SCHED_ROUNDS) return launch_rounds(h, s, p, n_slices);
     BatchedWorkspace* w = h->batched;
     const BatchKernel k = kernel_for(p.block);
     const int ctas = grid_ctas(h, p.block, p.cluster);
@@ -177,17 +304,21 @@ void load_cache(BatchedWorkspace* w) {
     if (path.empty()) return;
     FILE* f = std::fopen(path.c_str(), "r");
     if (!f) return;
-    // One entry per line: "<key>": {"block": B, "cluster": K, "big": G, "ms": T},
+    // One entry per line:
+    // "<key>": {"block": B, "cluster": K, "big": G, "ms": T, "schedule": S, "tile": L},
     char line[1024];
     while (std::fgets(line, sizeof(line), f)) {
         char key[512];
-        int block = 0, cluster = 0;
+        int block = 0, cluster = 0, schedule = 0, tile = 0;
         long long big = 0;
         double ms = 0;
-        if (std::sscanf(line, " \"%511[^\"]\": {\"block\": %d, \"cluster\": %d, \"big\": %lld, \"ms\": %lf",
-                        key, &block, &cluster, &big, &ms) == 5 &&
-            (block == 256 || block == 512) && (cluster == 1 || cluster == 2 || cluster == 4 || cluster == 8))
-            w->plans[key] = fcm_batch_plan{block, cluster, (int64_t)big, ms};
+        if (std::sscanf(line,
+                        " \"%511[^\"]\": {\"block\": %d, \"cluster\": %d, \"big\": %lld, \"ms\": %lf, "
+                        "\"schedule\": %d, \"tile\": %d",
+                        key, &block, &cluster, &big, &ms, &schedule, &tile) == 7) {
+            const fcm_batch_plan p{block, cluster, (int64_t)big, ms, schedule, tile};
+            if (plan_valid(p)) w->plans[key] = p;
+        }
     }
     std::fclose(f);
 }
@@ -201,9 +332,11 @@ void save_cache(BatchedWorkspace* w) {
     std::fprintf(f, "{\n");
     size_t i = 0;
     for (auto& kv : w->plans) {
-        std::fprintf(f, "  \"%s\": {\"block\": %d, \"cluster\": %d, \"big\": %lld, \"ms\": %.4f}%s\n",
-                     kv.first.c_str(), kv.second.block, kv.second.cluster, (long long)kv.second.big,
-                     kv.second.ms, ++i < w->plans.size() ? "," : "");
+        std::fprintf(f,
+                     "  \"%s\": {\"block\": %d, \"cluster\": %d, \"big\": %lld, \"ms\": %.4f, "
+                     "\"schedule\": %d, \"tile\": %d}%s\n",
+                     kv.first.c_str(), kv.second.block, kv.second.cluster, (long long)kv.second.big, kv.second.ms,
+                     kv.second.schedule, kv.second.tile, ++i < w->plans.size() ? "," : "");
     }
     std::fprintf(f, "}\n");
     std::fclose(f);
@@ -233,7 +366,7 @@ std::string bucket_key(fcm_ctx* h, const fcm_slice* s, int n) {
     return buf;
 }
 
-fcm_batch_plan default_plan() { return fcm_batch_plan{512, 4, 65536, 0.0}; }
+fcm_batch_plan default_plan() { return fcm_batch_plan{512, 4, 65536, 0.0, FCM_SCHED_SLICES, 0}; }
 
 }  // namespace
 
@@ -245,9 +378,13 @@ void fcm_release_batched(fcm_ctx* h) {
     cudaFree(w->d_res);
     cudaFree(w->d_order);
     cudaFree(w->d_ctl);
+    void* dev[] = {w->d_rstate, w->d_rctl, w->d_rhdr, w->d_slot_base, w->d_rpart};
+    for (void* p : dev) cudaFree(p);
     cudaFreeHost(w->h_desc);
     cudaFreeHost(w->h_res);
     cudaFreeHost(w->h_order);
+    void* host[] = {w->h_rhdr, w->h_slot_base};
+    for (void* p : host) cudaFreeHost(p);
     if (w->cap_stream) cudaStreamDestroy(w->cap_stream);
     delete w;
     h->batched = nullptr;
@@ -270,22 +407,20 @@ int run_once(fcm_ctx* h, const fcm_batch_plan& p, int n, bool use_graph) {
     BatchedWorkspace* w = h->batched;
     int rc;
     if (!use_graph) {
-        CK(cudaMemcpyAsync(w->d_desc, w->h_desc, sizeof(SliceDesc) * n, cudaMemcpyHostToDevice, h->stream));
-        CK(cudaMemcpyAsync(w->d_order, w->h_order, sizeof(int) * n, cudaMemcpyHostToDevice, h->stream));
+        if ((rc = upload_batch(h, h->stream, p, n))) return rc;
         if ((rc = launch_kernel(h, h->stream, p, n))) return rc;
         CK(cudaMemcpyAsync(w->h_res, w->d_res, sizeof(SliceResult) * n, cudaMemcpyDeviceToHost, h->stream));
         CK(cudaStreamSynchronize(h->stream));
         return 0;
     }
-    const auto key = std::make_tuple(n, p.block, p.cluster, p.big);
+    const auto key = std::make_tuple(n, p.block, p.cluster, p.big, p.schedule, p.tile);
     auto it = w->graphs.find(key);
     if (it == w->graphs.end()) {
         cudaStream_t s = w->cap_stream;
         CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-        cudaError_t e = cudaMemcpyAsync(w->d_desc, w->h_desc, sizeof(SliceDesc) * n, cudaMemcpyHostToDevice, s);
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(w->d_order, w->h_order, sizeof(int) * n, cudaMemcpyHostToDevice, s);
-        int lrc = e == cudaSuccess ? launch_kernel(h, s, p, n) : 0;
+        cudaError_t e = cudaSuccess;
+        int lrc = upload_batch(h, s, p, n);
+        if (lrc == 0) lrc = launch_kernel(h, s, p, n);
         if (e == cudaSuccess && lrc == 0)
             e = cudaMemcpyAsync(w->h_res, w->d_res, sizeof(SliceResult) * n, cudaMemcpyDeviceToHost, s);
         cudaGraph_t g = nullptr;
@@ -310,8 +445,11 @@ int run_once(fcm_ctx* h, const fcm_batch_plan& p, int n, bool use_graph) {
 }
 
 // Time one plan on the batch: best of `reps` launches after one warm-up.
-int time_plan(fcm_ctx* h, const fcm_batch_plan& p, int n, int reps, double* ms_out) {
-    int rc = launch_kernel(h, h->stream, p, n);
+int time_plan(fcm_ctx* h, const fcm_slice* slices, const fcm_batch_plan& p, int n, int reps, double* ms_out) {
+    int rc = 0;
+    if (p.schedule == FCM_SCHED_ROUNDS && (rc = fill_slots(h, slices, n, p.tile))) return rc;
+    if ((rc = upload_batch(h, h->stream, p, n))) return rc;
+    rc = launch_kernel(h, h->stream, p, n);
     if (rc) return rc;
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
@@ -360,7 +498,18 @@ int fcm_run_batched(fcm_handle h, fcm_slice* slices, int n_slices, int options) 
     for (int i = 0; i < n_slices; ++i) {
         const fcm_slice& s = slices[i];
         const float* U0 = s.init_mode == FCM_INIT_U ? (s.U0 ? s.U0 : s.U) : s.U;
-        if (!device_ptr(s.x) || !device_ptr(s.U) || !device_ptr(s.V) || !device_ptr(U0)) {
+        const void* ptrs[4] = {s.x, s.U, s.V, U0};
+        bool dev = true;
+        for (const void* q : ptrs) {
+            if (w->known_device.count(q)) continue;
+            if (!device_ptr(q)) {
+                dev = false;
+                break;
+            }
+            if (w->known_device.size() > (1u << 16)) w->known_device.clear();
+            w->known_device.insert(q);
+        }
+        if (!dev) {
             char buf[96];
             std::snprintf(buf, sizeof(buf), "slice %d: x, U, U0 and V must be device memory", i);
             return ctx_invalid(h, buf);
@@ -397,28 +546,30 @@ int fcm_run_batched(fcm_handle h, fcm_slice* slices, int n_slices, int options) 
         if (it != w->plans.end() && !(options & FCM_BATCH_RETUNE)) {
             plan = it->second;
         } else if (may_tune) {
-            // upload the batch once, then time every candidate shape on it
-            CK(cudaMemcpyAsync(w->d_desc, w->h_desc, sizeof(SliceDesc) * n_slices, cudaMemcpyHostToDevice,
-                               h->stream));
-            CK(cudaMemcpyAsync(w->d_order, w->h_order, sizeof(int) * n_slices, cudaMemcpyHostToDevice,
-                               h->stream));
-            fcm_batch_plan best = default_plan();
-            best.ms = 1e30;
+            // time every candidate shape of both schedules on the batch itself
+            std::vector<fcm_batch_plan> cands;
             const int blocks[2] = {256, 512};
             const int clusters[4] = {1, 2, 4, 8};
             const int64_t bigs[3] = {16384, 65536, 131072};
-            for (int b : blocks)
+            const int tiles[3] = {2048, 8192, 32768};
+            for (int b : blocks) {
                 for (int k : clusters)
-                    for (int gi = 0; gi < (k == 1 ? 1 : 3); ++gi) {
-                        fcm_batch_plan p{b, k, k == 1 ? ((int64_t)1 << 62) : bigs[gi], 0.0};
-                        if (grid_ctas(h, b, k) < k) continue;
-                        double ms = 0;
-                        if ((rc = time_plan(h, p, n_slices, 2, &ms))) return rc;
-                        if (ms < best.ms) {
-                            best = p;
-                            best.ms = ms;
-                        }
-                    }
+                    for (int gi = 0; gi < (k == 1 ? 1 : 3); ++gi)
+                        if (grid_ctas(h, b, k) >= k)
+                            cands.push_back({b, k, k == 1 ? ((int64_t)1 << 62) : bigs[gi], 0.0, FCM_SCHED_SLICES, 0});
+                if (n_slices <= ROUND_MAX_SLICES && round_ctas(h, b, round_smem(n_slices)) > 0)
+                    for (int t : tiles) cands.push_back({b, 1, 0, 0.0, FCM_SCHED_ROUNDS, t});
+            }
+            fcm_batch_plan best = default_plan();
+            best.ms = 1e30;
+            for (const fcm_batch_plan& p : cands) {
+                double ms = 0;
+                if ((rc = time_plan(h, slices, p, n_slices, 2, &ms))) return rc;
+                if (ms < best.ms) {
+                    best = p;
+                    best.ms = ms;
+                }
+            }
             plan = best;
             w->plans[key] = best;
             save_cache(w);
@@ -426,7 +577,12 @@ int fcm_run_batched(fcm_handle h, fcm_slice* slices, int n_slices, int options) 
             plan = default_plan();
         }
     }
-    if ((rc = run_once(h, plan, n_slices, !(options & FCM_BATCH_NO_GRAPH)))) return rc;
+    if (plan.schedule == FCM_SCHED_ROUNDS && (rc = fill_slots(h, slices, n_slices, plan.tile))) return rc;
+    const bool use_graph = !(options & FCM_BATCH_NO_GRAPH);
+    rc = run_once(h, plan, n_slices, use_graph);
+    // a runtime that cannot capture the cooperative round launch runs it directly
+    if (rc && use_graph && plan.schedule == FCM_SCHED_ROUNDS) rc = run_once(h, plan, n_slices, false);
+    if (rc) return rc;
     w->last = plan;
 
     int worst = FCM_OK;
@@ -459,9 +615,10 @@ int fcm_batched_set_plan(fcm_handle h, const fcm_batch_plan* plan) {
         h->batched->forced = false;
         return FCM_OK;
     }
-    if ((plan->block != 256 && plan->block != 512) ||
-        (plan->cluster != 1 && plan->cluster != 2 && plan->cluster != 4 && plan->cluster != 8) || plan->big < 1)
-        return ctx_invalid(h, "plan: block 256|512, cluster 1|2|4|8, big >= 1");
+    if (!plan_valid(*plan))
+        return ctx_invalid(h,
+                           "plan: block 256|512; slices schedule: cluster 1|2|4|8, big >= 1; "
+                           "rounds schedule: tile 1024..65536, a multiple of 1024");
     h->batched->forced = true;
     h->batched->forced_plan = *plan;
     return FCM_OK;

@@ -58,4 +58,59 @@ struct BatchKernel {
 BatchKernel batched_kernel_256();
 BatchKernel batched_kernel_512();
 
+// ---- round-synchronous schedule (every slice steps in every round) ----
+
+constexpr int ROUND_SUMS = 2 * FCM_MAX_CLUSTERS + 3;  // values per slot: num[C], den[C], J, max|dU|, bad
+constexpr int ROUND_MAX_SLICES = 8192;                 // the per-round prefix lives in shared memory
+
+// Mutable per-slice state, written by the slice's finaliser.
+struct alignas(16) RoundSlice {
+    double v64[FCM_MAX_CLUSTERS];   // FP64 quotients behind vcur
+    float vcur[FCM_MAX_CLUSTERS];   // V^k
+    float vprev[FCM_MAX_CLUSTERS];  // V^{k-1}
+    unsigned ticket;                // segments of this round finished (reset by the finaliser)
+    int end_round;                  // open (INT_MAX), round of the U write, or -1 (bad input)
+    int flags;
+    int pad;
+};
+
+struct alignas(128) RoundCtl {
+    unsigned bar;        // grid barrier arrivals
+    unsigned undecided;  // slices without a stop decision
+    int last_round;      // latest round in which some slice writes its U
+    unsigned timeout;    // set when a grid barrier wait gave up
+    unsigned pad[28];
+};
+
+// Sizes of one batch, uploaded with the descriptors (so one captured graph
+// serves every batch of the same slice count and plan).
+struct alignas(16) RoundsHdr {
+    int n_slices;
+    int max_rounds;  // largest max_iter + 1
+    int pad[2];
+};
+
+struct RoundsArgs {
+    const SliceDesc* descs;
+    SliceResult* results;
+    RoundSlice* state;
+    RoundCtl* ctl;
+    const RoundsHdr* hdr;
+    const int* slot_base;  // [n_slices + 1] first slot of each slice
+    double* partials;      // [slots * ROUND_SUMS], sum-major within a slice
+    int min_chunk;         // fewest pixels a CTA takes in a round (even)
+    int pad;
+};
+
+// Slots a slice needs: at most ceil(n / min_chunk) + 1 CTAs share it in a round.
+inline int64_t round_slots(int64_t n, int min_chunk) { return (n + 1 + min_chunk - 1) / min_chunk + 2; }
+
+struct RoundsKernel {
+    void (*fn)(RoundsArgs);
+    void (*init)(RoundSlice*, SliceResult*, RoundCtl*, int);
+};
+
+RoundsKernel rounds_kernel_256();
+RoundsKernel rounds_kernel_512();
+
 }  // namespace fcm

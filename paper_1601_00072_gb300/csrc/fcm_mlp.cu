@@ -20,6 +20,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <unordered_set>
 #include <vector>
 
 #include "fcm.h"
@@ -53,6 +54,8 @@ struct MlpWorkspace {
     int feat_cap = 0;
     void* hdesc_dev = nullptr;
     int hdesc_cap = 0;
+    float* v0 = nullptr;  // [feat_cap][9]: sorted initial centers and a usability flag
+    std::unordered_set<const void*> known_device;  // slice x pointers already checked
 };
 
 }  // namespace fcm
@@ -227,6 +230,35 @@ __global__ void k_features(const HistDesc* __restrict__ d, int ns, float* __rest
     if (threadIdx.x < D_ONE) f[D_HIST + threadIdx.x] = (threadIdx.x == d[s].C - 1) ? 1.0f : 0.0f;
 }
 
+// Initial centers from the network output, one thread per slice: the first C
+// outputs times 255, sorted ascending (insertion sort of at most 8), and a flag
+// telling whether they can start a run (all finite, neighbours more than 1e-3
+// apart). Row s of P holds V0[0..7] then the flag (1 or 0).
+__global__ void k_v0(const HistDesc* __restrict__ d, const float* __restrict__ y, int ns, float* __restrict__ P) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= ns) return;
+    const int C = d[s].C;
+    float v[D_OUT];
+#pragma unroll
+    for (int j = 0; j < D_OUT; ++j) v[j] = j < C ? 255.0f * y[(int64_t)s * D_OUT + j] : 0.0f;
+    bool ok = true;
+    for (int j = 0; j < C; ++j) ok &= (v[j] == v[j]) && fabsf(v[j]) != __int_as_float(0x7f800000);
+    for (int j = 1; j < C; ++j) {
+        const float t = v[j];
+        int k = j - 1;
+        while (k >= 0 && v[k] > t) {
+            v[k + 1] = v[k];
+            --k;
+        }
+        v[k + 1] = t;
+    }
+    for (int j = 1; j < C; ++j) ok &= v[j] - v[j - 1] > 1e-3f;
+    float* o = P + (int64_t)s * (D_OUT + 1);
+#pragma unroll
+    for (int j = 0; j < D_OUT; ++j) o[j] = v[j];
+    o[D_OUT] = ok ? 1.0f : 0.0f;
+}
+
 }  // namespace
 
 #define CK(call)                                              \
@@ -349,10 +381,76 @@ void fcm_release_mlp(fcm_ctx* h) {
     if (!h || !h->mlp) return;
     MlpWorkspace* w = h->mlp;
     void* ps[] = {w->master, w->wbf, w->adam_m, w->adam_v, w->grad, w->xb, w->tb, w->z1, w->a1, w->z2,
-                  w->a2, w->y, w->dy, w->dz2, w->dz1, w->loss, w->cb, w->idx, w->feats, w->hdesc_dev};
+                  w->a2, w->y, w->dy, w->dz2, w->dz1, w->loss, w->cb, w->idx, w->feats, w->hdesc_dev, w->v0};
     for (void* p : ps) cudaFree(p);
     delete w;
     h->mlp = nullptr;
+}
+
+int fcm_features_impl(fcm_ctx* h, const fcm_slice* slices, int n, float* feats) {
+    if (!h || !slices || n < 1 || !feats) return FCM_ERR_INVALID_ARG;
+    if (!device_mem(feats)) return ctx_invalid(h, "features must be device memory");
+    DeviceGuard g(h->device);
+    int rc = ensure_mlp(h, 1);
+    if (rc) return rc;
+    MlpWorkspace* w = h->mlp;
+    std::vector<HistDesc> d(n);
+    for (int i = 0; i < n; ++i) {
+        if (!slices[i].x || slices[i].n < 1 || slices[i].C < 1 || slices[i].C > FCM_MAX_CLUSTERS)
+            return ctx_invalid(h, "slice: bad x, n or C");
+        if (!w->known_device.count(slices[i].x)) {
+            if (!device_mem(slices[i].x)) return ctx_invalid(h, "slice: x must be device memory");
+            if (w->known_device.size() > (1u << 16)) w->known_device.clear();
+            w->known_device.insert(slices[i].x);
+        }
+        d[i] = HistDesc{slices[i].x, slices[i].n, slices[i].C, 0};
+    }
+    if (w->hdesc_cap < n) {
+        cudaFree(w->hdesc_dev);
+        w->hdesc_dev = nullptr;
+        CK(cudaMalloc(&w->hdesc_dev, sizeof(HistDesc) * n));
+        w->hdesc_cap = n;
+    }
+    CK(cudaMemcpyAsync(w->hdesc_dev, d.data(), sizeof(HistDesc) * n, cudaMemcpyHostToDevice, h->stream));
+    k_features<<<n, 512, 0, h->stream>>>((const HistDesc*)w->hdesc_dev, n, feats);
+    CK(cudaGetLastError());
+    return FCM_OK;
+}
+
+// Features, forward pass and k_v0 for a batch; fills each slice's V0 and sets
+// FCM_INIT_V. ok (when given) receives the usability flag of each prediction.
+int predict_v0(fcm_ctx* h, fcm_slice* slices, int n, std::vector<unsigned char>* ok) {
+    if (!h || !slices || n < 1) return FCM_ERR_INVALID_ARG;
+    int rc = need_model(h);
+    if (rc) return rc;
+    DeviceGuard g(h->device);
+    MlpWorkspace* w = h->mlp;
+    if (w->feat_cap < n) {
+        cudaFree(w->feats);
+        cudaFree(w->v0);
+        w->feats = nullptr;
+        w->v0 = nullptr;
+        w->feat_cap = 0;
+        CK(cudaMalloc(&w->feats, sizeof(float) * D_IN * n));
+        CK(cudaMalloc(&w->v0, sizeof(float) * (D_OUT + 1) * n));
+        w->feat_cap = n;
+    }
+    if ((rc = fcm_features_impl(h, slices, n, w->feats))) return rc;
+    if ((rc = ensure_mlp(h, n))) return rc;
+    if ((rc = forward(h, w->feats, n))) return rc;
+    k_v0<<<(n + 127) / 128, 128, 0, h->stream>>>((const HistDesc*)w->hdesc_dev, w->y, n, w->v0);
+    CK(cudaGetLastError());
+    std::vector<float> P((size_t)n * (D_OUT + 1));
+    CK(cudaMemcpyAsync(P.data(), w->v0, sizeof(float) * P.size(), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    if (ok) ok->assign(n, 0);
+    for (int i = 0; i < n; ++i) {
+        const float* r = &P[(size_t)i * (D_OUT + 1)];
+        for (int j = 0; j < FCM_MAX_CLUSTERS; ++j) slices[i].V0[j] = j < slices[i].C ? r[j] : 0.0f;
+        slices[i].init_mode = FCM_INIT_V;
+        if (ok) (*ok)[i] = r[D_OUT] != 0.0f;
+    }
+    return FCM_OK;
 }
 
 extern "C" {
@@ -507,75 +605,28 @@ int fcm_model_train(fcm_handle h, const float* feats, const float* targets, cons
 }
 
 int fcm_features(fcm_handle h, const fcm_slice* slices, int n, float* feats) {
-    if (!h || !slices || n < 1 || !feats) return FCM_ERR_INVALID_ARG;
-    if (!device_mem(feats)) return ctx_invalid(h, "features must be device memory");
-    DeviceGuard g(h->device);
-    int rc = ensure_mlp(h, 1);
+    const int rc = fcm_features_impl(h, slices, n, feats);
     if (rc) return rc;
-    MlpWorkspace* w = h->mlp;
-    std::vector<HistDesc> d(n);
-    for (int i = 0; i < n; ++i) {
-        if (!slices[i].x || slices[i].n < 1 || slices[i].C < 1 || slices[i].C > FCM_MAX_CLUSTERS ||
-            !device_mem(slices[i].x))
-            return ctx_invalid(h, "slice: bad x, n or C");
-        d[i] = HistDesc{slices[i].x, slices[i].n, slices[i].C, 0};
-    }
-    if (w->hdesc_cap < n) {
-        cudaFree(w->hdesc_dev);
-        w->hdesc_dev = nullptr;
-        CK(cudaMalloc(&w->hdesc_dev, sizeof(HistDesc) * n));
-        w->hdesc_cap = n;
-    }
-    CK(cudaMemcpyAsync(w->hdesc_dev, d.data(), sizeof(HistDesc) * n, cudaMemcpyHostToDevice, h->stream));
-    k_features<<<n, 512, 0, h->stream>>>((const HistDesc*)w->hdesc_dev, n, feats);
-    CK(cudaGetLastError());
+    DeviceGuard g(h->device);
     CK(cudaStreamSynchronize(h->stream));
     return FCM_OK;
 }
 
 int fcm_predict_centers(fcm_handle h, fcm_slice* slices, int n) {
-    if (!h || !slices || n < 1) return FCM_ERR_INVALID_ARG;
-    int rc = need_model(h);
-    if (rc) return rc;
-    DeviceGuard g(h->device);
-    MlpWorkspace* w = h->mlp;
-    if (w->feat_cap < n) {
-        cudaFree(w->feats);
-        w->feats = nullptr;
-        CK(cudaMalloc(&w->feats, sizeof(float) * D_IN * n));
-        w->feat_cap = n;
-    }
-    if ((rc = fcm_features(h, slices, n, w->feats))) return rc;
-    if ((rc = ensure_mlp(h, n))) return rc;
-    if ((rc = forward(h, w->feats, n))) return rc;
-    std::vector<float> y((size_t)n * D_OUT);
-    CK(cudaMemcpyAsync(y.data(), w->y, sizeof(float) * D_OUT * n, cudaMemcpyDeviceToHost, h->stream));
-    CK(cudaStreamSynchronize(h->stream));
-    for (int i = 0; i < n; ++i) {
-        float v[D_OUT];
-        const int C = slices[i].C;
-        for (int j = 0; j < C; ++j) v[j] = 255.0f * y[(size_t)i * D_OUT + j];
-        std::sort(v, v + C);
-        for (int j = 0; j < FCM_MAX_CLUSTERS; ++j) slices[i].V0[j] = j < C ? v[j] : 0.0f;
-        slices[i].init_mode = FCM_INIT_V;
-    }
-    return FCM_OK;
+    return predict_v0(h, slices, n, nullptr);
 }
 
 int fcm_run_batched_warm(fcm_handle h, fcm_slice* slices, int n, int options, int* n_cold) {
     if (!h || !slices || n < 1) return FCM_ERR_INVALID_ARG;
     if (n_cold) *n_cold = 0;
-    int rc = fcm_predict_centers(h, slices, n);
+    std::vector<unsigned char> ok;
+    int rc = predict_v0(h, slices, n, &ok);
     if (rc) return rc;
     // predictions that cannot start a run go back to the cold start
     int cold = 0;
     for (int i = 0; i < n; ++i) {
-        fcm_slice& s = slices[i];
-        bool ok = true;
-        for (int j = 0; j < s.C; ++j) ok &= std::isfinite(s.V0[j]);
-        for (int j = 1; j < s.C && ok; ++j) ok &= s.V0[j] - s.V0[j - 1] > 1e-3f;
-        if (!ok && s.U0) {
-            s.init_mode = FCM_INIT_U;
+        if (!ok[i] && slices[i].U0) {
+            slices[i].init_mode = FCM_INIT_U;
             ++cold;
         }
     }

@@ -14,6 +14,9 @@ import numpy as np
 from . import _lib
 
 
+_SLICE_DTYPE = np.dtype(_lib.fcm_slice)
+
+
 def _ptr(a) -> int:
     """Device or host pointer of a contiguous float32 torch tensor / numpy array."""
     if isinstance(a, np.ndarray):
@@ -71,7 +74,35 @@ class Slice:
     delta: float = 0.0
     J: float = 0.0
     V64: np.ndarray | None = None
-    init: str = ""
+    init: str = ""           # start the last run took: "U" (U0) or "V" (centers)
+    V0_warm: np.ndarray | None = None  # predicted centers a warm-started run began from
+
+
+class Batch:
+    """Slices marshalled once into the library's fcm_slice array, for batches
+    run again and again on the same buffers (a serving loop, a benchmark).
+    Pass it wherever a list of slices is taken; the slices' result fields are
+    filled after each run as usual."""
+
+    def __init__(self, slices):
+        self.slices = list(slices)
+        self.arr = FCM._c_slices(self.slices)
+        self._init = self.arr[["init_mode", "V0"]].copy()
+
+    def reset(self):
+        """Back to each slice's own start (a warm-started run rewrites it)."""
+        self.arr["init_mode"] = self._init["init_mode"]
+        self.arr["V0"] = self._init["V0"]
+
+    def __len__(self):
+        return len(self.slices)
+
+
+def _as_batch(slices) -> Batch:
+    if isinstance(slices, Batch):
+        slices.reset()
+        return slices
+    return Batch(slices)
 
 
 class FCM:
@@ -187,33 +218,44 @@ class FCM:
 
     @staticmethod
     def _c_slices(slices):
+        """The fcm_slice array of a batch, as a numpy structured array (its
+        memory is what the library reads and writes)."""
         import torch
-        arr = (_lib.fcm_slice * len(slices))()
-        for i, s in enumerate(slices):
-            n = _numel(s.x)
+        for s in slices:
             if s.U is None:
-                s.U = torch.empty((s.C, n), dtype=torch.float32, device=s.x.device)
+                s.U = torch.empty((s.C, _numel(s.x)), dtype=torch.float32, device=s.x.device)
             if s.V is None:
                 s.V = torch.empty(s.C, dtype=torch.float32, device=s.x.device)
-            a = arr[i]
-            a.x, a.n, a.C, a.m, a.eps, a.max_iter = _ptr(s.x), n, s.C, s.m, s.eps, s.max_iter
-            a.U, a.V = _ptr(s.U), _ptr(s.V)
-            a.U0 = None if s.U0 is None else _ptr(s.U0)
+        a = np.zeros(len(slices), dtype=_SLICE_DTYPE)
+        a["x"] = [_ptr(s.x) for s in slices]
+        a["n"] = [_numel(s.x) for s in slices]
+        a["C"] = [s.C for s in slices]
+        a["m"] = [s.m for s in slices]
+        a["eps"] = [s.eps for s in slices]
+        a["max_iter"] = [s.max_iter for s in slices]
+        a["U"] = [_ptr(s.U) for s in slices]
+        a["V"] = [_ptr(s.V) for s in slices]
+        a["U0"] = [0 if s.U0 is None else _ptr(s.U0) for s in slices]
+        a["init_mode"] = [_lib.FCM_INIT_U if s.V0 is None else _lib.FCM_INIT_V for s in slices]
+        for i, s in enumerate(slices):
             if s.V0 is not None:
-                a.init_mode = _lib.FCM_INIT_V
-                for j, vj in enumerate(np.asarray(s.V0, dtype=np.float64).reshape(-1)[:s.C]):
-                    a.V0[j] = float(vj)
-            else:
-                a.init_mode = _lib.FCM_INIT_U
-        return arr
+                v0 = np.asarray(s.V0, dtype=np.float64).reshape(-1)[:s.C]
+                a["V0"][i, :v0.size] = v0
+        return a
 
     @staticmethod
-    def _read_back(arr, slices):
+    def _arr_ptr(a):
+        return a.ctypes.data_as(ctypes.POINTER(_lib.fcm_slice))
+
+    @staticmethod
+    def _read_back(a, slices):
+        iters, status, flags = a["iters"].tolist(), a["status"].tolist(), a["flags"].tolist()
+        delta, J, modes = a["delta"].tolist(), a["J"].tolist(), a["init_mode"].tolist()
+        V64 = a["V64"]
         for i, s in enumerate(slices):
-            a = arr[i]
-            s.iters, s.status, s.flags, s.delta, s.J = a.iters, a.status, a.flags, a.delta, a.J
-            s.V64 = np.array(a.V64[:s.C])
-            s.init = "V" if a.init_mode == _lib.FCM_INIT_V else "U"
+            s.iters, s.status, s.flags, s.delta, s.J = iters[i], status[i], flags[i], delta[i], J[i]
+            s.V64 = V64[i, :s.C].copy()
+            s.init = "V" if modes[i] == _lib.FCM_INIT_V else "U"
 
     def _batch_opts(self, tune, retune, graph):
         return ((0 if tune else _lib.FCM_BATCH_NO_TUNE) | (_lib.FCM_BATCH_RETUNE if retune else 0)
@@ -224,28 +266,28 @@ class FCM:
         """Algorithm 1 on every slice in one persistent launch (see
         ``fcm_run_batched``). Fills each Slice's U, V and result fields and
         returns the aggregate status."""
-        arr = self._c_slices(slices)
+        b = _as_batch(slices)
         self._bind_stream()
-        st = self._lib.fcm_run_batched(self._h, arr, len(slices), self._batch_opts(tune, retune, graph))
+        st = self._lib.fcm_run_batched(self._h, self._arr_ptr(b.arr), len(b), self._batch_opts(tune, retune, graph))
         if st in (_lib.FCM_ERR_INVALID_ARG, _lib.FCM_ERR_CUDA, _lib.FCM_ERR_OOM) or raise_on_error:
             _lib.check(st, self._h)
-        self._read_back(arr, slices)
+        self._read_back(b.arr, b.slices)
         return st
 
     def run_batched_warm(self, slices, tune: bool = True, retune: bool = False, graph: bool = True):
         """Warm-started batch (``fcm_run_batched_warm``): predicted V^0, with the
         plain cold start (each slice's U0) as the fallback. Returns
         (status, number of slices that ran cold). ``s.init`` tells which."""
-        arr = self._c_slices(slices)
+        b = _as_batch(slices)
         cold = ctypes.c_int(0)
         self._bind_stream()
-        st = self._lib.fcm_run_batched_warm(self._h, arr, len(slices), self._batch_opts(tune, retune, graph),
-                                            ctypes.byref(cold))
+        st = self._lib.fcm_run_batched_warm(self._h, self._arr_ptr(b.arr), len(b),
+                                            self._batch_opts(tune, retune, graph), ctypes.byref(cold))
         if st in (_lib.FCM_ERR_INVALID_ARG, _lib.FCM_ERR_CUDA, _lib.FCM_ERR_OOM):
             _lib.check(st, self._h)
-        self._read_back(arr, slices)
-        for i, s in enumerate(slices):
-            s.V0 = np.array(arr[i].V0[:s.C]) if arr[i].init_mode == _lib.FCM_INIT_V else s.V0
+        self._read_back(b.arr, b.slices)
+        for i, sl in enumerate(b.slices):
+            sl.V0_warm = b.arr["V0"][i, :sl.C].copy() if sl.init == "V" else None
         return st, cold.value
 
     # ---- warm-start network ------------------------------------------------
@@ -276,7 +318,7 @@ class FCM:
         arr = self._c_slices(slices)
         out = torch.empty((len(slices), _lib.MODEL_D_IN), dtype=torch.float32, device=slices[0].x.device)
         self._bind_stream()
-        _lib.check(self._lib.fcm_features(self._h, arr, len(slices), _ptr(out)), self._h)
+        _lib.check(self._lib.fcm_features(self._h, self._arr_ptr(arr), len(slices), _ptr(out)), self._h)
         return out
 
     def model_forward(self, feats):
@@ -308,20 +350,25 @@ class FCM:
         """Sets each slice's V0 to the network's prediction."""
         arr = self._c_slices(slices)
         self._bind_stream()
-        _lib.check(self._lib.fcm_predict_centers(self._h, arr, len(slices)), self._h)
+        _lib.check(self._lib.fcm_predict_centers(self._h, self._arr_ptr(arr), len(slices)), self._h)
         for i, s in enumerate(slices):
-            s.V0 = np.array(arr[i].V0[:s.C])
+            s.V0 = arr["V0"][i, :s.C].copy()
 
     def batched_plan(self) -> dict:
         p = _lib.fcm_batch_plan()
         _lib.check(self._lib.fcm_batched_plan(self._h, ctypes.byref(p)), self._h)
-        return {"block": p.block, "cluster": p.cluster, "big": p.big, "ms": p.ms}
+        return {"schedule": "rounds" if p.schedule == _lib.FCM_SCHED_ROUNDS else "slices",
+                "block": p.block, "cluster": p.cluster, "big": p.big, "tile": p.tile, "ms": p.ms}
 
-    def set_batched_plan(self, block=None, cluster=None, big=None):
+    def set_batched_plan(self, block=None, cluster=1, big=1 << 62, schedule="slices", tile=0):
         """Force a launch shape for later batched runs; no arguments returns
-        to the autotuner."""
+        to the autotuner. ``schedule="rounds"`` takes ``block`` and ``tile``;
+        ``"slices"`` takes ``block``, ``cluster`` and ``big``."""
         if block is None:
             _lib.check(self._lib.fcm_batched_set_plan(self._h, None), self._h)
             return
-        p = _lib.fcm_batch_plan(int(block), int(cluster), int(big), 0.0)
+        rounds = schedule == "rounds"
+        p = _lib.fcm_batch_plan(int(block), 1 if rounds else int(cluster), 0 if rounds else int(big), 0.0,
+                                _lib.FCM_SCHED_ROUNDS if rounds else _lib.FCM_SCHED_SLICES,
+                                int(tile) if rounds else 0)
         _lib.check(self._lib.fcm_batched_set_plan(self._h, ctypes.byref(p)), self._h)

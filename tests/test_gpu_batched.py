@@ -98,17 +98,31 @@ def assert_batch(slices, host, m=2.0):
         assert_slice(rep, f"slice {i} (n={s.x.numel()}, C={s.C})")
 
 
-PLANS = [None, (512, 1, 1 << 40), (256, 1, 1 << 40), (512, 4, 4096), (256, 2, 4096), (512, 8, 16384),
-         (256, 4, 65536)]
+SLICE_PLANS = [dict(block=512, cluster=1, big=1 << 40), dict(block=256, cluster=1, big=1 << 40),
+               dict(block=512, cluster=4, big=4096), dict(block=256, cluster=2, big=4096),
+               dict(block=512, cluster=8, big=16384), dict(block=256, cluster=4, big=65536)]
+ROUND_PLANS = [dict(schedule="rounds", block=512, tile=2048), dict(schedule="rounds", block=256, tile=4096),
+               dict(schedule="rounds", block=512, tile=16384), dict(schedule="rounds", block=256, tile=65536)]
+PLANS = [None] + SLICE_PLANS + ROUND_PLANS
+# one plan of each schedule for the tests that run every schedule
+EACH = [dict(block=512, cluster=2, big=8192), dict(schedule="rounds", block=256, tile=4096)]
 
 
-@pytest.mark.parametrize("plan", PLANS, ids=lambda p: "auto" if p is None else f"b{p[0]}_k{p[1]}_big{p[2]}")
+def plan_id(p):
+    if p is None:
+        return "auto"
+    if p.get("schedule") == "rounds":
+        return f"rounds_b{p['block']}_t{p['tile']}"
+    return f"slices_b{p['block']}_k{p['cluster']}_big{p['big']}"
+
+
+@pytest.mark.parametrize("plan", PLANS, ids=plan_id)
 def test_batch_matches_oracle(fcm, plan):
     slices, host = make_batch(range(24))
     if plan is None:
         fcm.set_batched_plan()
     else:
-        fcm.set_batched_plan(*plan)
+        fcm.set_batched_plan(**plan)
     try:
         st = fcm.run_batched(slices)
     finally:
@@ -117,7 +131,8 @@ def test_batch_matches_oracle(fcm, plan):
     assert_batch(slices, host)
 
 
-def test_init_from_centers_and_other_fuzzifiers(fcm):
+@pytest.mark.parametrize("plan", EACH, ids=plan_id)
+def test_init_from_centers_and_other_fuzzifiers(fcm, plan):
     from paper_1601_00072_gb300.fcm import Slice
     slices, host = make_batch(range(24, 32), init="V")
     ms = [2.0] * len(slices)
@@ -132,7 +147,7 @@ def test_init_from_centers_and_other_fuzzifiers(fcm):
         extra.append(Slice(x=_cuda(x), C=C, m=m, eps=EPS, max_iter=300, U0=_cuda(u0)))
         host.append((x, u0, None))
         ms.append(m)
-    fcm.set_batched_plan(512, 2, 8192)
+    fcm.set_batched_plan(**plan)
     try:
         fcm.run_batched(slices + extra)
     finally:
@@ -142,7 +157,8 @@ def test_init_from_centers_and_other_fuzzifiers(fcm):
         assert_slice(rep, f"slice {i} (n={s.x.numel()}, C={s.C}, m={m})")
 
 
-def test_more_clusters_than_grey_levels(fcm):
+@pytest.mark.parametrize("plan", EACH, ids=plan_id)
+def test_more_clusters_than_grey_levels(fcm, plan):
     """Degenerate input: 5 pixels, 8 clusters. Centers land exactly on grey
     levels and how many tie on each depends on exact equality at the working
     precision, so the checks are the precision-free ones: memberships in
@@ -153,7 +169,11 @@ def test_more_clusters_than_grey_levels(fcm):
     x = np.array([10, 10, 50, 200, 200], dtype=np.uint8)
     u0 = phantom.dirichlet_u0((77, 5), 8, x.size)
     s = Slice(x=_cuda(x), C=8, m=2.0, eps=EPS, max_iter=300, U0=_cuda(u0))
-    fcm.run_batched([s], tune=False)
+    fcm.set_batched_plan(**plan)
+    try:
+        fcm.run_batched([s])
+    finally:
+        fcm.set_batched_plan()
     assert s.status in (0, 1)
     gU, gV = s.U.cpu().numpy(), s.V.cpu().numpy()
     assert np.all(gU >= 0) and np.all(gU <= 1 + 1e-6)
@@ -161,21 +181,31 @@ def test_more_clusters_than_grey_levels(fcm):
     assert np.max(np.abs(gU - oracle.memberships(x.astype(np.float64), gV.astype(np.float64), 2.0))) <= 1e-5
 
 
-def test_bad_slice_does_not_spoil_the_batch(fcm):
+@pytest.mark.parametrize("plan", EACH, ids=plan_id)
+def test_bad_slice_does_not_spoil_the_batch(fcm, plan):
     slices, host = make_batch(range(6))
     x_bad = host[2][0].astype(np.float32).copy()
     x_bad[17] = np.nan
     slices[2].x = _cuda(x_bad)
-    st = fcm.run_batched(slices, tune=False)
+    fcm.set_batched_plan(**plan)
+    try:
+        st = fcm.run_batched(slices)
+    finally:
+        fcm.set_batched_plan()
     assert st == -4 and slices[2].status == -4
     for i in (0, 1, 3, 4, 5):
         rep, _ = check_slice(slices[i], *host[i], 2.0)
         assert_slice(rep, f"slice {i}")
 
 
-def test_max_iter_reached(fcm):
+@pytest.mark.parametrize("plan", EACH, ids=plan_id)
+def test_max_iter_reached(fcm, plan):
     slices, host = make_batch(range(4), max_iter=5)
-    st = fcm.run_batched(slices, tune=False)
+    fcm.set_batched_plan(**plan)
+    try:
+        st = fcm.run_batched(slices)
+    finally:
+        fcm.set_batched_plan()
     assert st == 1
     for s, (x, u0, V0) in zip(slices, host):
         assert s.status == 1 and s.iters == 5
@@ -183,10 +213,11 @@ def test_max_iter_reached(fcm):
         assert center_err(s.V.cpu().numpy(), ok["V"]) < 1e-4  # early iterate, FP32 vs FP64
 
 
-def test_graph_and_direct_launch_agree_bitwise(fcm):
+@pytest.mark.parametrize("plan", EACH, ids=plan_id)
+def test_graph_and_direct_launch_agree_bitwise(fcm, plan):
     a, host = make_batch(range(8))
     b, _ = make_batch(range(8))
-    fcm.set_batched_plan(512, 2, 16384)
+    fcm.set_batched_plan(**plan)
     try:
         fcm.run_batched(a)
         fcm.run_batched(b, graph=False)
@@ -208,23 +239,32 @@ def test_autotuner_caches_its_plan(tmp_path, monkeypatch):
     plan = h.batched_plan()
     h.close()
     assert plan["block"] in (256, 512) and plan["cluster"] in (1, 2, 4, 8) and plan["ms"] > 0
+    assert plan["schedule"] in ("slices", "rounds")
     text = path.read_text()
-    assert '"block": %d' % plan["block"] in text
+    assert '"block": %d' % plan["block"] in text and '"tile": %d' % plan["tile"] in text
     # a new handle takes the cached plan without tuning
     h2 = FCM(0)
     slices2, _ = make_batch(range(40, 56))
     h2.run_batched(slices2)
     p2 = h2.batched_plan()
-    assert (p2["block"], p2["cluster"], p2["big"]) == (plan["block"], plan["cluster"], plan["big"])
+    assert {k: p2[k] for k in ("schedule", "block", "cluster", "big", "tile")} == \
+        {k: plan[k] for k in ("schedule", "block", "cluster", "big", "tile")}
     assert abs(p2["ms"] - plan["ms"]) < 1e-3
     h2.close()
     assert_batch(slices2, host)
 
 
-def test_full_512_slice_batch_matches_oracle(fcm):
-    """The whole 512-slice workload (sides 64..512, C in {3, 4, 5})."""
+@pytest.mark.parametrize("plan", [None, dict(schedule="rounds", block=512, tile=4096)], ids=plan_id)
+def test_full_512_slice_batch_matches_oracle(fcm, plan):
+    """The whole 512-slice workload (sides 64..512, C in {3, 4, 5}), with the
+    autotuned plan and with the round schedule."""
     slices, host = make_batch(range(512))
-    st = fcm.run_batched(slices)
+    if plan is not None:
+        fcm.set_batched_plan(**plan)
+    try:
+        st = fcm.run_batched(slices)
+    finally:
+        fcm.set_batched_plan()
     assert st in (0, 1)
     worst = {"center_rel_err": 0.0, "max_abs_dU": 0.0, "label_agreement": 1.0, "sensitive": 0}
     for i, (s, (x, u0, V0)) in enumerate(zip(slices, host)):
@@ -234,5 +274,5 @@ def test_full_512_slice_batch_matches_oracle(fcm):
         worst["max_abs_dU"] = max(worst["max_abs_dU"], rep["max_abs_dU"])
         worst["label_agreement"] = min(worst["label_agreement"], rep["label_agreement"])
         worst["sensitive"] += rep["conditioning"] == "sensitive"
-    print("worst over 512 slices:", worst)
+    print("worst over 512 slices:", worst, fcm.batched_plan())
     assert worst["sensitive"] <= 10  # trajectory-sensitive slices, judged on converged results
