@@ -254,9 +254,10 @@ def batch_inputs(dev, n=512):
     return xs, u0s, Cs
 
 
-def bench_batched(h, dev, steps, warmup):
+def bench_batched(h, dev, steps, warmup, plan=None):
     """Cold versus warm-started batch, timed with CUDA events on the launching
-    stream (each call returns after its results are read back)."""
+    stream (each call returns after its results are read back). ``plan``
+    (a dict of FCM.set_batched_plan arguments) replaces the autotuner."""
     import torch
     from paper_1601_00072_gb300 import warmstart
     from paper_1601_00072_gb300.fcm import Batch, Slice
@@ -279,8 +280,11 @@ def bench_batched(h, dev, steps, warmup):
         torch.cuda.synchronize(dev)
         return e0.elapsed_time(e1) / reps
 
+    if plan:
+        h.set_batched_plan(**plan)
     cold = Batch(cold)
     ms_cold = timed(lambda: h.run_batched(cold), steps)
+    plan_used = h.batched_plan()
     warm = Batch([Slice(x=x, C=c, U0=u) for x, c, u in zip(xs, Cs, u0s)])
     n_ran_cold = [0]
 
@@ -305,7 +309,7 @@ def bench_batched(h, dev, steps, warmup):
                  "mean_iters": float(it_w.mean()), "max_iters": int(it_w.max()),
                  "accepted": float(ok.mean()), "ran_cold_at_run_time": int(n_ran_cold[0])},
         "warm_over_cold": warm_ips / cold_ips,
-        "plan": h.batched_plan(),
+        "plan": plan_used,
     }
 
 
@@ -486,6 +490,12 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the cold versus warm batch measurement")
+    ap.add_argument("--batched-only", action="store_true",
+                    help="only the cold versus warm batch measurement, printed as its own JSON object "
+                         "(a profiling aid; not the benchmark line)")
+    ap.add_argument("--batch-plan", default=None,
+                    help='with --batched-only: a fixed launch plan instead of the autotuner, as JSON, '
+                         'e.g. \'{"block": 256, "cluster": 4, "big": 16384}\'')
     ap.add_argument("--variant", choices=["tma", "ldg"], default="tma",
                     help="pass kernel: TMA-fed ring (default) or plain loads")
     ap.add_argument("--no-graph", action="store_true",
@@ -496,6 +506,15 @@ def main():
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     if args.impl == "reference":
         bench_reference(args)
+    elif args.batched_only:
+        import torch
+        from paper_1601_00072_gb300 import _build
+        _build.build()
+        from paper_1601_00072_gb300.fcm import FCM
+        h = FCM(0)
+        plan = json.loads(args.batch_plan) if args.batch_plan else None
+        print(json.dumps(bench_batched(h, torch.device("cuda", 0), max(1, args.steps), args.warmup, plan)))
+        h.close()
     else:
         bench_ours(args)
 
