@@ -237,7 +237,7 @@ def cpu_baseline_leg(x, u0, m, gV, gU_sample, idx, g_iters, g_J):
         "J_rel_err": float(abs(g_J - o["J"][-1]) / abs(o["J"][-1])) if o["iters"] == g_iters else None,
         "U_sample_voxels": int(idx.size),
     }
-    return base, prec
+    return base, prec, o
 
 
 def batch_inputs(dev, n=512):
@@ -396,6 +396,31 @@ def bench_ours(args):
                "h2d_bytes_per_step": 4 * n + 4 * C * n,
                "d2h_bytes_per_step": 4 * C * n + 4 * C}
 
+    # the same run on the grey-level histogram (fcm_run_hist), inputs resident
+    hist = None
+    if not args.no_hist:
+        Uh = torch.empty_like(U0d)
+        Vh = torch.empty(C, dtype=torch.float32, device=dev)
+        for _ in range(args.warmup):
+            rh = h.run_hist(xd, C, m, EPS, MAX_ITER, U0=U0d, U=Uh, V=Vh)
+        hs = max(3, min(args.steps, 50))
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        for _ in range(hs):
+            rh = h.run_hist(xd, C, m, EPS, MAX_ITER, U0=U0d, U=Uh, V=Vh)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        hms = e0.elapsed_time(e1) / hs
+        hbytes = 3 * (4 + 4 * C) * n  # histogram + V^1 pass, first-stop pass, U write
+        hist = {"kernel": "fcm_run_hist: pixel passes for the histogram, the first stop and the U write; "
+                          "the iterations on 256 bins in one CTA",
+                "ms_per_run": hms, "iters": rh.iters, "launches_per_run": rh.launches,
+                "equivalent_pixel_iter_per_s": n * rh.iters / (hms / 1e3),
+                "roofline": {"bound": "hbm", "achieved": hbytes / (hms / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
+                             "frac": hbytes / (hms / 1e3) / 1e9 / peak, "algorithmic_bytes_per_run": hbytes},
+                "speedup_vs_pixel_path": (ms / args.steps) / hms,
+                "_V": Vh.cpu().numpy().astype(np.float64)}
+
     out = {
         "metric": METRIC,
         "value": value,
@@ -426,6 +451,7 @@ def bench_ours(args):
                      "algorithmic_bytes_per_step": bytes_local / args.steps},
         "clocks": clocks,
         "e2e": e2e,
+        "histogram_domain": hist,
     }
     if not args.no_batched:
         out["batched"] = bench_batched(h, dev, max(3, min(args.steps, 20)), 3)
@@ -433,9 +459,17 @@ def bench_ours(args):
         idx = np.random.default_rng(0).choice(n, 100_000, replace=False)
         gU_sample = Ud[:, torch.from_numpy(idx).to(dev)].cpu().numpy().astype(np.float64)
         gV = Vd.cpu().numpy().astype(np.float64)
-        base, prec = cpu_baseline_leg(x, u0, m, gV, gU_sample, idx, r.iters, r.J)
+        base, prec, o = cpu_baseline_leg(x, u0, m, gV, gU_sample, idx, r.iters, r.J)
         out["cpu_baseline"] = base
         out["precision"] = prec
+        if hist is not None:
+            hv = hist.pop("_V")
+            hist["precision"] = {
+                "vs": "FP64 oracle (256-bin form), same x and U0",
+                "center_rel_err": float(np.max(np.abs(hv - o["V"]) / np.maximum(np.abs(o["V"]), 1.0))),
+                "d_iters": int(hist["iters"] - o["iters"]) if o["iters"] == r.iters else None}
+    if hist is not None:
+        hist.pop("_V", None)
     h.close()
     if rank == 0:
         print(json.dumps(out))
@@ -490,6 +524,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the cold versus warm batch measurement")
+    ap.add_argument("--no-hist", action="store_true", help="skip the histogram-domain measurement")
     ap.add_argument("--batched-only", action="store_true",
                     help="only the cold versus warm batch measurement, printed as its own JSON object "
                          "(a profiling aid; not the benchmark line)")

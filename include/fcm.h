@@ -138,6 +138,29 @@ int fcm_run(fcm_handle h, const float* x, int64_t n, int C, float m,
             float* V, int options, fcm_report* rep);
 
 /*
+ * fcm_run_hist — Algorithm 1 (Sec. 2.1) for images whose intensities are
+ * integer grey levels 0..255, run on the 256-bin histogram (the grey-level
+ * reduction of brFCM, cited in Sec. 3). Under Eq. 4 a pixel's memberships
+ * depend only on its grey level, so after pass 0 every center update (Eq. 3),
+ * J (Eq. 1) and stopping quantity is a sum or maximum over the grey levels
+ * present, weighted by their pixel counts. The iterates equal fcm_run's up to
+ * the order of rounding: same U^0, V^1, stopping rule and outputs. With
+ * FCM_INIT_U the first stopping quantity compares U^1 with every pixel's U^0.
+ *
+ * Arguments as fcm_run, except: x, U and U0 must be device memory (V may be
+ * host or device), and there are no options. Passes over the pixels: one
+ * (histogram, and with FCM_INIT_U the sums of V^1), one more with FCM_INIT_U
+ * (first stopping quantity), and one that writes U^k; the iterations run in
+ * one CTA on the bins.
+ *
+ * Returns as fcm_run; FCM_ERR_BAD_INPUT when some x_i is not an integer in
+ * [0, 255] (or not finite), or U^0 holds a negative or non-finite value, or V^0
+ * a non-finite one. U is not written then.
+ */
+int fcm_run_hist(fcm_handle h, const float* x, int64_t n, int C, float m, float eps, int max_iter,
+                 int init_mode, const float* U0, float* U, float* V, fcm_report* rep);
+
+/*
  * Batched runs: many independent images ("slices") of different sizes, cluster
  * counts and fuzzifiers in one persistent launch (not in the paper, which
  * segments one image at a time; each slice follows Algorithm 1 exactly as

@@ -291,6 +291,7 @@ void fcm_destroy(fcm_handle h) {
         if (h->d_stage_U) cudaFree(h->d_stage_U);
         fcm_release_batched(h);
         fcm_release_mlp(h);
+        fcm_release_hist(h);
     }
     delete h;
 }

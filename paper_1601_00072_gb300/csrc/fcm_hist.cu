@@ -1,0 +1,569 @@
+// Histogram-domain FCM for images of integer grey levels 0..255.
+//
+// When every intensity is one of 256 grey levels, the membership of a pixel
+// under Eq. 4 depends only on its grey level, so after the first center
+// update the whole of Algorithm 1 (Sec. 2.1) can run on the 256-bin
+// histogram: the center sums of Eq. 3 and J of Eq. 1 become sums over bins
+// weighted by their pixel counts, and the stopping quantity max |U^k - U^{k-1}|
+// is a maximum over the bins that occur. This is the grey-level reduction the
+// paper cites among related GPU work (brFCM, Sec. 3); the results equal the
+// per-pixel run's up to the order of rounding.
+//
+// Per run: one pass over the pixels builds the histogram (and, from U^0, the
+// sums of V^1); with U^0 given, a second pass takes the first stopping
+// quantity against the pixels' U^0; one CTA then iterates on the bins; a last
+// pass writes U^k by table lookup. HBM traffic is 4 + 4C bytes per pixel for
+// each of the (up to) three passes instead of 4 + 8C per iteration.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "fcm.h"
+#include "fcm_device.cuh"
+#include "fcm_runtime.h"
+
+namespace fcm {
+
+struct alignas(16) HistState {
+    unsigned long long hist[256];
+    double V64[FCM_MAX_CLUSTERS];
+    float V[FCM_MAX_CLUSTERS];
+    float V0[FCM_MAX_CLUSTERS];
+    double delta, J;
+    unsigned d1bits;  // max |U^1 - U^0| over the pixels, as float bits (from U^0)
+    int bad;
+    int iters, status, flags, pad;
+};
+
+struct HistWorkspace {
+    HistState* d_st = nullptr;
+    HistState* h_st = nullptr;  // pinned
+    double* part = nullptr;
+    int part_blocks = 0;
+    float* table = nullptr;  // [256][C] final memberships of each grey level
+};
+
+}  // namespace fcm
+
+using namespace fcm;
+
+namespace {
+
+constexpr int HNT = 256;
+constexpr int HCHUNK = 8;
+
+__device__ __forceinline__ bool grey_level(float v) {
+    return v >= 0.0f && v <= 255.0f && v == rintf(v);  // false for NaN
+}
+
+// Pass over the pixels: histogram, input checks, and (from U^0) the
+// numerators and denominators of V^1 (Eq. 3) as per-block FP64 slots.
+template <int C, int MK, bool FROM_U>
+__global__ void __launch_bounds__(HNT) k_hist_pass0(const float* __restrict__ x, const float* __restrict__ U0,
+                                                   int64_t n, float m, HistState* st, double* __restrict__ part) {
+    __shared__ unsigned hs[HNT / 32][256];  // one sub-histogram per warp
+    __shared__ float w[HNT / 32][4 * C];
+    for (int t = threadIdx.x; t < (HNT / 32) * 256; t += HNT) (&hs[0][0])[t] = 0u;
+    __syncthreads();
+    DF acc[2 * C];
+#pragma unroll
+    for (int q = 0; q < 2 * C; ++q) acc[q] = DF{0.0f, 0.0f};
+    bool bad = false;
+    const int64_t stride = (int64_t)gridDim.x * HNT;
+    const int lane_id = threadIdx.x & 31;
+    unsigned* hw = hs[threadIdx.x >> 5];
+    // the loop bounds are the same for all lanes of a warp (its first lane's
+    // index), so every lane reaches the warp-wide match below
+    for (int64_t i0 = (int64_t)blockIdx.x * HNT + threadIdx.x; i0 - lane_id < n; i0 += stride * HCHUNK) {
+        // the chunk's loads are all issued before any is used
+        float xc[HCHUNK], uc[HCHUNK][FROM_U ? C : 1];
+#pragma unroll
+        for (int q = 0; q < HCHUNK; ++q) {
+            const int64_t i = i0 + (int64_t)q * stride;
+            const bool in = i < n;
+            xc[q] = in ? __ldg(x + i) : 0.0f;
+            if (FROM_U) {
+#pragma unroll
+                for (int j = 0; j < C; ++j) uc[q][j] = in ? __ldg(U0 + (int64_t)j * n + i) : 0.0f;
+            }
+        }
+        float num[C], den[C];
+#pragma unroll
+        for (int j = 0; j < C; ++j) num[j] = den[j] = 0.0f;
+#pragma unroll
+        for (int q = 0; q < HCHUNK; ++q) {
+            const int64_t i = i0 + (int64_t)q * stride;
+            if (i - lane_id >= n) break;  // warp-uniform
+            const bool in = i < n;
+            const float xi = xc[q];
+            const bool good = in && grey_level(xi);
+            bad |= in && !good;
+            // lanes that hold the same grey level add once, through their leader
+            const int key = good ? (int)xi : -1;
+            const unsigned same = __match_any_sync(0xffffffffu, key);
+            if (good && lane_id == __ffs(same) - 1) atomicAdd(&hw[key], (unsigned)__popc(same));
+            if (FROM_U && good) {
+#pragma unroll
+                for (int j = 0; j < C; ++j) {
+                    const float u0 = uc[q][j];
+                    bad |= !(u0 >= 0.0f) || !finite_f(u0);
+                    const float wt = pow_m<MK>(u0, m);
+                    num[j] = fmaf(wt, xi, num[j]);
+                    den[j] += wt;
+                }
+            }
+        }
+        if (FROM_U) {
+#pragma unroll
+            for (int j = 0; j < C; ++j) {
+                df_add(acc[j], num[j]);
+                df_add(acc[C + j], den[j]);
+            }
+        }
+    }
+    __syncthreads();
+    for (int b = threadIdx.x; b < 256; b += HNT) {
+        unsigned t = 0u;
+        for (int v = 0; v < HNT / 32; ++v) t += hs[v][b];
+        if (t) atomicAdd(&st->hist[b], (unsigned long long)t);
+    }
+    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(&st->bad, 1);
+    if (!FROM_U) return;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int q = 0; q < 2 * C; ++q) {
+        const DF d = warp_sum_df(acc[q]);
+        if (lane == 0) {
+            w[warp][2 * q] = d.hi;
+            w[warp][2 * q + 1] = d.lo;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < 2 * C) {
+        const int q = threadIdx.x;
+        double t = 0.0;
+        for (int v = 0; v < HNT / 32; ++v) t += (double)w[v][2 * q] + (double)w[v][2 * q + 1];
+        part[(int64_t)blockIdx.x * 2 * C + q] = t;
+    }
+}
+
+// Block-wide FP64 sums of S values per thread and one float maximum, the same
+// fixed order in every call; every thread receives the totals.
+template <int S>
+__device__ __forceinline__ void block_sums(double (&v)[S], float& mx, double (*red)[S + 1], double* tot) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int q = 0; q < S; ++q) v[q] = warp_sum(v[q]);
+    mx = warp_max(mx);
+    if (lane == 0) {
+#pragma unroll
+        for (int q = 0; q < S; ++q) red[warp][q] = v[q];
+        red[warp][S] = (double)mx;
+    }
+    __syncthreads();
+    if (threadIdx.x <= S) {
+        const int q = threadIdx.x;
+        double t = 0.0;
+        for (int u = 0; u < HNT / 32; ++u) t = q < S ? t + red[u][q] : fmax(t, red[u][q]);
+        tot[q] = t;
+    }
+    __syncthreads();
+}
+
+// w * (hh + hl) as a double-float pair: the exact product w * hh (TwoProd by
+// FMA) plus the small w * hl.
+__device__ __forceinline__ DF weighted(float w, float hh, float hl) {
+    const float p = w * hh;
+    const float e = fmaf(w, hh, -p);
+    DF d{p, 0.0f};
+    df_add(d, fmaf(w, hl, e));
+    return d;
+}
+
+// V^1: from the pass-0 slots (U^0 given), or from the bins with
+// U^0 = f(grey level, V^0) (Eq. 4 then Eq. 3). One CTA.
+template <int C, int MK, bool FROM_U>
+__global__ void __launch_bounds__(HNT) k_hist_init(HistState* st, const double* __restrict__ part, int nblocks,
+                                                  float m, float inv_m1) {
+    __shared__ double red[HNT / 32][2 * C + 1];
+    __shared__ double tot[2 * C + 1];
+    bool bad = st->bad != 0;
+    if (!FROM_U) {
+#pragma unroll
+        for (int j = 0; j < C; ++j) bad |= !finite_f(st->V0[j]);
+    }
+    if (bad) {
+        if (threadIdx.x == 0) {
+            st->bad = 1;
+            st->status = FCM_ERR_BAD_INPUT;
+            st->iters = 0;
+#pragma unroll
+            for (int j = 0; j < C; ++j) {
+                st->V[j] = st->V0[j];
+                st->V64[j] = st->V0[j];
+            }
+        }
+        return;
+    }
+    if (FROM_U) {
+        // thread t adds slots t, t + HNT, ... of every sum; then one block sum
+        double s[2 * C];
+        float mx = 0.0f;
+#pragma unroll
+        for (int q = 0; q < 2 * C; ++q) s[q] = 0.0;
+        for (int b = threadIdx.x; b < nblocks; b += HNT) {
+#pragma unroll
+            for (int q = 0; q < 2 * C; ++q) s[q] += part[(int64_t)b * 2 * C + q];
+        }
+        block_sums<2 * C>(s, mx, red, tot);
+    } else {
+        const int b = threadIdx.x;
+        const double hb = (double)st->hist[b];
+        float v0[C], u[C], um[C];
+#pragma unroll
+        for (int j = 0; j < C; ++j) v0[j] = st->V0[j];
+        membership<C, MK>((float)b, v0, m, inv_m1, u, um);
+        double s[2 * C];
+        float mx = 0.0f;
+#pragma unroll
+        for (int j = 0; j < C; ++j) {
+            s[j] = hb * (double)um[j] * (double)b;
+            s[C + j] = hb * (double)um[j];
+        }
+        block_sums<2 * C>(s, mx, red, tot);
+    }
+    if (threadIdx.x == 0) {
+        int flags = 0;
+#pragma unroll
+        for (int j = 0; j < C; ++j) {
+            const double den = tot[C + j];
+            if (den > 0.0) {
+                st->V64[j] = tot[j] / den;
+                st->V[j] = (float)st->V64[j];
+            } else {
+                flags |= FCM_FLAG_EMPTY_CLUSTER;  // V^0 kept, or 0 from a U^0
+                st->V[j] = FROM_U ? 0.0f : st->V0[j];
+                st->V64[j] = st->V[j];
+            }
+        }
+        st->flags = flags;
+    }
+}
+
+// The first stopping quantity from U^0: max over pixels and clusters of
+// |f(x_i, V^1)_j - U^0_ij|, with f tabulated per grey level.
+template <int C, int MK>
+__global__ void __launch_bounds__(HNT) k_hist_delta1(const float* __restrict__ x, const float* __restrict__ U0,
+                                                    int64_t n, float m, float inv_m1, HistState* st) {
+    __shared__ float T[256][C];
+    __shared__ float wm[HNT / 32];
+    if (st->bad) return;
+    {
+        float v[C], u[C], um[C];
+#pragma unroll
+        for (int j = 0; j < C; ++j) v[j] = st->V[j];
+        membership<C, MK>((float)threadIdx.x, v, m, inv_m1, u, um);
+#pragma unroll
+        for (int j = 0; j < C; ++j) T[threadIdx.x][j] = u[j];
+    }
+    __syncthreads();
+    float d = 0.0f;
+    const int64_t stride = (int64_t)gridDim.x * HNT;
+    for (int64_t i = (int64_t)blockIdx.x * HNT + threadIdx.x; i < n; i += stride) {
+        const int b = (int)__ldg(x + i);
+#pragma unroll
+        for (int j = 0; j < C; ++j) d = fmaxf(d, fabsf(T[b][j] - __ldg(U0 + (int64_t)j * n + i)));
+    }
+    d = warp_max(d);
+    if ((threadIdx.x & 31) == 0) wm[threadIdx.x >> 5] = d;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float t = 0.0f;
+        for (int u = 0; u < HNT / 32; ++u) t = fmaxf(t, wm[u]);
+        atomicMax(&st->d1bits, __float_as_uint(t));  // non-negative floats order as their bits
+    }
+}
+
+// Quotient of two double-float values, as a double-float (one FP32 division
+// and a residual correction): accurate to about 2^-44 relative.
+__device__ __forceinline__ DF df_div(DF a, DF b) {
+    const float q0 = a.hi / b.hi;
+    const float p = q0 * b.hi;
+    const float e = fmaf(q0, b.hi, -p);  // q0 * b.hi = p + e exactly
+    const float r = ((a.hi - p) - e + a.lo) - q0 * b.lo;
+    const float q1 = r / b.hi;
+    const float s = q0 + q1;
+    return DF{s, q1 - (s - q0)};
+}
+
+// Algorithm 1 on the bins, one CTA, thread b = grey level b. Sums over the
+// bins run in compensated FP32 (per-bin exact products, double-float warp
+// trees, the eight warp totals merged in a fixed order by warp 0), so the
+// loop needs no FP64 arithmetic; V64 is formed once at the end.
+template <int C, int MK, bool FROM_U>
+__global__ void __launch_bounds__(HNT) k_hist_solve(HistState* st, float* __restrict__ table, float m, float inv_m1,
+                                                   float eps, int max_iter) {
+    constexpr int S = 2 * C + 1;
+    __shared__ DF wtot[HNT / 32][S];
+    __shared__ float wmax[HNT / 32];
+    __shared__ DF tot[S];
+    __shared__ float s_v[C], s_delta;
+    __shared__ double s_v64[C];
+    __shared__ int s_empty;
+    if (st->bad) return;
+    const int b = threadIdx.x, lane = b & 31, warp = b >> 5;
+    const unsigned long long cnt = st->hist[b];
+    const bool present = cnt > 0ull;
+    // the count as an unevaluated float pair (exact below 2^48)
+    const float hh = (float)cnt, hl = (float)((double)cnt - (double)hh);
+    float v[C], up[C], u[C], um[C];
+#pragma unroll
+    for (int j = 0; j < C; ++j) v[j] = st->V[j];
+    if (!FROM_U) {
+        float v0[C], um0[C];
+#pragma unroll
+        for (int j = 0; j < C; ++j) v0[j] = st->V0[j];
+        membership<C, MK>((float)b, v0, m, inv_m1, up, um0);
+    }
+    int flags = st->flags;
+    double v64 = b < C ? st->V64[b] : 0.0;  // thread j keeps the FP64 quotient behind v_j
+    int status = FCM_NOT_CONVERGED, k = 1;
+    float delta = 0.0f;
+    for (k = 1;; ++k) {
+        const float Ji = membership<C, MK>((float)b, v, m, inv_m1, u, um);
+        DF s[S];
+        float mx = 0.0f;
+#pragma unroll
+        for (int j = 0; j < C; ++j) {
+            s[j] = weighted(um[j] * (float)b, hh, hl);
+            s[C + j] = weighted(um[j], hh, hl);
+            if (present && !(FROM_U && k == 1)) mx = fmaxf(mx, fabsf(u[j] - up[j]));
+        }
+        s[2 * C] = weighted(Ji, hh, hl);
+#pragma unroll
+        for (int q = 0; q < S; ++q) s[q] = warp_sum_df(s[q]);
+        mx = warp_max(mx);
+        if (lane == 0) {
+#pragma unroll
+            for (int q = 0; q < S; ++q) wtot[warp][q] = s[q];
+            wmax[warp] = mx;
+        }
+        __syncthreads();
+        if (warp == 0) {
+            // lane q merges sum q over the warps, in warp order
+            if (lane < S) {
+                DF t = wtot[0][lane];
+                for (int w = 1; w < HNT / 32; ++w) t = df_merge(t, wtot[w][lane]);
+                tot[lane] = t;
+            }
+            float dm = lane < HNT / 32 ? wmax[lane] : 0.0f;
+            dm = warp_max(dm);
+            __syncwarp();
+            if (lane == 0) s_delta = (FROM_U && k == 1) ? __uint_as_float(st->d1bits) : dm;
+            // V^{k+1} (Eq. 3), computed by lane j; an empty cluster keeps v_j
+            bool empty = false;
+            if (lane < C) {
+                const DF den = tot[C + lane];
+                if (den.hi > 0.0f) {
+                    const DF q = df_div(tot[lane], den);
+                    s_v[lane] = q.hi;
+                    s_v64[lane] = (double)q.hi + (double)q.lo;
+                } else {
+                    s_v[lane] = v[lane];
+                    s_v64[lane] = v64;
+                    empty = true;
+                }
+            }
+            const unsigned em = __ballot_sync(0xffffffffu, empty);
+            if (lane == 0) s_empty = em != 0u;
+        }
+        __syncthreads();
+        delta = s_delta;
+        if (delta < eps) {
+            status = FCM_OK;
+            break;
+        }
+        if (k >= max_iter) break;
+#pragma unroll
+        for (int j = 0; j < C; ++j) {
+            up[j] = u[j];
+            v[j] = s_v[j];
+        }
+        if (b < C) v64 = s_v64[b];
+        if (s_empty) flags |= FCM_FLAG_EMPTY_CLUSTER;
+        __syncthreads();  // s_v and the totals are reused by the next iteration
+    }
+#pragma unroll
+    for (int j = 0; j < C; ++j) table[b * C + j] = u[j];
+    if (b == 0) {
+        st->iters = k;
+        st->status = status;
+        st->flags = flags;
+        st->delta = (double)delta;
+        st->J = (double)tot[2 * C].hi + (double)tot[2 * C].lo;
+#pragma unroll
+        for (int j = 0; j < C; ++j) st->V[j] = v[j];
+    }
+    if (b < C) st->V64[b] = v64;
+}
+
+// U^k by table lookup: U_ij = table[x_i][j].
+template <int C>
+__global__ void __launch_bounds__(HNT) k_hist_emit(const float* __restrict__ x, int64_t n,
+                                                  const float* __restrict__ table, const HistState* st,
+                                                  float* __restrict__ U) {
+    __shared__ float T[256 * C];
+    if (st->bad) return;
+    for (int t = threadIdx.x; t < 256 * C; t += HNT) T[t] = table[t];
+    __syncthreads();
+    const int64_t stride = (int64_t)gridDim.x * HNT;
+    for (int64_t i = (int64_t)blockIdx.x * HNT + threadIdx.x; i < n; i += stride) {
+        const int b = (int)__ldg(x + i);
+#pragma unroll
+        for (int j = 0; j < C; ++j) __stcs(U + (int64_t)j * n + i, T[b * C + j]);
+    }
+}
+
+typedef void (*Pass0Fn)(const float*, const float*, int64_t, float, HistState*, double*);
+typedef void (*InitFn)(HistState*, const double*, int, float, float);
+typedef void (*Delta1Fn)(const float*, const float*, int64_t, float, float, HistState*);
+typedef void (*SolveFn)(HistState*, float*, float, float, float, int);
+typedef void (*EmitFn)(const float*, int64_t, const float*, const HistState*, float*);
+
+struct HistKernels {
+    Pass0Fn pass0[2];
+    InitFn init[2];
+    Delta1Fn delta1;
+    SolveFn solve[2];
+    EmitFn emit;
+};
+
+template <int C, int MK>
+HistKernels kernels_cm() {
+    return HistKernels{{k_hist_pass0<C, MK, false>, k_hist_pass0<C, MK, true>},
+                       {k_hist_init<C, MK, false>, k_hist_init<C, MK, true>},
+                       k_hist_delta1<C, MK>,
+                       {k_hist_solve<C, MK, false>, k_hist_solve<C, MK, true>},
+                       k_hist_emit<C>};
+}
+
+template <int C>
+HistKernels kernels_c(int mk) {
+    switch (mk) {
+        case M_TWO: return kernels_cm<C, M_TWO>();
+        case M_THREE: return kernels_cm<C, M_THREE>();
+        case M_ONE_HALF: return kernels_cm<C, M_ONE_HALF>();
+        default: return kernels_cm<C, M_GENERIC>();
+    }
+}
+
+HistKernels kernels_for(int C, int mk) {
+    switch (C) {
+        case 1: return kernels_c<1>(mk);
+        case 2: return kernels_c<2>(mk);
+        case 3: return kernels_c<3>(mk);
+        case 4: return kernels_c<4>(mk);
+        case 5: return kernels_c<5>(mk);
+        case 6: return kernels_c<6>(mk);
+        case 7: return kernels_c<7>(mk);
+        default: return kernels_c<8>(mk);
+    }
+}
+
+bool device_buffer(const void* p) {
+    cudaPointerAttributes a;
+    if (!p || cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace
+
+#define CK(call)                                              \
+    do {                                                      \
+        cudaError_t e_ = (call);                              \
+        if (e_ != cudaSuccess) return ctx_fail(h, e_, #call); \
+    } while (0)
+
+void fcm_release_hist(fcm_ctx* h) {
+    if (!h || !h->hist) return;
+    HistWorkspace* w = h->hist;
+    cudaFree(w->d_st);
+    cudaFree(w->part);
+    cudaFree(w->table);
+    cudaFreeHost(w->h_st);
+    delete w;
+    h->hist = nullptr;
+}
+
+extern "C" int fcm_run_hist(fcm_handle h, const float* x, int64_t n, int C, float m, float eps, int max_iter,
+                            int init_mode, const float* U0, float* U, float* V, fcm_report* rep) {
+    if (!h) return FCM_ERR_INVALID_ARG;
+    if (!x || !U || !V) return ctx_invalid(h, "null x, U or V");
+    if (n < 1 || n > ((int64_t)1 << 40)) return ctx_invalid(h, "n must be in [1, 2^40]");
+    if (C < 1 || C > FCM_MAX_CLUSTERS) return ctx_invalid(h, "C must be in [1, 8]");
+    if (!(m > 1.0f) || !std::isfinite(m)) return ctx_invalid(h, "m must be a finite number > 1");
+    if (!(eps >= 0.0f) || !std::isfinite(eps)) return ctx_invalid(h, "eps must be finite and >= 0");
+    if (max_iter < 1) return ctx_invalid(h, "max_iter must be >= 1");
+    if (init_mode != FCM_INIT_U && init_mode != FCM_INIT_V) return ctx_invalid(h, "bad init_mode");
+    const bool from_u = init_mode == FCM_INIT_U;
+    if (from_u && !U0) U0 = U;
+    if (!device_buffer(x) || !device_buffer(U) || (from_u && !device_buffer(U0)))
+        return ctx_invalid(h, "x, U and U0 must be device memory");
+    const bool V_dev = device_buffer(V);
+    DeviceGuard g(h->device);
+    if (!h->hist) h->hist = new HistWorkspace();
+    HistWorkspace* w = h->hist;
+    if (!w->d_st) {
+        CK(cudaMalloc(&w->d_st, sizeof(HistState)));
+        CK(cudaMallocHost(&w->h_st, sizeof(HistState)));
+        CK(cudaMalloc(&w->table, sizeof(float) * 256 * FCM_MAX_CLUSTERS));
+    }
+    const int64_t want = (n + (int64_t)HNT * HCHUNK - 1) / ((int64_t)HNT * HCHUNK);
+    const int nblocks = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)h->num_sms * 8));
+    if (w->part_blocks < nblocks) {
+        cudaFree(w->part);
+        w->part = nullptr;
+        w->part_blocks = 0;
+        CK(cudaMalloc(&w->part, sizeof(double) * 2 * FCM_MAX_CLUSTERS * nblocks));
+        w->part_blocks = nblocks;
+    }
+    HistState* hs = w->h_st;
+    std::memset(hs, 0, sizeof(HistState));
+    hs->status = FCM_ERR_TIMEOUT;  // overwritten by the solver
+    if (!from_u && !V_dev) std::memcpy(hs->V0, V, sizeof(float) * C);
+    CK(cudaMemcpyAsync(w->d_st, hs, sizeof(HistState), cudaMemcpyHostToDevice, h->stream));
+    if (!from_u && V_dev)
+        CK(cudaMemcpyAsync(&w->d_st->V0, V, sizeof(float) * C, cudaMemcpyDeviceToDevice, h->stream));
+
+    const HistKernels k = kernels_for(C, mkind_of(m));
+    const float inv_m1 = (float)(1.0 / ((double)m - 1.0));
+    const int fu = from_u ? 1 : 0;
+    k.pass0[fu]<<<nblocks, HNT, 0, h->stream>>>(x, from_u ? U0 : nullptr, n, m, w->d_st, w->part);
+    k.init[fu]<<<1, HNT, 0, h->stream>>>(w->d_st, w->part, nblocks, m, inv_m1);
+    if (from_u) k.delta1<<<nblocks, HNT, 0, h->stream>>>(x, U0, n, m, inv_m1, w->d_st);
+    k.solve[fu]<<<1, HNT, 0, h->stream>>>(w->d_st, w->table, m, inv_m1, eps, max_iter);
+    k.emit<<<nblocks, HNT, 0, h->stream>>>(x, n, w->table, w->d_st, U);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(hs, w->d_st, sizeof(HistState), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaMemcpyAsync(V, &w->d_st->V, sizeof(float) * C, V_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                       h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    if (rep) {
+        std::memset(rep, 0, sizeof(*rep));
+        rep->iters = hs->iters;
+        rep->status = hs->status;
+        rep->flags = hs->flags;
+        rep->C = C;
+        rep->delta = hs->delta;
+        rep->J = hs->J;
+        for (int j = 0; j < C; ++j) rep->V64[j] = hs->V64[j];
+        rep->launches = from_u ? 5 : 4;
+    }
+    if (hs->status == FCM_ERR_BAD_INPUT) h->last_error = "x must hold integer grey levels 0..255 (and U0 be valid)";
+    return hs->status;
+}

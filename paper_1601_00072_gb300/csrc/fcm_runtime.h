@@ -26,6 +26,7 @@ struct GraphEntry {
 
 struct BatchedWorkspace;  // fcm_batched.cu
 struct MlpWorkspace;      // fcm_mlp.cu
+struct HistWorkspace;     // fcm_hist.cu
 
 }  // namespace fcm
 
@@ -61,6 +62,7 @@ struct fcm_ctx {
     // other paths
     fcm::BatchedWorkspace* batched = nullptr;
     fcm::MlpWorkspace* mlp = nullptr;
+    fcm::HistWorkspace* hist = nullptr;
 };
 
 namespace fcm {
@@ -85,3 +87,4 @@ int ctx_grow(fcm_ctx* h, void** p, size_t* cap, size_t bytes, const char* what);
 
 void fcm_release_batched(fcm_ctx* h);
 void fcm_release_mlp(fcm_ctx* h);
+void fcm_release_hist(fcm_ctx* h);

@@ -205,6 +205,40 @@ class FCM:
         return FCMResult(U=U, V=V, iters=rep.iters, status=st, delta=rep.delta, J=rep.J,
                          V64=np.array(rep.V64[:C]), flags=rep.flags, launches=rep.launches, trace=tr)
 
+    def run_hist(self, x, C: int, m: float = 2.0, eps: float = 1e-5, max_iter: int = 300, *,
+                 U0=None, V0=None, U=None, V=None, raise_on_error: bool = True) -> FCMResult:
+        """Algorithm 1 on the 256-bin histogram (``fcm_run_hist``) for x that
+        holds integer grey levels 0..255. Same arguments and result as
+        ``run``; x, U and U0 must be CUDA tensors."""
+        import torch
+        n = _numel(x)
+        if V0 is not None:
+            mode = _lib.FCM_INIT_V
+            if V is None:
+                V = V0
+            elif V is not V0:
+                V[...] = V0
+            u0p = None
+        else:
+            mode = _lib.FCM_INIT_U
+            if U0 is None and U is None:
+                raise ValueError("give U0, V0, or U holding U^0")
+            u0p = U0
+        if U is None:
+            U = torch.empty((C, n), dtype=torch.float32, device=x.device)
+        if V is None:
+            V = torch.empty(C, dtype=torch.float32, device=x.device)
+        if _numel(U) != C * n or _numel(V) != C or (u0p is not None and _numel(u0p) != C * n):
+            raise ValueError("U and U0 must hold C*n floats and V C floats")
+        rep = _lib.fcm_report()
+        self._bind_stream()
+        st = self._lib.fcm_run_hist(self._h, _ptr(x), n, int(C), float(m), float(eps), int(max_iter), mode,
+                                    None if u0p is None else _ptr(u0p), _ptr(U), _ptr(V), ctypes.byref(rep))
+        if raise_on_error:
+            _lib.check(st, self._h)
+        return FCMResult(U=U, V=V, iters=rep.iters, status=st, delta=rep.delta, J=rep.J,
+                         V64=np.array(rep.V64[:C]), flags=rep.flags, launches=rep.launches, trace=None)
+
     def time_pass(self, x, C: int, m: float, U, V, launches: int = 20, tma: bool = True) -> float:
         """Average milliseconds per launch of the iteration pass, from
         ``launches`` back-to-back launches timed with CUDA events (U updated in
