@@ -421,6 +421,31 @@ def bench_ours(args):
                 "speedup_vs_pixel_path": (ms / args.steps) / hms,
                 "_V": Vh.cpu().numpy().astype(np.float64)}
 
+    # the same run keeping no U between iterations (FCM_OPT_RECOMPUTE)
+    recompute = None
+    if not args.no_recompute:
+        Ur = torch.empty_like(U0d)
+        Vr = torch.empty(C, dtype=torch.float32, device=dev)
+        for _ in range(args.warmup):
+            rr = h.run(xd, C, m, EPS, MAX_ITER, U0=U0d, U=Ur, V=Vr, recompute=True)
+        rs = max(3, min(args.steps, 50))
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        for _ in range(rs):
+            rr = h.run(xd, C, m, EPS, MAX_ITER, U0=U0d, U=Ur, V=Vr, recompute=True)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        rms = e0.elapsed_time(e1) / rs
+        rbytes = 2 * (4 + 4 * C) * n + (rr.iters - 1) * 4 * n + (4 + 4 * C) * n
+        recompute = {"kernel": "k_fcm_run_rc: one cooperative launch; U^{k-1} recomputed from V^{k-1}, "
+                               "x read per iteration (L2-resident), U written once",
+                     "ms_per_run": rms, "iters": rr.iters, "pixel_iter_per_s": n * rr.iters / (rms / 1e3),
+                     "bound": "alu",
+                     "dram_bytes_per_run_algorithmic": rbytes,
+                     "center_rel_err_vs_stored_U_run": float(np.max(np.abs(Vr.cpu().numpy() - Vd.cpu().numpy())
+                                                                   / np.maximum(np.abs(Vd.cpu().numpy()), 1.0))),
+                     "speedup_vs_pixel_path": (ms / args.steps) / rms}
+
     out = {
         "metric": METRIC,
         "value": value,
@@ -452,6 +477,7 @@ def bench_ours(args):
         "clocks": clocks,
         "e2e": e2e,
         "histogram_domain": hist,
+        "recompute": recompute,
     }
     if not args.no_batched:
         out["batched"] = bench_batched(h, dev, max(3, min(args.steps, 20)), 3)
@@ -525,6 +551,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the cold versus warm batch measurement")
     ap.add_argument("--no-hist", action="store_true", help="skip the histogram-domain measurement")
+    ap.add_argument("--no-recompute", action="store_true", help="skip the U-free (recompute) measurement")
     ap.add_argument("--batched-only", action="store_true",
                     help="only the cold versus warm batch measurement, printed as its own JSON object "
                          "(a profiling aid; not the benchmark line)")

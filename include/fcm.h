@@ -74,6 +74,10 @@ extern "C" {
 #define FCM_OPT_NO_TMA 4   /* plain-load pass kernel instead of the TMA-fed one */
 #define FCM_OPT_NO_PERSISTENT 8 /* one launch per pass (graph or host loop) instead of
                                     one cooperative launch for the whole run */
+#define FCM_OPT_RECOMPUTE 16 /* do not store U between iterations: recompute U^{k-1}
+                                 from V^{k-1}, so an iteration reads only x; U^k is
+                                 written once at the end (one cooperative launch;
+                                 needs n % 4 == 0 and 16-byte-aligned rows) */
 
 typedef struct fcm_ctx* fcm_handle;
 

@@ -2,7 +2,8 @@
 
 Every translation unit is compiled by its own ``nvcc -c`` process, in
 parallel, then linked with ``nvcc -shared``. The single-image pass source is
-compiled eight times, once per cluster count (``-DFCM_INST_C=1..8``), and the
+and the recompute-run source are compiled eight times each, once per cluster
+count (``-DFCM_INST_C=1..8``), and the
 two batched kernels twice each, once per block size (``-DFCM_BATCH_NT`` and
 ``-DFCM_ROUNDS_NT`` = 256, 512).
 Nothing is rebuilt when the library is newer than every source.
@@ -38,7 +39,7 @@ def _units():
     units = []
     for src in sorted(glob.glob(os.path.join(CSRC, "*.cu"))):
         base = os.path.splitext(os.path.basename(src))[0]
-        if base == "fcm_single_inst":
+        if base in ("fcm_single_inst", "fcm_recompute_inst"):
             for c in range(1, 9):
                 units.append((src, os.path.join(BUILD, f"{base}_c{c}.o"), [f"-DFCM_INST_C={c}"]))
         elif base == "fcm_batched_inst":

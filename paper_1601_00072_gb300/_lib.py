@@ -27,6 +27,7 @@ FCM_OPT_TRACE = 1
 FCM_OPT_NO_GRAPH = 2
 FCM_OPT_NO_TMA = 4
 FCM_OPT_NO_PERSISTENT = 8
+FCM_OPT_RECOMPUTE = 16
 
 
 class fcm_report(ctypes.Structure):

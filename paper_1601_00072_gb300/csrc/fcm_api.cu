@@ -26,6 +26,7 @@
 #include "fcm.h"
 #include "fcm_device.cuh"
 #include "fcm_internal.h"
+#include "fcm_recompute.h"
 #include "fcm_runtime.h"
 
 using namespace fcm;
@@ -34,9 +35,19 @@ namespace {
 
 SingleTable g_table;
 std::once_flag g_table_once;
+RcTable g_rc;
 
 void init_table() {
     std::memset(&g_table, 0, sizeof(g_table));
+    std::memset(&g_rc, 0, sizeof(g_rc));
+    register_rc_c1(g_rc);
+    register_rc_c2(g_rc);
+    register_rc_c3(g_rc);
+    register_rc_c4(g_rc);
+    register_rc_c5(g_rc);
+    register_rc_c6(g_rc);
+    register_rc_c7(g_rc);
+    register_rc_c8(g_rc);
     register_single_c1(g_table);
     register_single_c2(g_table);
     register_single_c3(g_table);
@@ -387,9 +398,14 @@ int fcm_run(fcm_handle h, const float* x, int64_t n, int C, float m, float eps, 
     const bool aligned = (n % 4 == 0) && ((uintptr_t)dx % 16 == 0) && ((uintptr_t)dU % 16 == 0) &&
                          ((uintptr_t)hs->Uprev % 16 == 0);
     int run_blocks = 0;
-    const void* krun = (const void*)g_table.run[C][mk][init_mode == FCM_INIT_U ? 0 : 1];
-    const int run_smem = g_table.run_smem[C];
-    if (aligned && h->coop && !(options & (FCM_OPT_NO_TMA | FCM_OPT_NO_PERSISTENT | FCM_OPT_NO_GRAPH))) {
+    const bool recompute = (options & FCM_OPT_RECOMPUTE) != 0;
+    const int iu = init_mode == FCM_INIT_U ? 0 : 1;
+    const void* krun = recompute ? (const void*)g_rc.run[C][mk][iu] : (const void*)g_table.run[C][mk][iu];
+    const int run_smem = recompute ? g_rc.smem[C][iu] : g_table.run_smem[C];
+    if (recompute && !(aligned && h->coop))
+        return ctx_invalid(h, "FCM_OPT_RECOMPUTE needs n % 4 == 0, 16-byte-aligned rows and cooperative launch");
+    if (recompute ||
+        (aligned && h->coop && !(options & (FCM_OPT_NO_TMA | FCM_OPT_NO_PERSISTENT | FCM_OPT_NO_GRAPH)))) {
         const int bps = blocks_per_sm(h, krun, run_smem);
         const int64_t want = (n + (int64_t)WARP_TILE * NWARP - 1) / ((int64_t)WARP_TILE * NWARP);
         run_blocks = (int)std::min<int64_t>(want, (int64_t)h->num_sms * bps);

@@ -146,14 +146,16 @@ class FCM:
 
     def run(self, x, C: int, m: float = 2.0, eps: float = 1e-5, max_iter: int = 300, *,
             U0=None, V0=None, U=None, V=None, trace: bool = False, graph: bool = True,
-            tma: bool = True, persistent: bool = True, raise_on_error: bool = True) -> FCMResult:
+            tma: bool = True, persistent: bool = True, recompute: bool = False,
+            raise_on_error: bool = True) -> FCMResult:
         """Algorithm 1 on one image.
 
         ``x``: n float32 pixels (CUDA tensor, pinned/CPU tensor or numpy).
         Start from memberships: ``U0`` [C, n] (read only), or no ``U0`` and
         ``U`` holding U^0 (updated in place). Start from centers: ``V0`` [C].
         ``U`` (allocated when None) receives U^k and ``V`` (allocated when
-        None, or V0 itself) receives V^k.
+        None, or V0 itself) receives V^k. ``recompute=True`` keeps no U
+        between iterations (``FCM_OPT_RECOMPUTE``).
         """
         import torch
         n = _numel(x)
@@ -184,7 +186,8 @@ class FCM:
         if _numel(U) != C * n or _numel(V) != C or (u0p is not None and _numel(u0p) != C * n):
             raise ValueError("U and U0 must hold C*n floats and V C floats")
         opts = ((_lib.FCM_OPT_TRACE if trace else 0) | (0 if graph else _lib.FCM_OPT_NO_GRAPH)
-                | (0 if tma else _lib.FCM_OPT_NO_TMA) | (0 if persistent else _lib.FCM_OPT_NO_PERSISTENT))
+                | (0 if tma else _lib.FCM_OPT_NO_TMA) | (0 if persistent else _lib.FCM_OPT_NO_PERSISTENT)
+                | (_lib.FCM_OPT_RECOMPUTE if recompute else 0))
         rep = _lib.fcm_report()
         self._bind_stream()
         st = self._lib.fcm_run(self._h, _ptr(x), n, int(C), float(m), float(eps), int(max_iter),

@@ -79,16 +79,16 @@ def test_phantom1024_matches_oracle(fcm):
     assert_within(rep)
 
 
-@pytest.mark.parametrize("m", [2.0, 1.5, 3.0])
-def test_volume256_matches_oracle(fcm, m):
+@pytest.mark.parametrize("m,recompute", [(2.0, False), (1.5, False), (3.0, False), (2.0, True)])
+def test_volume256_matches_oracle(fcm, m, recompute):
     """Full 16.7M-voxel run; U compared on a 200k-voxel sample."""
     x, _, u0, C = phantom.single_image("volume256")
-    g, gU, gV = gpu_run(fcm, x, C, m, u0=u0)
+    g, gU, gV = gpu_run(fcm, x, C, m, u0=u0, recompute=recompute)
     o = oracle_run(x, C, m, EPS, MAX_ITER, u0=u0, quantized=True, want_U=False)
     assert abs(g.iters - o["iters"]) <= 1
     k = min(g.iters, o["iters"])
     if g.iters > k:
-        g, gU, gV = gpu_run(fcm, x, C, m, max_iter=k, u0=u0)
+        g, gU, gV = gpu_run(fcm, x, C, m, max_iter=k, u0=u0, recompute=recompute)
     if o["iters"] > k:
         o = oracle_run(x, C, m, EPS, k, u0=u0, quantized=True, want_U=False)
     idx = np.random.default_rng(0).choice(x.size, 200_000, replace=False)
@@ -158,13 +158,14 @@ def test_every_iteration_is_one_oracle_step(fcm, m):
     assert np.all(np.diff(tr["J"]) <= 1e-6 * tr["J"][0])
 
 
-@pytest.mark.parametrize("path", ["persistent", "graph", "host_loop", "plain_loads"])
-@pytest.mark.parametrize("m", [2.0, 3.0])
+@pytest.mark.parametrize("path", ["persistent", "graph", "host_loop", "plain_loads", "recompute"])
+@pytest.mark.parametrize("m", [2.0, 3.0, 1.5, 2.5])
 def test_every_execution_path_matches_oracle(fcm, path, m):
     """One cooperative launch for the whole run (default), one launch per pass
-    in a graph WHILE loop, the host-driven loop, and the plain-load kernel."""
+    in a graph WHILE loop, the host-driven loop, the plain-load kernel, and
+    the run that recomputes U^{k-1} instead of storing it."""
     kw = {"persistent": {}, "graph": {"persistent": False}, "host_loop": {"graph": False},
-          "plain_loads": {"tma": False}}[path]
+          "plain_loads": {"tma": False}, "recompute": {"recompute": True}}[path]
     x, _, u0, C = phantom.single_image("phantom200")
     g, gU, gV = gpu_run(fcm, x, C, m, u0=u0, **kw)
     o = oracle_run(x, C, m, EPS, MAX_ITER, u0=u0)
@@ -189,6 +190,32 @@ def test_small_aligned_sizes_match_oracle(fcm, n, C):
     V0 = np.linspace(10.0, 200.0, C)
     rep, *_ = paired(fcm, x, C, 3.0, V0=V0)
     assert_within(rep)
+
+
+@pytest.mark.parametrize("n,C", [(4, 2), (132, 3), (1024, 8), (40960, 5), (65536, 1)])
+def test_recompute_small_aligned_sizes(fcm, n, C):
+    """The recompute run where warps hold fewer tiles than ring stages (or
+    none), from U^0 and from centers."""
+    side = int(np.ceil(np.sqrt(n)))
+    img, _ = phantom.phantom2d(3000 + n, side, side, 9.0)
+    x = img.reshape(-1)[:n]
+    u0 = phantom.dirichlet_u0((3000 + n, 3), C, n)
+    for kw in ({"u0": u0}, {"V0": np.linspace(10.0, 200.0, C)}):
+        g, gU, gV = gpu_run(fcm, x, C, 2.0, recompute=True, **kw)
+        o = oracle_run(x, C, 2.0, EPS, MAX_ITER, **kw)
+        k = min(g.iters, o["iters"])
+        d_iters = g.iters - o["iters"]
+        if g.iters > k:
+            g, gU, gV = gpu_run(fcm, x, C, 2.0, max_iter=k, recompute=True, **kw)
+        if o["iters"] > k:
+            o = oracle_run(x, C, 2.0, EPS, k, **kw)
+        assert_within(precision_report(gU, gV, g.iters + d_iters, o["U"], o["V"], o["iters"]))
+
+
+def test_recompute_rejects_unaligned_sizes(fcm):
+    x, _, u0, C = phantom.single_image("phantom200")
+    with pytest.raises(Exception):
+        gpu_run(fcm, x[:4001], C, 2.0, u0=u0[:, :4001], recompute=True)
 
 
 def test_graph_and_host_loop_agree_bitwise(fcm):
