@@ -188,11 +188,11 @@ def allreduce(value: float, op: str, world: int) -> float:
     return float(t.item())
 
 
-def load_workload(m: float):
+def load_workload(m: float, with_labels: bool = False):
     import phantom
-    x, _, u0, c = phantom.single_image(WORKLOAD)
+    x, lab, u0, c = phantom.single_image(WORKLOAD)
     assert c == C
-    return x, u0
+    return (x, u0, lab) if with_labels else (x, u0)
 
 
 def cpu_sample(x, u0):
@@ -325,7 +325,7 @@ def bench_ours(args):
     from paper_1601_00072_gb300.fcm import FCM
 
     m = args.m
-    x, u0 = load_workload(m)
+    x, u0, lab = load_workload(m, with_labels=True)
     n = x.size
     dev = torch.device("cuda", local)
     xd = torch.from_numpy(x.astype(np.float32)).to(dev)
@@ -446,6 +446,13 @@ def bench_ours(args):
                                                                    / np.maximum(np.abs(Vd.cpu().numpy()), 1.0))),
                      "speedup_vs_pixel_path": (ms / args.steps) / rms}
 
+    # the paper's quantitative score (Dice per tissue class, Sec. 5.2) of the
+    # timed run's segmentation against the phantom's generator labels
+    labd = torch.from_numpy(lab.astype(np.uint8)).to(dev)
+    dsc, _ = h.dsc(Ud, labd, n_classes=C, V=Vd)
+    dsc_line = {"classes": ["background", "CSF", "GM", "WM"], "dsc": [round(float(d), 6) for d in dsc],
+                "truth": "phantom generator labels", "cluster_to_class": "by ascending center"}
+
     out = {
         "metric": METRIC,
         "value": value,
@@ -478,6 +485,7 @@ def bench_ours(args):
         "e2e": e2e,
         "histogram_domain": hist,
         "recompute": recompute,
+        "segmentation_dsc": dsc_line,
     }
     if not args.no_batched:
         out["batched"] = bench_batched(h, dev, max(3, min(args.steps, 20)), 3)

@@ -165,6 +165,28 @@ int fcm_run_hist(fcm_handle h, const float* x, int64_t n, int C, float m, float 
                  int init_mode, const float* U0, float* U, float* V, fcm_report* rep);
 
 /*
+ * fcm_dsc — defuzzify a result and score it against ground truth with the
+ * Dice similarity coefficient per class (Sec. 5.2, Eq. 5):
+ * DSC_c = 2 |PR_c n GT_c| / (|PR_c| + |GT_c|).
+ *
+ *   U                 C*n floats, cluster-major, device memory (a run's U^k).
+ *                     Pixel i's label is argmax_j U[j*n + i], ties to the
+ *                     lowest j (Sec. 2.1).
+ *   truth             n bytes, device memory: the true class of each pixel, in
+ *                     [0, n_classes).
+ *   class_of_cluster  C ints, host memory: the class each cluster stands for.
+ *   n_classes         1..16.
+ *   counts            nullable, host, 3*n_classes: |PR_c|, |GT_c|, |PR_c n GT_c|.
+ *   dsc               host, n_classes doubles. A class absent from both the
+ *                     segmentation and the truth scores 1.
+ *
+ * The counts are exact integers. Returns FCM_OK, or FCM_ERR_INVALID_ARG (also
+ * for a truth label outside [0, n_classes)).
+ */
+int fcm_dsc(fcm_handle h, const float* U, int64_t n, int C, const uint8_t* truth, const int* class_of_cluster,
+            int n_classes, int64_t* counts, double* dsc);
+
+/*
  * Batched runs: many independent images ("slices") of different sizes, cluster
  * counts and fuzzifiers in one persistent launch (not in the paper, which
  * segments one image at a time; each slice follows Algorithm 1 exactly as

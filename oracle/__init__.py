@@ -70,6 +70,10 @@ def _bind(lib):
     lib.oracle_fcm.restype = ctypes.c_int
     lib.oracle_fcm_quantized.argtypes = [_u8] + common
     lib.oracle_fcm_quantized.restype = ctypes.c_int
+    if hasattr(lib, "oracle_dsc"):
+        lib.oracle_dsc.argtypes = [_i32, _u8, ctypes.c_int64, _i32, ctypes.c_int, ctypes.c_int,
+                                   ctypes.POINTER(ctypes.c_int64), _d]
+        lib.oracle_dsc.restype = ctypes.c_int
     return lib
 
 
@@ -131,6 +135,23 @@ def labels(U, L=None):
     out = np.empty(U.shape[1], dtype=np.int32)
     L.oracle_labels(_p(U), U.shape[1], U.shape[0], _p(out, _i32))
     return out
+
+
+def dsc(labels_, truth, class_of_label, n_classes, L=None):
+    """Dice similarity per class (Sec. 5.2, Eq. 5) of labels (mapped to
+    classes by class_of_label) against truth. Returns (dsc [n_classes],
+    counts [n_classes, 3] of |PR|, |GT|, |PR n GT|)."""
+    L = L or lib()
+    lab = np.ascontiguousarray(labels_, dtype=np.int32).reshape(-1)
+    tr = np.ascontiguousarray(truth, dtype=np.uint8).reshape(-1)
+    cl = np.ascontiguousarray(class_of_label, dtype=np.int32).reshape(-1)
+    out = np.empty(n_classes)
+    counts = np.empty(3 * n_classes, dtype=np.int64)
+    st = L.oracle_dsc(_p(lab, _i32), _p(tr, _u8), lab.size, _p(cl, _i32), cl.size, n_classes,
+                      counts.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), _p(out))
+    if st < 0:
+        raise ValueError("oracle rejected the arguments")
+    return out, counts.reshape(n_classes, 3)
 
 
 def _run(fn, xarg, n, C, m, eps, max_iter, U0, V0, want_U):

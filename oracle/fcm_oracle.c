@@ -309,3 +309,33 @@ int oracle_fcm_quantized(const uint8_t* xq, int64_t n, int C, double m,
     if (empty_out) *empty_out = empty;
     return status;
 }
+
+/* Dice similarity coefficient of a segmentation against ground truth, per
+ * class (Sec. 5.2, Eq. 5: DSC = 2 |PR n GT| / (|PR| + |GT|)). The segmented
+ * class of pixel i is class_of_label[labels[i]]; truth[i] is its true class.
+ * counts (3 * n_classes, nullable) receives |PR_c|, |GT_c|, |PR_c n GT_c|.
+ * A class absent from both gets DSC 1 (the two agree that it is empty). */
+int oracle_dsc(const int32_t* labels, const uint8_t* truth, int64_t n, const int32_t* class_of_label,
+               int n_labels, int n_classes, int64_t* counts, double* dsc) {
+    if (!labels || !truth || !class_of_label || !dsc || n < 1 || n_labels < 1 || n_classes < 1)
+        return ORACLE_BAD_ARG;
+    int64_t pr[256] = {0}, gt[256] = {0}, both[256] = {0};
+    if (n_classes > 256) return ORACLE_BAD_ARG;
+    for (int64_t i = 0; i < n; ++i) {
+        if (labels[i] < 0 || labels[i] >= n_labels || truth[i] >= n_classes) return ORACLE_BAD_ARG;
+        const int p = class_of_label[labels[i]], g = truth[i];
+        if (p < 0 || p >= n_classes) return ORACLE_BAD_ARG;
+        pr[p] += 1;
+        gt[g] += 1;
+        if (p == g) both[p] += 1;
+    }
+    for (int c = 0; c < n_classes; ++c) {
+        dsc[c] = (pr[c] + gt[c]) == 0 ? 1.0 : 2.0 * (double)both[c] / (double)(pr[c] + gt[c]);
+        if (counts) {
+            counts[3 * c] = pr[c];
+            counts[3 * c + 1] = gt[c];
+            counts[3 * c + 2] = both[c];
+        }
+    }
+    return 0;
+}

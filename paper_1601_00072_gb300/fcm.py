@@ -242,6 +242,28 @@ class FCM:
         return FCMResult(U=U, V=V, iters=rep.iters, status=st, delta=rep.delta, J=rep.J,
                          V64=np.array(rep.V64[:C]), flags=rep.flags, launches=rep.launches, trace=None)
 
+    def dsc(self, U, truth, n_classes: int, class_of_cluster=None, V=None):
+        """Dice similarity per class of the defuzzified U against ``truth``
+        (``fcm_dsc``). ``class_of_cluster`` maps clusters to classes; when it
+        is None, clusters are matched to classes by ascending center (``V``),
+        for classes numbered in ascending order of intensity. Returns
+        (dsc [n_classes], counts [n_classes, 3] of |PR|, |GT|, |PR n GT|)."""
+        C = int(U.shape[0])
+        n = _numel(U) // C
+        if class_of_cluster is None:
+            order = np.argsort(np.asarray(V.cpu() if hasattr(V, "cpu") else V, dtype=np.float64).reshape(-1))
+            class_of_cluster = np.empty(C, dtype=np.int32)
+            class_of_cluster[order] = np.arange(C)
+        cmap = np.ascontiguousarray(class_of_cluster, dtype=np.int32)
+        out = np.empty(n_classes)
+        counts = np.empty(3 * n_classes, dtype=np.int64)
+        self._bind_stream()
+        _lib.check(self._lib.fcm_dsc(self._h, _ptr(U), n, C, ctypes.c_void_p(truth.data_ptr()),
+                                     cmap.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), int(n_classes),
+                                     counts.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                     out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))), self._h)
+        return out, counts.reshape(n_classes, 3)
+
     def time_pass(self, x, C: int, m: float, U, V, launches: int = 20, tma: bool = True) -> float:
         """Average milliseconds per launch of the iteration pass, from
         ``launches`` back-to-back launches timed with CUDA events (U updated in

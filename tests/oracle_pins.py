@@ -232,6 +232,28 @@ def pin_quantized_matches_plain(L):
     return fails
 
 
+def pin_dsc(L):
+    """Dice similarity (Eq. 5) on a hand example with rational values, on
+    identical and on disjoint segmentations, and through a label-to-class
+    map: PR = [0, 0, 1, 1], GT = [0, 1, 1, 1] gives class 0: 2*1/(2+1) = 2/3,
+    class 1: 2*2/(2+3) = 4/5; an absent class scores 1."""
+    fails = []
+    d, c = oracle.dsc([0, 0, 1, 1], [0, 1, 1, 1], [0, 1], 3, L=L)
+    _check(fails, abs(d[0] - 2 / 3) < 1e-15 and abs(d[1] - 4 / 5) < 1e-15 and d[2] == 1.0,
+           f"dsc hand example {d}")
+    _check(fails, c.tolist() == [[2, 1, 1], [2, 3, 2], [0, 0, 0]], f"dsc counts {c.tolist()}")
+    g = np.random.default_rng(3)
+    t = g.integers(0, 4, 500)
+    d, _ = oracle.dsc(t, t, [0, 1, 2, 3], 4, L=L)
+    _check(fails, np.all(d == 1.0), f"dsc identical {d}")
+    d, _ = oracle.dsc((t + 1) % 4, t, [0, 1, 2, 3], 4, L=L)
+    _check(fails, np.all(d == 0.0), f"dsc disjoint {d}")
+    # labels 0..3 named in reverse order: mapping them back restores DSC 1
+    d, _ = oracle.dsc(3 - t, t, [3, 2, 1, 0], 4, L=L)
+    _check(fails, np.all(d == 1.0), f"dsc through a map {d}")
+    return fails
+
+
 ALL_PINS = [pin_toy_rationals, pin_singular_points, pin_closed_form_objective,
             pin_optimality, pin_special_cases, pin_descent_and_invariants,
-            pin_metamorphic, pin_quantized_matches_plain]
+            pin_metamorphic, pin_quantized_matches_plain, pin_dsc]
