@@ -187,6 +187,31 @@ int fcm_dsc(fcm_handle h, const float* U, int64_t n, int C, const uint8_t* truth
             int n_classes, int64_t* counts, double* dsc);
 
 /*
+ * fcm_run_multi — Algorithm 1 on pixels with D channels (colour, or
+ * co-registered MR sequences). Sec. 2.1 defines d_ij as a norm of x_i - v_j;
+ * here it is the Euclidean norm over the channels, so Eq. 4 uses
+ * d_ij^2 = sum_d (x_id - v_jd)^2, Eq. 3 gives each center channel by channel
+ * and Eq. 1 sums u_ij^m d_ij^2. Readings as fcm_run (zero distance, L-infinity
+ * stopping test, empty clusters). One cooperative launch per run; U^{k-1} is
+ * recomputed from V^{k-1}, so an iteration reads only x and U^k is written
+ * once at the end.
+ *
+ *   x        D*n floats, channel-major (x[d*n + i]), device memory.
+ *   D        1..4 channels.  C, m, eps, max_iter, init_mode as fcm_run.
+ *   U0       nullable; C*n floats, device, read only (FCM_INIT_U; NULL means
+ *            U holds U^0).
+ *   U        C*n floats, device. Out: U^k.
+ *   V        C*D floats, cluster-major (V[j*D + d]), device or host. In: V^0
+ *            with FCM_INIT_V. Out: V^k.
+ *   V64      nullable, host, C*D doubles: the FP64 quotients behind V^k.
+ *   rep      nullable; its V64 holds the first min(C*D, 8) of them.
+ *
+ * Returns as fcm_run.
+ */
+int fcm_run_multi(fcm_handle h, const float* x, int64_t n, int D, int C, float m, float eps, int max_iter,
+                  int init_mode, const float* U0, float* U, float* V, double* V64, fcm_report* rep);
+
+/*
  * Batched runs: many independent images ("slices") of different sizes, cluster
  * counts and fuzzifiers in one persistent launch (not in the paper, which
  * segments one image at a time; each slice follows Algorithm 1 exactly as

@@ -70,6 +70,17 @@ def _bind(lib):
     lib.oracle_fcm.restype = ctypes.c_int
     lib.oracle_fcm_quantized.argtypes = [_u8] + common
     lib.oracle_fcm_quantized.restype = ctypes.c_int
+    if hasattr(lib, "oracle_fcm_multi"):
+        lib.oracle_memberships_multi.argtypes = [_d, ctypes.c_int64, ctypes.c_int, ctypes.c_int,
+                                                 ctypes.c_double, _d, _d]
+        lib.oracle_memberships_multi.restype = None
+        lib.oracle_objective_multi.argtypes = [_d, ctypes.c_int64, ctypes.c_int, ctypes.c_int,
+                                               ctypes.c_double, _d, _d]
+        lib.oracle_objective_multi.restype = ctypes.c_double
+        lib.oracle_fcm_multi.argtypes = [_d, ctypes.c_int64, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                         ctypes.c_double, ctypes.c_int, ctypes.c_int, _d, _d, _d, _i, _d,
+                                         _d, _i]
+        lib.oracle_fcm_multi.restype = ctypes.c_int
     if hasattr(lib, "oracle_dsc"):
         lib.oracle_dsc.argtypes = [_i32, _u8, ctypes.c_int64, _i32, ctypes.c_int, ctypes.c_int,
                                    ctypes.POINTER(ctypes.c_int64), _d]
@@ -135,6 +146,44 @@ def labels(U, L=None):
     out = np.empty(U.shape[1], dtype=np.int32)
     L.oracle_labels(_p(U), U.shape[1], U.shape[0], _p(out, _i32))
     return out
+
+
+def memberships_multi(x, V, m, L=None):
+    """Eq. 4 with the Euclidean norm over D channels: x [D, n], V [C, D]."""
+    L = L or lib()
+    x = _f64(x)
+    V = _f64(V)
+    D, n = x.shape
+    U = np.empty((V.shape[0], n))
+    L.oracle_memberships_multi(_p(x), n, D, V.shape[0], float(m), _p(V), _p(U))
+    return U
+
+
+def objective_multi(x, U, V, m, L=None):
+    L = L or lib()
+    x, U, V = _f64(x), _f64(U), _f64(V)
+    return L.oracle_objective_multi(_p(x), x.shape[1], x.shape[0], V.shape[0], float(m), _p(U), _p(V))
+
+
+def fcm_multi(x, C, m, eps, max_iter, U0=None, V0=None, want_U=True, L=None):
+    """Algorithm 1 on D-channel pixels: x [D, n]; give U0 [C, n] or V0 [C, D].
+    Returns U, V [C, D], iters, status, delta/J traces, empty."""
+    L = L or lib()
+    x = _f64(x)
+    D, n = x.shape
+    if (U0 is None) == (V0 is None):
+        raise ValueError("give exactly one of U0 and V0")
+    mode, init = (INIT_U, _f64(U0).reshape(C, n)) if U0 is not None else (INIT_V, _f64(V0).reshape(C, D))
+    U = np.empty((C, n)) if want_U else None
+    V = np.empty((C, D))
+    iters, empty = ctypes.c_int(0), ctypes.c_int(0)
+    td, tJ = np.zeros(max_iter), np.zeros(max_iter)
+    st = L.oracle_fcm_multi(_p(x), n, D, C, float(m), float(eps), int(max_iter), mode, _p(init), _p(U), _p(V),
+                            ctypes.byref(iters), _p(td), _p(tJ), ctypes.byref(empty))
+    if st < 0:
+        raise ValueError(f"oracle rejected the arguments (status {st})")
+    k = iters.value
+    return {"U": U, "V": V, "iters": k, "status": st, "delta": td[:k], "J": tJ[:k], "empty": empty.value}
 
 
 def dsc(labels_, truth, class_of_label, n_classes, L=None):

@@ -339,3 +339,126 @@ int oracle_dsc(const int32_t* labels, const uint8_t* truth, int64_t n, const int
     }
     return 0;
 }
+
+/*
+ * Multi-feature FCM: each pixel is a vector x_i of D channels (Sec. 2.1
+ * defines d_ij as a norm of x_i - v_j; here the Euclidean norm), each center
+ * a vector v_j. Eq. 4 with d_ij = ||x_i - v_j||, Eq. 3 per channel, Eq. 1 with
+ * ||x_i - v_j||^2, and the loop and readings of oracle_fcm. x is channel-major
+ * (x[d*n + i]); V and V^0 are cluster-major (V[j*D + d]); U is [C][n].
+ */
+static void membership_of_vector(const double* x, int64_t n, int64_t i, int D, int C, double m,
+                                 const double* V, double* u) {
+    double dist[64];
+    int nzero = 0;
+    for (int j = 0; j < C; ++j) {
+        double s = 0.0;
+        for (int d = 0; d < D; ++d) {
+            const double t = x[(int64_t)d * n + i] - V[j * D + d];
+            s += t * t;
+        }
+        dist[j] = sqrt(s);
+        if (dist[j] == 0.0) ++nzero;
+    }
+    if (nzero > 0) {
+        for (int j = 0; j < C; ++j) u[j] = dist[j] == 0.0 ? 1.0 / nzero : 0.0;
+        return;
+    }
+    const double e = 2.0 / (m - 1.0);
+    for (int j = 0; j < C; ++j) {
+        double s = 0.0;
+        for (int k = 0; k < C; ++k) s += pow(dist[j] / dist[k], e);
+        u[j] = 1.0 / s;
+    }
+}
+
+void oracle_memberships_multi(const double* x, int64_t n, int D, int C, double m, const double* V,
+                              double* U) {
+    double u[64];
+    for (int64_t i = 0; i < n; ++i) {
+        membership_of_vector(x, n, i, D, C, m, V, u);
+        for (int j = 0; j < C; ++j) U[(int64_t)j * n + i] = u[j];
+    }
+}
+
+/* Eq. 3 per channel; an empty cluster keeps Vprev (or 0). Returns the count
+ * of empty clusters. */
+static int centers_multi(const double* x, int64_t n, int D, int C, double m, const double* U,
+                         const double* Vprev, double* V) {
+    int empty = 0;
+    for (int j = 0; j < C; ++j) {
+        double den = 0.0, num[16] = {0};
+        const double* Uj = U + (int64_t)j * n;
+        for (int64_t i = 0; i < n; ++i) {
+            const double w = pow(Uj[i], m);
+            den += w;
+            for (int d = 0; d < D; ++d) num[d] += w * x[(int64_t)d * n + i];
+        }
+        for (int d = 0; d < D; ++d) {
+            if (den > 0.0) V[j * D + d] = num[d] / den;
+            else V[j * D + d] = Vprev ? Vprev[j * D + d] : 0.0;
+        }
+        if (!(den > 0.0)) ++empty;
+    }
+    return empty;
+}
+
+double oracle_objective_multi(const double* x, int64_t n, int D, int C, double m, const double* U,
+                              const double* V) {
+    double J = 0.0;
+    for (int64_t i = 0; i < n; ++i)
+        for (int j = 0; j < C; ++j) {
+            double s = 0.0;
+            for (int d = 0; d < D; ++d) {
+                const double t = x[(int64_t)d * n + i] - V[j * D + d];
+                s += t * t;
+            }
+            J += pow(U[(int64_t)j * n + i], m) * s;
+        }
+    return J;
+}
+
+int oracle_fcm_multi(const double* x, int64_t n, int D, int C, double m, double eps, int max_iter,
+                     int init_mode, const double* init, double* U_out, double* V_out, int* iters,
+                     double* trace_delta, double* trace_J, int* empty_out) {
+    if (check_args(n, C, m, eps, max_iter) || D < 1 || D > 16) return ORACLE_BAD_ARG;
+    if (!x || !init || !V_out || !iters) return ORACLE_BAD_ARG;
+    const int64_t cn = (int64_t)C * n;
+    double* Uprev = (double*)malloc(sizeof(double) * cn);
+    double* Ucur = (double*)malloc(sizeof(double) * cn);
+    if (!Uprev || !Ucur) { free(Uprev); free(Ucur); return ORACLE_NO_MEMORY; }
+    double V[64 * 16], Vnext[64 * 16];
+    int empty = 0;
+    if (init_mode == ORACLE_INIT_U) {
+        memcpy(Uprev, init, sizeof(double) * cn);
+    } else if (init_mode == ORACLE_INIT_V) {
+        oracle_memberships_multi(x, n, D, C, m, init, Uprev);
+    } else {
+        free(Uprev); free(Ucur);
+        return ORACLE_BAD_ARG;
+    }
+    {
+        double zero[64 * 16] = {0};
+        empty += centers_multi(x, n, D, C, m, Uprev, init_mode == ORACLE_INIT_V ? init : zero, V);
+    }
+    int status = ORACLE_NOT_CONVERGED;
+    int k;
+    for (k = 1; k <= max_iter; ++k) {
+        oracle_memberships_multi(x, n, D, C, m, V, Ucur);
+        const double delta = oracle_max_abs_diff(Ucur, Uprev, cn);
+        if (trace_delta) trace_delta[k - 1] = delta;
+        if (trace_J) trace_J[k - 1] = oracle_objective_multi(x, n, D, C, m, Ucur, V);
+        if (delta < eps) { status = ORACLE_CONVERGED; break; }
+        if (k == max_iter) break;
+        empty += centers_multi(x, n, D, C, m, Ucur, V, Vnext);
+        memcpy(V, Vnext, sizeof(double) * C * D);
+        double* t = Uprev; Uprev = Ucur; Ucur = t;
+    }
+    if (k > max_iter) k = max_iter;
+    *iters = k;
+    memcpy(V_out, V, sizeof(double) * C * D);
+    if (U_out) memcpy(U_out, Ucur, sizeof(double) * cn);
+    if (empty_out) *empty_out = empty;
+    free(Uprev); free(Ucur);
+    return status;
+}

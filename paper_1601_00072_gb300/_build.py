@@ -45,6 +45,9 @@ def _units():
         elif base == "fcm_batched_inst":
             for nt in (256, 512):
                 units.append((src, os.path.join(BUILD, f"{base}_nt{nt}.o"), [f"-DFCM_BATCH_NT={nt}"]))
+        elif base == "fcm_multi_inst":
+            for d in (1, 2, 3, 4):
+                units.append((src, os.path.join(BUILD, f"{base}_d{d}.o"), [f"-DFCM_MULTI_D={d}"]))
         elif base == "fcm_rounds_inst":
             for nt in (256, 512):
                 units.append((src, os.path.join(BUILD, f"{base}_nt{nt}.o"), [f"-DFCM_ROUNDS_NT={nt}"]))

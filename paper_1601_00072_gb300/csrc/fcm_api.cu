@@ -303,6 +303,7 @@ void fcm_destroy(fcm_handle h) {
         fcm_release_batched(h);
         fcm_release_mlp(h);
         fcm_release_hist(h);
+        fcm_release_multi(h);
     }
     delete h;
 }

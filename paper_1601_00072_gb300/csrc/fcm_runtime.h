@@ -27,6 +27,7 @@ struct GraphEntry {
 struct BatchedWorkspace;  // fcm_batched.cu
 struct MlpWorkspace;      // fcm_mlp.cu
 struct HistWorkspace;     // fcm_hist.cu
+struct MultiWorkspace;    // fcm_multi.cu
 
 }  // namespace fcm
 
@@ -63,6 +64,7 @@ struct fcm_ctx {
     fcm::BatchedWorkspace* batched = nullptr;
     fcm::MlpWorkspace* mlp = nullptr;
     fcm::HistWorkspace* hist = nullptr;
+    fcm::MultiWorkspace* multi = nullptr;
 };
 
 namespace fcm {
@@ -88,3 +90,4 @@ int ctx_grow(fcm_ctx* h, void** p, size_t* cap, size_t bytes, const char* what);
 void fcm_release_batched(fcm_ctx* h);
 void fcm_release_mlp(fcm_ctx* h);
 void fcm_release_hist(fcm_ctx* h);
+void fcm_release_multi(fcm_ctx* h);

@@ -242,6 +242,42 @@ class FCM:
         return FCMResult(U=U, V=V, iters=rep.iters, status=st, delta=rep.delta, J=rep.J,
                          V64=np.array(rep.V64[:C]), flags=rep.flags, launches=rep.launches, trace=None)
 
+    def run_multi(self, x, C: int, m: float = 2.0, eps: float = 1e-5, max_iter: int = 300, *,
+                  U0=None, V0=None, U=None, V=None, raise_on_error: bool = True) -> FCMResult:
+        """Algorithm 1 on pixels of D channels (``fcm_run_multi``): ``x`` is a
+        CUDA tensor [D, n]; ``V0``/``V`` are [C, D]; ``U0``/``U`` [C, n]. The
+        result's V64 holds the FP64 centers, shape [C, D]."""
+        import torch
+        D, n = int(x.shape[0]), int(x.shape[1])
+        if V0 is not None:
+            mode = _lib.FCM_INIT_V
+            if V is None:
+                V = V0
+            elif V is not V0:
+                V[...] = V0
+            u0p = None
+        else:
+            mode = _lib.FCM_INIT_U
+            if U0 is None and U is None:
+                raise ValueError("give U0, V0, or U holding U^0")
+            u0p = U0
+        if U is None:
+            U = torch.empty((C, n), dtype=torch.float32, device=x.device)
+        if V is None:
+            V = torch.empty((C, D), dtype=torch.float32, device=x.device)
+        if _numel(U) != C * n or _numel(V) != C * D or (u0p is not None and _numel(u0p) != C * n):
+            raise ValueError("U and U0 must hold C*n floats and V C*D floats")
+        v64 = np.empty(C * D)
+        rep = _lib.fcm_report()
+        self._bind_stream()
+        st = self._lib.fcm_run_multi(self._h, _ptr(x), n, D, int(C), float(m), float(eps), int(max_iter), mode,
+                                     None if u0p is None else _ptr(u0p), _ptr(U), _ptr(V),
+                                     v64.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), ctypes.byref(rep))
+        if raise_on_error:
+            _lib.check(st, self._h)
+        return FCMResult(U=U, V=V, iters=rep.iters, status=st, delta=rep.delta, J=rep.J,
+                         V64=v64.reshape(C, D), flags=rep.flags, launches=rep.launches, trace=None)
+
     def dsc(self, U, truth, n_classes: int, class_of_cluster=None, V=None):
         """Dice similarity per class of the defuzzified U against ``truth``
         (``fcm_dsc``). ``class_of_cluster`` maps clusters to classes; when it

@@ -103,6 +103,23 @@ def phantom2d(seed: int, H: int, W: int, sigma: float,
     return img, lab
 
 
+def multichannel2d(seed: int, H: int, W: int, sigma: float, contrasts):
+    """One nested-ellipse layout rendered once per channel with that
+    channel's class means (``contrasts[d]``) and its own Gaussian noise, as
+    co-registered images of different tissue contrast.
+
+    Returns ``(image uint8 [D, H*W], labels uint8 [H*W])``.
+    """
+    g = rng(seed)
+    params = _ellipse_params(g, len(contrasts[0]), H, W)
+    lab = _label_map_2d(params, H, W)
+    chans = []
+    for d, means in enumerate(contrasts):
+        mu = np.asarray(means, dtype=np.float64)[lab]
+        chans.append(_to_uint8(mu + rng(seed, 1000 + d).normal(0.0, sigma, size=(H, W))).reshape(-1))
+    return np.stack(chans), lab.reshape(-1)
+
+
 # ---------------------------------------------------------------------------
 # 3-D phantom
 # ---------------------------------------------------------------------------

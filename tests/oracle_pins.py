@@ -254,6 +254,46 @@ def pin_dsc(L):
     return fails
 
 
+def pin_multi_feature(L):
+    """Multi-feature FCM (Euclidean norm over D channels):
+    * a 2-D hand example with rational memberships: V = [(0,0), (6,8)],
+      pixels (3,4), (0,3), (6,0), m = 2 give u_1 = 1/2, 61/70, 16/25, and
+      J = 25/2 + 549/70 + 2304/100 (closed form 1 / sum_k 1/d_k^2 per pixel);
+    * one channel reproduces the scalar oracle; two identical channels give
+      the scalar memberships and the scalar centers in both channels;
+    * rotating the feature plane rotates V and leaves U unchanged;
+      translating it translates V."""
+    fails = []
+    x = np.array([[3.0, 0.0, 6.0], [4.0, 3.0, 0.0]])
+    V = np.array([[0.0, 0.0], [6.0, 8.0]])
+    U = oracle.memberships_multi(x, V, 2.0, L=L)
+    ref = np.array([[1 / 2, 61 / 70, 16 / 25], [1 / 2, 9 / 70, 9 / 25]])
+    _check(fails, np.allclose(U, ref, rtol=0, atol=1e-15), f"multi toy U {U.tolist()}")
+    J = oracle.objective_multi(x, U, V, 2.0, L=L)
+    _check(fails, abs(J - (25 / 2 + 549 / 70 + 2304 / 100)) < 1e-12, f"multi toy J {J}")
+    img, _ = phantom.phantom2d(11, 30, 30, 8.0)
+    xs = img.reshape(-1).astype(np.float64)
+    u0 = phantom.dirichlet_u0((11, 1), 3, xs.size).astype(np.float64)
+    a = oracle.fcm(xs, 3, 2.0, 1e-9, 200, U0=u0, L=L)
+    b = oracle.fcm_multi(xs[None, :], 3, 2.0, 1e-9, 200, U0=u0, L=L)
+    _check(fails, a["iters"] == b["iters"] and np.max(np.abs(a["U"] - b["U"])) < 1e-12
+           and np.max(np.abs(a["V"] - b["V"][:, 0])) < 1e-9, "multi D=1 vs scalar")
+    c = oracle.fcm_multi(np.stack([xs, xs]), 3, 2.0, 1e-9, 200, U0=u0, L=L)
+    _check(fails, c["iters"] == a["iters"] and np.max(np.abs(c["U"] - a["U"])) < 1e-12
+           and np.max(np.abs(c["V"] - np.stack([a["V"], a["V"]], 1))) < 1e-9, "multi duplicated channel")
+    g = np.random.default_rng(4)
+    x2 = np.stack([xs, g.permutation(xs)])
+    th = 0.7
+    R = np.array([[np.cos(th), -np.sin(th)], [np.sin(th), np.cos(th)]])
+    d = oracle.fcm_multi(x2, 3, 2.0, 1e-9, 60, U0=u0, L=L)
+    e = oracle.fcm_multi(R @ x2, 3, 2.0, 1e-9, 60, U0=u0, L=L)
+    _check(fails, d["iters"] == e["iters"] and np.max(np.abs(d["U"] - e["U"])) < 1e-9
+           and np.max(np.abs(d["V"] @ R.T - e["V"])) < 1e-7, "multi rotation")
+    f = oracle.fcm_multi(x2 + np.array([[5.0], [-3.0]]), 3, 2.0, 1e-9, 60, U0=u0, L=L)
+    _check(fails, np.max(np.abs(f["V"] - (d["V"] + np.array([5.0, -3.0])))) < 1e-7, "multi translation")
+    return fails
+
+
 ALL_PINS = [pin_toy_rationals, pin_singular_points, pin_closed_form_objective,
             pin_optimality, pin_special_cases, pin_descent_and_invariants,
-            pin_metamorphic, pin_quantized_matches_plain, pin_dsc]
+            pin_metamorphic, pin_quantized_matches_plain, pin_dsc, pin_multi_feature]

@@ -16,7 +16,8 @@ SRC = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
                    "oracle", "fcm_oracle.c")
 
 MUTANTS = {
-    "exponent_1_over_m-1": ("const double e = 2.0 / (m - 1.0);", "const double e = 1.0 / (m - 1.0);"),
+    "exponent_1_over_m-1": ("    const double e = 2.0 / (m - 1.0);\n    for (int j = 0; j < C; ++j) {\n        const double dij",
+                            "    const double e = 1.0 / (m - 1.0);\n    for (int j = 0; j < C; ++j) {\n        const double dij"),
     "ratio_transposed": ("s += pow(dij / dik, e);", "s += pow(dik / dij, e);"),
     "center_weight_not_powered": ("            const double w = pow(Uj[i], m);\n            num += w * x[i];",
                                   "            const double w = Uj[i];\n            num += w * x[i];"),
@@ -27,7 +28,11 @@ MUTANTS = {
     "stop_not_strict": ("        if (delta < eps) { status = ORACLE_CONVERGED; break; }\n        if (k == max_iter) break;\n        empty += oracle_centers",
                         "        if (delta <= eps) { status = ORACLE_CONVERGED; break; }\n        if (k == max_iter) break;\n        empty += oracle_centers"),
     "zero_distance_share_not_split": ("u[j] = (xi == V[j]) ? 1.0 / nzero : 0.0;", "u[j] = (xi == V[j]) ? 1.0 : 0.0;"),
-    "no_swap_of_previous_U": ("double* t = Uprev; Uprev = Ucur; Ucur = t;", "double* t = Ucur; (void)t;"),
+    "no_swap_of_previous_U": ("memcpy(V, Vnext, sizeof(double) * C);\n        double* t = Uprev; Uprev = Ucur; Ucur = t;",
+                              "memcpy(V, Vnext, sizeof(double) * C);\n        double* t = Ucur; (void)t;"),
+    "multi_squared_distance_as_norm": ("dist[j] = sqrt(s);", "dist[j] = s;"),
+    "multi_center_ignores_channel": ("for (int d = 0; d < D; ++d) num[d] += w * x[(int64_t)d * n + i];",
+                                     "for (int d = 0; d < D; ++d) num[d] += w * x[i];"),
     "delta_without_abs": ("const double d = fabs(a[t] - b[t]);", "const double d = (a[t] - b[t]);"),
     "labels_ties_to_highest": ("if (u > bu) { bu = u; best = j; }", "if (u >= bu) { bu = u; best = j; }"),
     "quantized_drops_count": ("                num += h[b] * w * val[b];\n                den += h[b] * w;\n            }\n            if (den > 0.0) Vnext",
