@@ -155,6 +155,25 @@ __device__ __forceinline__ void slice_reduce(BatchShared& sh, SliceAcc<C>& a, un
     __syncthreads();
 }
 
+// Where a CTA reads its share of x during the iterations: FP32 values (in
+// shared memory, or in global memory when the share does not fit), or bytes
+// in shared memory when every value of the share is an integer grey level
+// 0..255 (exact, and four times the pixels per byte of shared memory). The
+// choice is the same for the whole CTA.
+struct XSrc {
+    const float* f;
+    const uint8_t* b;
+    bool bytes;
+    __device__ __forceinline__ float at(int i) const { return bytes ? (float)b[i] : f[i]; }
+    __device__ __forceinline__ float2 pair(int q) const {
+        if (bytes) {
+            const uchar2 v = *reinterpret_cast<const uchar2*>(b + 2 * q);
+            return make_float2((float)v.x, (float)v.y);
+        }
+        return *reinterpret_cast<const float2*>(f + 2 * q);
+    }
+};
+
 template <int C, int MK>
 __device__ __noinline__ void process_slice(const SliceDesc& d, SliceResult& res, unsigned r, unsigned K, float* xs,
                                            BatchShared& sh) {
@@ -163,12 +182,23 @@ __device__ __noinline__ void process_slice(const SliceDesc& d, SliceResult& res,
     share += share & 1;  // even, so only the last pixel of the slice can be unpaired
     const int64_t lo = min(n, (int64_t)r * share), hi = min(n, lo + share);
     const int cnt = (int)(hi - lo);
-    const bool staged = cnt <= XCAP;
     if (threadIdx.x < C) sh.vcur[threadIdx.x] = sh.vprev[threadIdx.x] = d.V0[threadIdx.x];
-    if (staged)
+    XSrc xl{d.x + lo, reinterpret_cast<const uint8_t*>(xs), false};
+    if (cnt <= XCAP) {
         for (int i = threadIdx.x; i < cnt; i += NTB) xs[i] = __ldg(d.x + lo + i);
+        xl.f = xs;
+    } else if (cnt <= 4 * XCAP) {
+        uint8_t* xb = reinterpret_cast<uint8_t*>(xs);
+        bool ok = true;
+        for (int i = threadIdx.x; i < cnt; i += NTB) {
+            const float v = __ldg(d.x + lo + i);
+            const bool g = v >= 0.0f && v <= 255.0f && v == rintf(v);
+            ok &= g;
+            xb[i] = g ? (uint8_t)v : (uint8_t)0;
+        }
+        xl.bytes = __syncthreads_and(ok);
+    }
     __syncthreads();
-    const float* xl = staged ? xs : d.x + lo;
     const int npair = cnt >> 1;
     const bool odd_tail = (cnt & 1) && threadIdx.x == 0;  // the slice's last pixel, alone
     const float m = d.m, inv_m1 = d.inv_m1;
@@ -197,7 +227,7 @@ __device__ __noinline__ void process_slice(const SliceDesc& d, SliceResult& res,
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
                 const int i = 2 * p + h;
-                const float xi = xl[i];
+                const float xi = xl.at(i);
                 a.bad |= !finite_f(xi);
                 if (from_u) {
 #pragma unroll
@@ -226,7 +256,7 @@ __device__ __noinline__ void process_slice(const SliceDesc& d, SliceResult& res,
         }
     }
     if (odd_tail) {
-        const float xi = xl[cnt - 1];
+        const float xi = xl.at(cnt - 1);
         a.bad |= !finite_f(xi);
 #pragma unroll
         for (int j = 0; j < C; ++j) {
@@ -279,7 +309,7 @@ __device__ __noinline__ void process_slice(const SliceDesc& d, SliceResult& res,
 #pragma unroll
                 for (int j = 0; j < C; ++j) num2[j] = den2[j] = pack2(0.0f, 0.0f);
                 for (int q = 0, p = p0; q < CHUNK && p < npair; ++q, p += NTB) {
-                    const float2 xv = *reinterpret_cast<const float2*>(xl + 2 * p);
+                    const float2 xv = xl.pair(p);
                     const f2 xq = pack2(xv.x, xv.y);
                     f2 u2[C], um2[C];
                     J2 = add2(J2, membership_pair<C, MK>(xq, v2, m, inv_m1, v, u2, um2));
@@ -311,7 +341,7 @@ __device__ __noinline__ void process_slice(const SliceDesc& d, SliceResult& res,
                 df_add(a.s[2 * C], lo2(J2) + hi2(J2));
             }
             if (odd_tail) {
-                const float xi = xl[cnt - 1];
+                const float xi = xl.at(cnt - 1);
                 float u[C], um[C], uo[C], umo[C];
                 df_add(a.s[2 * C], membership<C, MK>(xi, v, m, inv_m1, u, um));
                 if (prev_given) {
@@ -361,7 +391,7 @@ __device__ __noinline__ void process_slice(const SliceDesc& d, SliceResult& res,
         // ---- U^k, written once ----
         float* U = d.U;
         for (int p = threadIdx.x; p < npair; p += NTB) {
-            const float2 xv = *reinterpret_cast<const float2*>(xl + 2 * p);
+            const float2 xv = xl.pair(p);
             f2 u2[C], um2[C];
             membership_pair<C, MK>(pack2(xv.x, xv.y), v2, m, inv_m1, v, u2, um2);
 #pragma unroll
@@ -375,7 +405,7 @@ __device__ __noinline__ void process_slice(const SliceDesc& d, SliceResult& res,
         }
         if (odd_tail) {
             float u[C], um[C];
-            membership<C, MK>(xl[cnt - 1], v, m, inv_m1, u, um);
+            membership<C, MK>(xl.at(cnt - 1), v, m, inv_m1, u, um);
 #pragma unroll
             for (int j = 0; j < C; ++j) __stcs(U + (int64_t)j * n + lo + cnt - 1, u[j]);
         }
