@@ -17,7 +17,7 @@ fixed point whose J is no larger than the cold start's.
 
 Command line (writes the model file the warm-start runs load):
 
-    python -m paper_1601_00072_gb300.warmstart --n-train 20000 \
+    python -m paper_1601_00072_gb300.warmstart --n-train 60000 \
         --out paper_1601_00072_gb300/data/warmstart.fcmw
 """
 from __future__ import annotations
@@ -122,7 +122,7 @@ def train(fcm, feats, targets, Cs, epochs=200, batch=256, lr=2e-3, seed=0):
 
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
-    ap.add_argument("--n-train", type=int, default=20000)
+    ap.add_argument("--n-train", type=int, default=60000)
     ap.add_argument("--epochs", type=int, default=200)
     ap.add_argument("--batch", type=int, default=256)
     ap.add_argument("--lr", type=float, default=2e-3)
