@@ -74,6 +74,7 @@ __device__ __forceinline__ int ld_dsmem_s32(const int* local, unsigned rank) {
 struct BatchShared {
     float w[NWB][2 * SBMAX];  // warp totals: (hi, lo) of each sum, then the maxima
     double red[2][SBMAX];     // block totals, double-buffered for the cluster exchange
+    double xch[8][SBMAX];     // every rank's block totals, gathered for the rank-order sum
     double tot[SBMAX];        // slice totals (the same on every rank)
     double vq[FCM_MAX_CLUSTERS];  // next centers, FP64 quotients
     float vcur[FCM_MAX_CLUSTERS], vprev[FCM_MAX_CLUSTERS];  // centers, for the scalar path
@@ -133,13 +134,14 @@ __device__ __forceinline__ void slice_reduce(BatchShared& sh, SliceAcc<C>& a, un
     }
     if (K > 1) {
         cluster_sync();
+        // all remote reads at once (one thread per rank and value), then the
+        // sums in rank order
+        for (int t = threadIdx.x; t < (int)K * S; t += NTB) sh.xch[t / S][t % S] = ld_dsmem_f64(&sh.red[parity][t % S], t / S);
+        __syncthreads();
         if (threadIdx.x < S) {
             const int s = threadIdx.x;
-            double t = ld_dsmem_f64(&sh.red[parity][s], 0);
-            for (unsigned q = 1; q < K; ++q) {
-                const double u = ld_dsmem_f64(&sh.red[parity][s], q);
-                t = (s < NS) ? t + u : fmax(t, u);
-            }
+            double t = sh.xch[0][s];
+            for (unsigned q = 1; q < K; ++q) t = (s < NS) ? t + sh.xch[q][s] : fmax(t, sh.xch[q][s]);
             sh.tot[s] = t;
         }
     } else {

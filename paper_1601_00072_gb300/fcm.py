@@ -94,6 +94,11 @@ class Batch:
         self.arr["init_mode"] = self._init["init_mode"]
         self.arr["V0"] = self._init["V0"]
 
+    def read_back(self):
+        """Copy the last run's per-slice results from ``arr`` into the Slice
+        fields (iters, status, flags, delta, J, V64, init, V0_warm)."""
+        FCM._read_back(self.arr, self.slices)
+
     def __len__(self):
         return len(self.slices)
 
@@ -346,30 +351,36 @@ class FCM:
     def _read_back(a, slices):
         iters, status, flags = a["iters"].tolist(), a["status"].tolist(), a["flags"].tolist()
         delta, J, modes = a["delta"].tolist(), a["J"].tolist(), a["init_mode"].tolist()
-        V64 = a["V64"]
+        V64, V0 = a["V64"].copy(), a["V0"]
         for i, s in enumerate(slices):
             s.iters, s.status, s.flags, s.delta, s.J = iters[i], status[i], flags[i], delta[i], J[i]
-            s.V64 = V64[i, :s.C].copy()
+            s.V64 = V64[i, :s.C]
+            warm = modes[i] == _lib.FCM_INIT_V and s.V0 is None
             s.init = "V" if modes[i] == _lib.FCM_INIT_V else "U"
+            s.V0_warm = V0[i, :s.C].copy() if warm else None
 
     def _batch_opts(self, tune, retune, graph):
         return ((0 if tune else _lib.FCM_BATCH_NO_TUNE) | (_lib.FCM_BATCH_RETUNE if retune else 0)
                 | (0 if graph else _lib.FCM_BATCH_NO_GRAPH))
 
     def run_batched(self, slices, tune: bool = True, retune: bool = False, graph: bool = True,
-                    raise_on_error: bool = False) -> int:
+                    raise_on_error: bool = False, read_back: bool = True) -> int:
         """Algorithm 1 on every slice in one persistent launch (see
         ``fcm_run_batched``). Fills each Slice's U, V and result fields and
-        returns the aggregate status."""
+        returns the aggregate status. With a ``Batch`` and ``read_back=False``
+        the per-slice results stay in ``batch.arr`` (host memory) until
+        ``batch.read_back()``; U and V are written either way."""
         b = _as_batch(slices)
         self._bind_stream()
         st = self._lib.fcm_run_batched(self._h, self._arr_ptr(b.arr), len(b), self._batch_opts(tune, retune, graph))
         if st in (_lib.FCM_ERR_INVALID_ARG, _lib.FCM_ERR_CUDA, _lib.FCM_ERR_OOM) or raise_on_error:
             _lib.check(st, self._h)
-        self._read_back(b.arr, b.slices)
+        if read_back or not isinstance(slices, Batch):
+            b.read_back()
         return st
 
-    def run_batched_warm(self, slices, tune: bool = True, retune: bool = False, graph: bool = True):
+    def run_batched_warm(self, slices, tune: bool = True, retune: bool = False, graph: bool = True,
+                         read_back: bool = True):
         """Warm-started batch (``fcm_run_batched_warm``): predicted V^0, with the
         plain cold start (each slice's U0) as the fallback. Returns
         (status, number of slices that ran cold). ``s.init`` tells which."""
@@ -380,9 +391,8 @@ class FCM:
                                             self._batch_opts(tune, retune, graph), ctypes.byref(cold))
         if st in (_lib.FCM_ERR_INVALID_ARG, _lib.FCM_ERR_CUDA, _lib.FCM_ERR_OOM):
             _lib.check(st, self._h)
-        self._read_back(b.arr, b.slices)
-        for i, sl in enumerate(b.slices):
-            sl.V0_warm = b.arr["V0"][i, :sl.C].copy() if sl.init == "V" else None
+        if read_back or not isinstance(slices, Batch):
+            b.read_back()
         return st, cold.value
 
     # ---- warm-start network ------------------------------------------------
