@@ -55,6 +55,8 @@ struct MlpWorkspace {
     void* hdesc_dev = nullptr;
     int hdesc_cap = 0;
     float* v0 = nullptr;  // [feat_cap][9]: sorted initial centers and a usability flag
+    unsigned* counts = nullptr;  // [counts_cap][256] grey-level counters, kept zero between calls
+    int counts_cap = 0;
     std::unordered_set<const void*> known_device;  // slice x pointers already checked
 };
 
@@ -206,27 +208,44 @@ struct HistDesc {
     int pad;
 };
 
-// Features of one slice per block: 256-bin histogram of round(clip(x)) in
-// shared memory, normalised by n, then onehot(C). Non-finite pixels count in
-// no bin.
-__global__ void k_features(const HistDesc* __restrict__ d, int ns, float* __restrict__ F) {
+// Histogram features in two steps. k_hist_counts: block (s, c) counts the
+// grey levels round(clip(x)) of chunk c (FEAT_CHUNK pixels) of slice s in
+// shared memory and adds them to the slice's 256 counters; non-finite pixels
+// count in no bin. k_features: one block per slice turns its counters into
+// the normalised histogram and onehot(C), and clears them for the next call.
+constexpr int FEAT_CHUNK = 32768;
+
+__global__ void k_hist_counts(const HistDesc* __restrict__ d, int ns, unsigned* __restrict__ counts) {
     __shared__ unsigned int h[D_HIST];
     const int s = blockIdx.x;
-    if (s >= ns) return;
+    const int64_t lo = (int64_t)blockIdx.y * FEAT_CHUNK;
+    if (s >= ns || lo >= d[s].n) return;
     for (int b = threadIdx.x; b < D_HIST; b += blockDim.x) h[b] = 0;
     __syncthreads();
     const float* x = d[s].x;
-    const int64_t n = d[s].n;
-    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+    const int64_t hi = min(d[s].n, lo + FEAT_CHUNK);
+    for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
         const float v = __ldg(x + i);
         if (!(v == v) || fabsf(v) == __int_as_float(0x7f800000)) continue;
         const int b = (int)fminf(fmaxf(rintf(v), 0.0f), 255.0f);
         atomicAdd(&h[b], 1u);
     }
     __syncthreads();
-    const float inv = 1.0f / (float)n;
+    for (int b = threadIdx.x; b < D_HIST; b += blockDim.x)
+        if (h[b]) atomicAdd(&counts[(int64_t)s * D_HIST + b], h[b]);
+}
+
+__global__ void k_features(const HistDesc* __restrict__ d, int ns, unsigned* __restrict__ counts,
+                           float* __restrict__ F) {
+    const int s = blockIdx.x;
+    if (s >= ns) return;
+    const float inv = 1.0f / (float)d[s].n;
     float* f = F + (int64_t)s * D_IN;
-    for (int b = threadIdx.x; b < D_HIST; b += blockDim.x) f[b] = (float)h[b] * inv;
+    unsigned* c = counts + (int64_t)s * D_HIST;
+    for (int b = threadIdx.x; b < D_HIST; b += blockDim.x) {
+        f[b] = (float)c[b] * inv;
+        c[b] = 0u;
+    }
     if (threadIdx.x < D_ONE) f[D_HIST + threadIdx.x] = (threadIdx.x == d[s].C - 1) ? 1.0f : 0.0f;
 }
 
@@ -381,7 +400,7 @@ void fcm_release_mlp(fcm_ctx* h) {
     if (!h || !h->mlp) return;
     MlpWorkspace* w = h->mlp;
     void* ps[] = {w->master, w->wbf, w->adam_m, w->adam_v, w->grad, w->xb, w->tb, w->z1, w->a1, w->z2,
-                  w->a2, w->y, w->dy, w->dz2, w->dz1, w->loss, w->cb, w->idx, w->feats, w->hdesc_dev, w->v0};
+                  w->a2, w->y, w->dy, w->dz2, w->dz1, w->loss, w->cb, w->idx, w->feats, w->hdesc_dev, w->v0, w->counts};
     for (void* p : ps) cudaFree(p);
     delete w;
     h->mlp = nullptr;
@@ -412,7 +431,21 @@ int fcm_features_impl(fcm_ctx* h, const fcm_slice* slices, int n, float* feats) 
         w->hdesc_cap = n;
     }
     CK(cudaMemcpyAsync(w->hdesc_dev, d.data(), sizeof(HistDesc) * n, cudaMemcpyHostToDevice, h->stream));
-    k_features<<<n, 512, 0, h->stream>>>((const HistDesc*)w->hdesc_dev, n, feats);
+    if (w->counts_cap < n) {
+        cudaFree(w->counts);
+        w->counts = nullptr;
+        w->counts_cap = 0;
+        CK(cudaMalloc(&w->counts, sizeof(unsigned) * D_HIST * n));
+        CK(cudaMemsetAsync(w->counts, 0, sizeof(unsigned) * D_HIST * n, h->stream));
+        w->counts_cap = n;
+    }
+    int64_t chunks = 1;
+    for (int i = 0; i < n; ++i) chunks = std::max<int64_t>(chunks, (d[i].n + FEAT_CHUNK - 1) / FEAT_CHUNK);
+    if (chunks > 65535) return ctx_invalid(h, "slice too large for the feature kernel");
+    k_hist_counts<<<dim3((unsigned)n, (unsigned)chunks), 512, 0, h->stream>>>((const HistDesc*)w->hdesc_dev, n,
+                                                                              w->counts);
+    CK(cudaGetLastError());
+    k_features<<<n, 256, 0, h->stream>>>((const HistDesc*)w->hdesc_dev, n, w->counts, feats);
     CK(cudaGetLastError());
     return FCM_OK;
 }
