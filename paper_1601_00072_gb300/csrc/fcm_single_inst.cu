@@ -305,9 +305,10 @@ template <int PASS, int C>
 struct TmaShape {
     static constexpr int ROWS = (PASS == P_INITV) ? 1 : 1 + C;    // x, then U^{k-1} rows
     static constexpr int STAGE_FLOATS = ROWS * WTILE;              // one warp's stage
-    // three blocks per SM (C <= 4) or two: about 72 or 108 KB of ring per block
-    static constexpr int BLOCKS_PER_SM = C <= 4 ? 3 : 2;
-    static constexpr int RAW = ((BLOCKS_PER_SM == 3 ? 72 : 108) * 1024) / (NWARP * STAGE_FLOATS * 4);
+    // two blocks per SM with about 108 KB of ring each: deeper per-warp rings
+    // stream HBM better here than a third block with shallower ones
+    static constexpr int BLOCKS_PER_SM = 2;
+    static constexpr int RAW = (108 * 1024) / (NWARP * STAGE_FLOATS * 4);
     static constexpr int STAGES = RAW < 2 ? 2 : (RAW > 8 ? 8 : RAW);
     static constexpr int SMEM_BYTES = NWARP * STAGES * STAGE_FLOATS * 4;
 };
@@ -393,7 +394,7 @@ __device__ __forceinline__ void tile_work(const float* sb, int cnt, int64_t i0, 
 // lane processes 4 pixels, and after __syncwarp lane 0 refills the stage with
 // the warp's tile k + STAGES. Warps never wait for one another.
 template <int C, int MK, int PASS>
-__global__ void __launch_bounds__(NT, (C <= 4 ? 3 : 2)) k_fcm_pass_tma(RunState* __restrict__ st, double* __restrict__ partials,
+__global__ void __launch_bounds__(NT, 2) k_fcm_pass_tma(RunState* __restrict__ st, double* __restrict__ partials,
                                                          cudaGraphConditionalHandle cond, int use_cond) {
     using Sh = TmaShape<PASS, C>;
     extern __shared__ __align__(128) float ring_all[];
@@ -504,7 +505,7 @@ constexpr uint32_t GRID_WAIT_LIMIT = 1u << 23;
 // V^{k+1} and the same stop decision. Pass 0 is INIT (V^1 from U^0, or U^0
 // from V^0); pass p >= 1 is iteration p of Algorithm 1.
 template <int C, int MK, int INIT>
-__global__ void __launch_bounds__(NT, (C <= 4 ? 3 : 2)) k_fcm_run_tma(RunState* __restrict__ st,
+__global__ void __launch_bounds__(NT, 2) k_fcm_run_tma(RunState* __restrict__ st,
                                                                       double* __restrict__ partials_raw) {
     using Sh = TmaShape<P_ITER, C>;
     constexpr int S = 2 * C + 4;
