@@ -66,6 +66,47 @@ def kernel_hash() -> str:
     return h.hexdigest()[:16]
 
 
+def source_hash(files) -> str:
+    h = hashlib.sha256()
+    for rel in files:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_instructions(path, sources):
+    """Warp instructions per launch from a committed ncu summary, if it was
+    taken on the current kernel sources; else None."""
+    try:
+        text = open(os.path.join(ROOT, path)).read()
+    except OSError:
+        return None
+    mh = re.search(r"kernel source hash:\s*`?([0-9a-f]{16})", text)
+    mt = re.search(r"warp instructions per launch:\s*([0-9]+)", text)
+    line = next((ln for ln in text.splitlines() if ln.startswith("One launch")), "")
+    mi = re.search(r"([0-9]+) iterations", line)
+    if not mh or not mt or mh.group(1) != source_hash(sources):
+        return None
+    return float(mt.group(1)), (int(mi.group(1)) if mi else None)
+
+
+def issue_roofline(path, sources, ms, iters, sm_mhz):
+    """ALU-issue roofline of a kernel: warp instructions per launch (from its
+    committed ncu summary, for the same iteration count) over the live time,
+    against SMs x 4 schedulers x the SM clock."""
+    import torch
+    got = profiled_instructions(path, sources)
+    if got is None or got[1] != iters:
+        return None
+    inst, _ = got
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    peak = sms * 4 * (sm_mhz or 2070.0) * 1e6 / 1e9
+    achieved = inst / (ms / 1e3) / 1e9
+    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "G warp-instr/s", "frac": achieved / peak,
+            "instructions_per_launch": inst, "source": path,
+            "peak_source": f"{sms} SMs x 4 schedulers x {sm_mhz or 2070.0:.0f} MHz"}
+
+
 def measured_peak():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -477,7 +518,13 @@ def bench_ours(args):
                      "dram_bytes_per_run_algorithmic": rbytes,
                      "center_rel_err_vs_stored_U_run": float(np.max(np.abs(Vr.cpu().numpy() - Vd.cpu().numpy())
                                                                    / np.maximum(np.abs(Vd.cpu().numpy()), 1.0))),
-                     "speedup_vs_pixel_path": (ms / args.steps) / rms}
+                     "speedup_vs_pixel_path": (ms / args.steps) / rms,
+                     "roofline": issue_roofline("profiles/fcm_recompute_volume256.md",
+                                                ["paper_1601_00072_gb300/csrc/fcm_recompute_inst.cu",
+                                                 "paper_1601_00072_gb300/csrc/fcm_device.cuh",
+                                                 "paper_1601_00072_gb300/csrc/fcm_tma.cuh",
+                                                 "paper_1601_00072_gb300/csrc/fcm_internal.h"],
+                                                rms, rr.iters, clocks.get("sm_max_mhz"))}
 
     # multi-feature FCM on a 3-channel 2048^2 phantom (shared layout, per-channel
     # contrasts and noise), inputs resident
@@ -501,7 +548,12 @@ def bench_ours(args):
         torch.cuda.synchronize(dev)
         mms = e0.elapsed_time(e1) / ms_
         multi = {"workload": "3-channel 2048x2048 phantom, C=4, m=2, eps=1e-5", "channels": 3, "n_pixels": nm,
-                 "ms_per_run": mms, "iters": rm.iters, "pixel_iter_per_s": nm * rm.iters / (mms / 1e3)}
+                 "ms_per_run": mms, "iters": rm.iters, "pixel_iter_per_s": nm * rm.iters / (mms / 1e3),
+                 "roofline": issue_roofline("profiles/fcm_multi_3ch_2048.md",
+                                            ["paper_1601_00072_gb300/csrc/fcm_multi_inst.cu",
+                                             "paper_1601_00072_gb300/csrc/fcm_device.cuh",
+                                             "paper_1601_00072_gb300/csrc/fcm_multi.h"],
+                                            mms, rm.iters, clocks.get("sm_max_mhz"))}
 
     # the paper's quantitative score (Dice per tissue class, Sec. 5.2) of the
     # timed run's segmentation against the phantom's generator labels
