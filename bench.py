@@ -231,6 +231,11 @@ def allreduce(value: float, op: str, world: int) -> float:
     return float(t.item())
 
 
+def workload_name(m: float) -> str:
+    return ("256^3 uint8 ellipsoid phantom (bias +/-20 percent, Rician sigma 6) as f32, "
+            f"C=4, m={m:g}, eps=1e-5, max_iter=300, Dirichlet U0 seed 103")
+
+
 def load_workload(m: float, with_labels: bool = False):
     import phantom
     x, lab, u0, c = phantom.single_image(WORKLOAD)
@@ -577,8 +582,7 @@ def bench_ours(args):
         "vs_baseline": None,
         "dtype": "f32",
         "data": "synthetic",
-        "config": {"workload": "256^3 uint8 ellipsoid phantom (bias +/-20 percent, Rician sigma 6) "
-                               f"as f32, C=4, m={m:g}, eps=1e-5, max_iter=300, Dirichlet U0 seed 103",
+        "config": {"workload": workload_name(m),
                    "n_pixels": n, "iters_per_step": statistics.median(iters),
                    "parallelism": f"replicas x{world}",
                    "l2": "working set 603 MB > 129 MB L2; no flush"},
@@ -654,7 +658,8 @@ def bench_reference(args):
            "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "impl": "reference",
-           "config": {"workload": f"256^3 uint8 ellipsoid phantom as f64 (sampled), C=4, m={args.m:g}"},
+           "config": {"workload": workload_name(args.m), "n_pixels": 256 ** 3,
+                      "sample": "each step: 262,144 voxels (slices z=120..123) x 10 iterations of the FP64 oracle"},
            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
