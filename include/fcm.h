@@ -261,7 +261,10 @@ typedef struct {
     double ms;      /* measured batch time when the autotuner chose it, or 0          */
     int schedule;   /* FCM_SCHED_SLICES or FCM_SCHED_ROUNDS                           */
     int tile;       /* FCM_SCHED_ROUNDS: fewest pixels one CTA takes in a round,      */
-                    /* 1024 to 65536, a multiple of 1024; FCM_SCHED_SLICES: 0         */
+                    /* 1024 to 65536, a multiple of 1024. FCM_SCHED_SLICES: 0 for one */
+                    /* launch, or an iteration cap: slices not stopped after `tile`  */
+                    /* iterations are parked and finished by a second launch that    */
+                    /* gives big slices clusters of 8 (in the same graph)            */
 } fcm_batch_plan;
 
 /* Batch options (bit flags). */
@@ -279,7 +282,11 @@ typedef struct {
  *                     decreasing size; slices with n >= plan.big are shared by
  *                     the CTAs of a thread-block cluster (per-iteration sums
  *                     exchanged through distributed shared memory), smaller
- *                     ones run one per CTA.
+ *                     ones run one per CTA. With plan.tile > 0 the batch runs
+ *                     in two phases: slices still running after plan.tile
+ *                     iterations are parked and resumed by a second launch
+ *                     with bigger clusters, so the few slowly converging
+ *                     slices do not hold a few SMs while the rest idle.
  *   FCM_SCHED_ROUNDS  a cooperative launch; round k is iteration k of every
  *                     slice still running, the pixels of those slices cut
  *                     into one equal contiguous chunk per CTA (at least

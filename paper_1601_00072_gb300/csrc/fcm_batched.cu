@@ -81,7 +81,7 @@ bool plan_valid(const fcm_batch_plan& p) {
     if (p.block != 256 && p.block != 512) return false;
     if (p.schedule == FCM_SCHED_ROUNDS) return p.tile >= 1024 && p.tile <= 65536 && p.tile % 1024 == 0;
     if (p.schedule != FCM_SCHED_SLICES) return false;
-    return (p.cluster == 1 || p.cluster == 2 || p.cluster == 4 || p.cluster == 8) && p.big >= 1;
+    return (p.cluster == 1 || p.cluster == 2 || p.cluster == 4 || p.cluster == 8) && p.big >= 1 && p.tile >= 0;
 }
 
 void free_graphs(BatchedWorkspace* w) {
@@ -259,12 +259,15 @@ int upload_batch(fcm_ctx* h, cudaStream_t s, const fcm_batch_plan& p, int n) {
     return 0;
 }
 
-int launch_kernel(fcm_ctx* h, cudaStream_t s, const fcm_batch_plan& p, int n_slices) {
-    if (p.schedule == FCM_SCHED_ROUNDS) return launch_rounds(h, s, p, n_slices);
+// One launch of the slice-queue kernel over the whole order: phase 0 runs
+// every slice (parking those not stopped after `cap` iterations), phase 1
+// finishes the parked ones.
+int launch_slices(fcm_ctx* h, cudaStream_t s, int block, int cluster, int64_t big, int n_slices, int phase,
+                  int cap) {
     BatchedWorkspace* w = h->batched;
-    const BatchKernel k = kernel_for(p.block);
-    const int ctas = grid_ctas(h, p.block, p.cluster);
-    if (ctas < p.cluster) {
+    const BatchKernel k = kernel_for(block);
+    const int ctas = grid_ctas(h, block, cluster);
+    if (ctas < cluster) {
         h->last_error = "batched launch shape does not fit on this device";
         return FCM_ERR_CUDA;
     }
@@ -272,11 +275,11 @@ int launch_kernel(fcm_ctx* h, cudaStream_t s, const fcm_batch_plan& p, int n_sli
     std::memset(&cfg, 0, sizeof(cfg));
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = p.cluster;
+    attr[0].val.clusterDim.x = cluster;
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
     cfg.gridDim = dim3(ctas);
-    cfg.blockDim = dim3(p.block);
+    cfg.blockDim = dim3(block);
     cfg.dynamicSmemBytes = k.smem;
     cfg.stream = s;
     cfg.attrs = attr;
@@ -286,9 +289,19 @@ int launch_kernel(fcm_ctx* h, cudaStream_t s, const fcm_batch_plan& p, int n_sli
     const int* o = w->d_order;
     SliceResult* r = w->d_res;
     BatchCtl* c = w->d_ctl;
-    int64_t big = p.big;
-    CK(cudaLaunchKernelEx(&cfg, k.fn, d, o, n_slices, r, c, big));
+    CK(cudaLaunchKernelEx(&cfg, k.fn, d, o, n_slices, r, c, big, phase, cap));
     return 0;
+}
+
+int launch_kernel(fcm_ctx* h, cudaStream_t s, const fcm_batch_plan& p, int n_slices) {
+    if (p.schedule == FCM_SCHED_ROUNDS) return launch_rounds(h, s, p, n_slices);
+    if (p.tile <= 0) return launch_slices(h, s, p.block, p.cluster, p.big, n_slices, 0, 0x7fffffff);
+    // two phases: the slices that have not stopped after p.tile iterations
+    // are finished by a second launch that gives big slices clusters of 8
+    int rc = launch_slices(h, s, p.block, p.cluster, p.big, n_slices, 0, p.tile);
+    if (rc) return rc;
+    if (grid_ctas(h, 512, 8) >= 8) return launch_slices(h, s, 512, 8, 32768, n_slices, 1, 0x7fffffff);
+    return launch_slices(h, s, 256, 4, 16384, n_slices, 1, 0x7fffffff);
 }
 
 // ---- autotune cache ------------------------------------------------------
@@ -562,7 +575,26 @@ int fcm_run_batched(fcm_handle h, fcm_slice* slices, int n_slices, int options) 
             }
             fcm_batch_plan best = default_plan();
             best.ms = 1e30;
+            fcm_batch_plan best_slices = default_plan();
+            best_slices.ms = 1e30;
             for (const fcm_batch_plan& p : cands) {
+                double ms = 0;
+                if ((rc = time_plan(h, slices, p, n_slices, 2, &ms))) return rc;
+                if (ms < best.ms) {
+                    best = p;
+                    best.ms = ms;
+                }
+                if (p.schedule == FCM_SCHED_SLICES && ms < best_slices.ms) {
+                    best_slices = p;
+                    best_slices.ms = ms;
+                }
+            }
+            // then the best slice-queue shape split in two phases at a few caps
+            const int caps[3] = {24, 40, 64};
+            for (int cap : caps) {
+                fcm_batch_plan p = best_slices;
+                p.tile = cap;
+                p.ms = 0.0;
                 double ms = 0;
                 if ((rc = time_plan(h, slices, p, n_slices, 2, &ms))) return rc;
                 if (ms < best.ms) {
@@ -617,8 +649,8 @@ int fcm_batched_set_plan(fcm_handle h, const fcm_batch_plan* plan) {
     }
     if (!plan_valid(*plan))
         return ctx_invalid(h,
-                           "plan: block 256|512; slices schedule: cluster 1|2|4|8, big >= 1; "
-                           "rounds schedule: tile 1024..65536, a multiple of 1024");
+                           "plan: block 256|512; slices schedule: cluster 1|2|4|8, big >= 1, tile (first-phase "
+                           "iteration cap) >= 0; rounds schedule: tile 1024..65536, a multiple of 1024");
     h->batched->forced = true;
     h->batched->forced_plan = *plan;
     return FCM_OK;

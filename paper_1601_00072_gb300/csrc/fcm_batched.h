@@ -24,6 +24,10 @@ struct alignas(16) SliceDesc {
     float V0[FCM_MAX_CLUSTERS];  // initial centers (FCM_INIT_V), copied before the run
 };
 
+// Status of a slice parked by the first phase of a two-phase batch (never
+// returned to the caller: the second phase finishes every parked slice).
+constexpr int SLICE_PARKED = 3;
+
 struct alignas(16) SliceResult {
     int iters;
     int status;
@@ -32,6 +36,9 @@ struct alignas(16) SliceResult {
     double delta;
     double J;
     double V64[FCM_MAX_CLUSTERS];
+    // state of a parked slice: V^k and V^{k-1} for iteration k = iters + 1
+    float vcur[FCM_MAX_CLUSTERS];
+    float vprev[FCM_MAX_CLUSTERS];
 };
 
 struct alignas(128) BatchCtl {
@@ -46,7 +53,10 @@ struct BatchPlan {
     int64_t big;    // slices with n >= big are shared by a whole cluster
 };
 
-typedef void (*BatchFn)(const SliceDesc*, const int*, int, SliceResult*, BatchCtl*, int64_t);
+// phase 0: every slice from its start, parked before iteration cap + 1 when it
+// has not stopped by then; phase 1: only the parked slices, resumed from their
+// saved state.
+typedef void (*BatchFn)(const SliceDesc*, const int*, int, SliceResult*, BatchCtl*, int64_t, int, int);
 
 // Kernel of each block size, and its dynamic shared memory (x staging).
 struct BatchKernel {

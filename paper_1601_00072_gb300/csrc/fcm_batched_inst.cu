@@ -178,13 +178,16 @@ struct XSrc {
 
 template <int C, int MK>
 __device__ __noinline__ void process_slice(const SliceDesc& d, SliceResult& res, unsigned r, unsigned K, float* xs,
-                                           BatchShared& sh) {
+                                           BatchShared& sh, bool resume, int cap) {
     const int64_t n = d.n;
     int64_t share = (n + K - 1) / K;
     share += share & 1;  // even, so only the last pixel of the slice can be unpaired
     const int64_t lo = min(n, (int64_t)r * share), hi = min(n, lo + share);
     const int cnt = (int)(hi - lo);
-    if (threadIdx.x < C) sh.vcur[threadIdx.x] = sh.vprev[threadIdx.x] = d.V0[threadIdx.x];
+    if (threadIdx.x < C) {
+        sh.vcur[threadIdx.x] = resume ? res.vcur[threadIdx.x] : d.V0[threadIdx.x];
+        sh.vprev[threadIdx.x] = resume ? res.vprev[threadIdx.x] : d.V0[threadIdx.x];
+    }
     XSrc xl{d.x + lo, reinterpret_cast<const uint8_t*>(xs), false};
     if (cnt <= XCAP) {
         for (int i = threadIdx.x; i < cnt; i += NTB) xs[i] = __ldg(d.x + lo + i);
@@ -211,10 +214,22 @@ __device__ __noinline__ void process_slice(const SliceDesc& d, SliceResult& res,
 
     f2 v2[C], vp2[C];
 #pragma unroll
-    for (int j = 0; j < C; ++j) v2[j] = vp2[j] = pack2(d.V0[j], d.V0[j]);
-    int parity = 0, flags = 0;
+    for (int j = 0; j < C; ++j) {
+        v2[j] = pack2(v[j], v[j]);
+        vp2[j] = pack2(vp[j], vp[j]);
+    }
+    int parity = 0, flags = resume ? res.flags : 0;
     SliceAcc<C> a;
-
+    int status = FCM_NOT_CONVERGED, iters = 0;
+    double delta = 0.0, Jk = 0.0;
+    double v64[C];
+    bool ok0 = true;
+    if (resume) {
+        // a parked slice: V^k and V^{k-1} as saved, iteration k = iters + 1 next
+#pragma unroll
+        for (int j = 0; j < C; ++j) v64[j] = res.V64[j];
+        iters = res.iters;
+    } else {
     // ---- pass 0: V^1 from U^0 (Eq. 3), or U^0 = membership(V^0) (Eq. 4) ----
     a.reset();
     if (!from_u) {
@@ -277,16 +292,16 @@ __device__ __noinline__ void process_slice(const SliceDesc& d, SliceResult& res,
         }
     }
     slice_reduce<C>(sh, a, K, parity);
-
-    int status = FCM_NOT_CONVERGED, iters = 0;
-    double delta = 0.0, Jk = 0.0;
-    double v64[C];
 #pragma unroll
     for (int j = 0; j < C; ++j) v64[j] = d.V0[j];
-    if (sh.tot[2 * C + 2] != 0.0) {
+    ok0 = sh.tot[2 * C + 2] == 0.0;
+    }
+    bool parked = false;
+    if (!ok0) {
         status = FCM_ERR_BAD_INPUT;
     } else {
         float vn[C];
+        if (!resume) {
 #pragma unroll
         for (int j = 0; j < C; ++j) {
             if (sh.tot[C + j] > 0.0) {
@@ -302,8 +317,14 @@ __device__ __noinline__ void process_slice(const SliceDesc& d, SliceResult& res,
         __syncthreads();
         if (threadIdx.x < C) sh.vcur[threadIdx.x] = vn[threadIdx.x];
         __syncthreads();
+        }
         // ---- iterations: U^k from V^k, U^{k-1} recomputed from V^{k-1} ----
-        for (int k = 1;; ++k) {
+        for (int k = iters + 1;; ++k) {
+            if (k > cap) {
+                // first phase of a two-phase batch: park before iteration k
+                parked = true;
+                break;
+            }
             a.reset();
             const bool prev_given = from_u && k == 1;
             for (int p0 = threadIdx.x; p0 < npair; p0 += NTB * CHUNK) {
@@ -390,9 +411,9 @@ __device__ __noinline__ void process_slice(const SliceDesc& d, SliceResult& res,
             }
             __syncthreads();
         }
-        // ---- U^k, written once ----
+        // ---- U^k, written once (a parked slice writes it in the second phase) ----
         float* U = d.U;
-        for (int p = threadIdx.x; p < npair; p += NTB) {
+        for (int p = threadIdx.x; p < (parked ? 0 : npair); p += NTB) {
             const float2 xv = xl.pair(p);
             f2 u2[C], um2[C];
             membership_pair<C, MK>(pack2(xv.x, xv.y), v2, m, inv_m1, v, u2, um2);
@@ -405,7 +426,7 @@ __device__ __noinline__ void process_slice(const SliceDesc& d, SliceResult& res,
                 __stcs(row + 1, b0);
             }
         }
-        if (odd_tail) {
+        if (odd_tail && !parked) {
             float u[C], um[C];
             membership<C, MK>(xl.at(cnt - 1), v, m, inv_m1, u, um);
 #pragma unroll
@@ -414,14 +435,19 @@ __device__ __noinline__ void process_slice(const SliceDesc& d, SliceResult& res,
     }
     if (r == 0 && threadIdx.x == 0) {
         res.iters = iters;
-        res.status = status;
+        res.status = parked ? SLICE_PARKED : status;
         res.flags = flags;
         res.delta = delta;
         res.J = Jk;
 #pragma unroll
         for (int j = 0; j < C; ++j) {
             res.V64[j] = v64[j];
-            d.V[j] = v[j];
+            if (parked) {
+                res.vcur[j] = v[j];
+                res.vprev[j] = vp[j];
+            } else {
+                d.V[j] = v[j];
+            }
         }
     }
     // no rank leaves the slice (and reuses its shared memory) while another
@@ -431,14 +457,14 @@ __device__ __noinline__ void process_slice(const SliceDesc& d, SliceResult& res,
 }
 
 __device__ __forceinline__ void run_slice(const SliceDesc& d, SliceResult& res, unsigned r, unsigned K, float* xs,
-                                          BatchShared& sh) {
+                                          BatchShared& sh, bool resume, int cap) {
 #define FCM_BATCH_CASE(CC)                                                                  \
     case CC:                                                                                \
         switch (d.mk) {                                                                     \
-            case M_TWO: process_slice<CC, M_TWO>(d, res, r, K, xs, sh); break;              \
-            case M_THREE: process_slice<CC, M_THREE>(d, res, r, K, xs, sh); break;          \
-            case M_ONE_HALF: process_slice<CC, M_ONE_HALF>(d, res, r, K, xs, sh); break;    \
-            default: process_slice<CC, M_GENERIC>(d, res, r, K, xs, sh); break;             \
+            case M_TWO: process_slice<CC, M_TWO>(d, res, r, K, xs, sh, resume, cap); break;              \
+            case M_THREE: process_slice<CC, M_THREE>(d, res, r, K, xs, sh, resume, cap); break;          \
+            case M_ONE_HALF: process_slice<CC, M_ONE_HALF>(d, res, r, K, xs, sh, resume, cap); break;    \
+            default: process_slice<CC, M_GENERIC>(d, res, r, K, xs, sh, resume, cap); break;             \
         }                                                                                   \
         break;
     switch (d.C) {
@@ -457,10 +483,15 @@ __device__ __forceinline__ void run_slice(const SliceDesc& d, SliceResult& res, 
 
 __global__ void __launch_bounds__(NTB, MIN_BLOCKS)
     k_fcm_batched(const SliceDesc* __restrict__ descs, const int* __restrict__ order, int n_slices,
-                  SliceResult* __restrict__ results, BatchCtl* __restrict__ ctl, int64_t big) {
+                  SliceResult* __restrict__ results, BatchCtl* __restrict__ ctl, int64_t big, int phase,
+                  int cap) {
     extern __shared__ __align__(16) float xs[];
     __shared__ BatchShared sh;
     const unsigned K = cluster_size(), r = cluster_rank();
+    const bool resume = phase == 1;
+    // the second phase takes only the slices the first one parked (their
+    // status was written by the earlier launch; no one else writes it now)
+    auto wanted = [&](int s) { return !resume || __ldcg(&results[s].status) == SLICE_PARKED; };
     bool solo = K == 1;
     int first_solo = -1;
     // ---- the cluster shares the big slices ----
@@ -471,15 +502,16 @@ __global__ void __launch_bounds__(NTB, MIN_BLOCKS)
         cluster_sync();  // every rank has read the index before rank 0 takes another
         if (idx >= n_slices) return;
         const int s = order[idx];
+        if (!wanted(s)) continue;
         if (descs[s].n >= big) {
-            run_slice(descs[s], results[s], r, K, xs, sh);
+            run_slice(descs[s], results[s], r, K, xs, sh, resume, cap);
             continue;
         }
         // the queue has reached the small slices: every CTA works alone now
         solo = true;
         if (r == 0) first_solo = s;
     }
-    if (first_solo >= 0) run_slice(descs[first_solo], results[first_solo], 0, 1, xs, sh);
+    if (first_solo >= 0) run_slice(descs[first_solo], results[first_solo], 0, 1, xs, sh, resume, cap);
     for (;;) {
         if (threadIdx.x == 0) sh.idx = (int)atomicAdd(&ctl->next, 1u);
         __syncthreads();
@@ -487,7 +519,8 @@ __global__ void __launch_bounds__(NTB, MIN_BLOCKS)
         __syncthreads();
         if (idx >= n_slices) return;
         const int s = order[idx];
-        run_slice(descs[s], results[s], 0, 1, xs, sh);
+        if (!wanted(s)) continue;
+        run_slice(descs[s], results[s], 0, 1, xs, sh, resume, cap);
     }
 }
 

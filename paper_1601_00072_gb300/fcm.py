@@ -468,12 +468,13 @@ class FCM:
     def set_batched_plan(self, block=None, cluster=1, big=1 << 62, schedule="slices", tile=0):
         """Force a launch shape for later batched runs; no arguments returns
         to the autotuner. ``schedule="rounds"`` takes ``block`` and ``tile``;
-        ``"slices"`` takes ``block``, ``cluster`` and ``big``."""
+        ``"slices"`` takes ``block``, ``cluster``, ``big`` and ``tile`` (0, or
+        the first-phase iteration cap of a two-phase batch)."""
         if block is None:
             _lib.check(self._lib.fcm_batched_set_plan(self._h, None), self._h)
             return
         rounds = schedule == "rounds"
         p = _lib.fcm_batch_plan(int(block), 1 if rounds else int(cluster), 0 if rounds else int(big), 0.0,
                                 _lib.FCM_SCHED_ROUNDS if rounds else _lib.FCM_SCHED_SLICES,
-                                int(tile) if rounds else 0)
+                                int(tile))
         _lib.check(self._lib.fcm_batched_set_plan(self._h, ctypes.byref(p)), self._h)
