@@ -563,11 +563,11 @@ int fcm_run_batched(fcm_handle h, fcm_slice* slices, int n_slices, int options) 
             std::vector<fcm_batch_plan> cands;
             const int blocks[2] = {256, 512};
             const int clusters[4] = {1, 2, 4, 8};
-            const int64_t bigs[4] = {16384, 49152, 98304, 196608};
+            const int64_t bigs[6] = {4096, 8192, 16384, 49152, 98304, 196608};
             const int tiles[3] = {2048, 8192, 32768};
             for (int b : blocks) {
                 for (int k : clusters)
-                    for (int gi = 0; gi < (k == 1 ? 1 : 4); ++gi)
+                    for (int gi = 0; gi < (k == 1 ? 1 : 6); ++gi)
                         if (grid_ctas(h, b, k) >= k)
                             cands.push_back({b, k, k == 1 ? ((int64_t)1 << 62) : bigs[gi], 0.0, FCM_SCHED_SLICES, 0});
                 if (n_slices <= ROUND_MAX_SLICES && round_ctas(h, b, round_smem(n_slices)) > 0)

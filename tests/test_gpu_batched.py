@@ -101,7 +101,8 @@ def assert_batch(slices, host, m=2.0):
 SLICE_PLANS = [dict(block=512, cluster=1, big=1 << 40), dict(block=256, cluster=1, big=1 << 40),
                dict(block=512, cluster=4, big=4096), dict(block=256, cluster=2, big=4096),
                dict(block=512, cluster=8, big=16384), dict(block=256, cluster=4, big=65536),
-               dict(block=256, cluster=4, big=16384, tile=8), dict(block=512, cluster=2, big=4096, tile=3)]
+               dict(block=256, cluster=4, big=16384, tile=8), dict(block=512, cluster=2, big=4096, tile=3),
+               dict(block=256, cluster=4, big=4096)]
 ROUND_PLANS = [dict(schedule="rounds", block=512, tile=2048), dict(schedule="rounds", block=256, tile=4096),
                dict(schedule="rounds", block=512, tile=16384), dict(schedule="rounds", block=256, tile=65536)]
 PLANS = [None] + SLICE_PLANS + ROUND_PLANS
@@ -257,7 +258,8 @@ def test_autotuner_caches_its_plan(tmp_path, monkeypatch):
 
 
 @pytest.mark.parametrize("plan", [None, dict(schedule="rounds", block=512, tile=4096),
-                                  dict(block=256, cluster=4, big=16384, tile=40)], ids=plan_id)
+                                  dict(block=256, cluster=4, big=16384, tile=40),
+                                  dict(block=256, cluster=4, big=4096)], ids=plan_id)
 def test_full_512_slice_batch_matches_oracle(fcm, plan):
     """The whole 512-slice workload (sides 64..512, C in {3, 4, 5}), with the
     autotuned plan and with the round schedule."""
