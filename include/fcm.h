@@ -142,6 +142,39 @@ int fcm_run(fcm_handle h, const float* x, int64_t n, int C, float m,
             float* V, int options, fcm_report* rep);
 
 /*
+ * fcm_run_stream — fcm_run over a sequence of images of one shape (n pixels,
+ * C clusters, the same m, eps and max_iter), each read from and written back
+ * to host memory, with the host-device copies overlapped with the runs:
+ * while image i runs on the handle's stream, the upload of image i+1 and the
+ * download of image i-1 proceed on two copy streams of the handle, through
+ * three device staging sets it owns (3 x (4 + 4C) x n bytes). Each image is one run of Algorithm 1
+ * (Sec. 2.1) from its own U^0, computed by the same whole-run kernel as
+ * fcm_run with FCM_INIT_U, so each result equals that call's on the image.
+ *
+ *   n_images  >= 1.
+ *   x         n_images pointers to n floats each. Host memory (pinned memory
+ *             lets the copies overlap the runs; pageable memory works but the
+ *             driver stages it) or device memory.
+ *   U0        nullable array of n_images pointers to C*n floats, cluster-
+ *             major, read only. A NULL array, or a NULL entry, reads image
+ *             i's U^0 from U[i].
+ *   U         n_images pointers to C*n floats. Out: each image's U^k.
+ *   V         n_images*C floats, host memory. Out: row i = image i's V^k.
+ *   options   0 or FCM_OPT_RECOMPUTE.
+ *   reps      nullable; n_images reports.
+ *
+ * Needs n % 4 == 0 and a device with cooperative launch; returns
+ * FCM_ERR_INVALID_ARG otherwise. Returns after every image is done and every
+ * copy has landed: FCM_OK when all converged, FCM_NOT_CONVERGED when some
+ * image hit max_iter, else the first image's error status (reps[i].status
+ * holds each image's own; the other images' results are valid). A CUDA
+ * error ends the call with FCM_ERR_CUDA after the handle's streams drain.
+ */
+int fcm_run_stream(fcm_handle h, int n_images, const float* const* x, int64_t n, int C, float m,
+                   float eps, int max_iter, const float* const* U0, float* const* U, float* V,
+                   int options, fcm_report* reps);
+
+/*
  * fcm_run_hist — Algorithm 1 (Sec. 2.1) for images whose intensities are
  * integer grey levels 0..255, run on the 256-bin histogram (the grey-level
  * reduction of brFCM, cited in Sec. 3). Under Eq. 4 a pixel's memberships

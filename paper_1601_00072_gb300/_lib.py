@@ -77,6 +77,8 @@ SIGNATURES = [
     ("fcm_destroy", None, [_vp]),
     ("fcm_run", _i, [_vp, _vp, _i64, _i, _f, _f, _i, _i, _vp, _vp, _vp, _i,
                      ctypes.POINTER(fcm_report)]),
+    ("fcm_run_stream", _i, [_vp, _i, ctypes.POINTER(_vp), _i64, _i, _f, _f, _i, ctypes.POINTER(_vp),
+                            ctypes.POINTER(_vp), _vp, _i, ctypes.POINTER(fcm_report)]),
     ("fcm_run_hist", _i, [_vp, _vp, _i64, _i, _f, _f, _i, _i, _vp, _vp, _vp, ctypes.POINTER(fcm_report)]),
     ("fcm_dsc", _i, [_vp, _vp, _i64, _i, _vp, ctypes.POINTER(_i), _i, ctypes.POINTER(_i64), ctypes.POINTER(ctypes.c_double)]),
     ("fcm_run_multi", _i, [_vp, _vp, _i64, _i, _i, _f, _f, _i, _i, _vp, _vp, _vp,

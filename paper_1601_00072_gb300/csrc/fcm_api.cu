@@ -300,6 +300,17 @@ void fcm_destroy(fcm_handle h) {
         if (h->d_trace) cudaFree(h->d_trace);
         if (h->d_stage_x) cudaFree(h->d_stage_x);
         if (h->d_stage_U) cudaFree(h->d_stage_U);
+        if (h->pipe_in) cudaStreamSynchronize(h->pipe_in);
+        if (h->pipe_out) cudaStreamSynchronize(h->pipe_out);
+        for (int b = 0; b < fcm_ctx::PIPE_SETS; ++b) {
+            if (h->d_pipe_x[b]) cudaFree(h->d_pipe_x[b]);
+            if (h->d_pipe_U[b]) cudaFree(h->d_pipe_U[b]);
+        }
+        if (h->h_pipe_st) cudaFreeHost(h->h_pipe_st);
+        for (cudaEvent_t ev : h->pipe_ev)
+            if (ev) cudaEventDestroy(ev);
+        if (h->pipe_in) cudaStreamDestroy(h->pipe_in);
+        if (h->pipe_out) cudaStreamDestroy(h->pipe_out);
         fcm_release_batched(h);
         fcm_release_mlp(h);
         fcm_release_hist(h);
@@ -463,6 +474,143 @@ int fcm_run(fcm_handle h, const float* x, int64_t n, int C, float m, float eps, 
         return FCM_ERR_CUDA;
     }
     return hs->status;
+}
+
+int fcm_run_stream(fcm_handle h, int n_images, const float* const* x, int64_t n, int C, float m, float eps,
+                   int max_iter, const float* const* U0, float* const* U, float* V, int options,
+                   fcm_report* reps) {
+    if (!h) return FCM_ERR_INVALID_ARG;
+    if (n_images < 1 || !x || !U || !V) return ctx_invalid(h, "n_images >= 1 and non-null x, U and V");
+    for (int i = 0; i < n_images; ++i)
+        if (!x[i] || !U[i]) return ctx_invalid(h, "null x[i] or U[i]");
+    if (n < 1) return ctx_invalid(h, "n must be >= 1");
+    if (C < 1 || C > FCM_MAX_CLUSTERS) return ctx_invalid(h, "C must be in [1, 8]");
+    if (!(m > 1.0f) || !std::isfinite(m)) return ctx_invalid(h, "m must be a finite number > 1");
+    if (!(eps >= 0.0f) || !std::isfinite(eps)) return ctx_invalid(h, "eps must be finite and >= 0");
+    if (max_iter < 1) return ctx_invalid(h, "max_iter must be >= 1");
+    if (n > (int64_t)1 << 40) return ctx_invalid(h, "n too large");
+    if (n % 4 != 0) return ctx_invalid(h, "fcm_run_stream needs n % 4 == 0");
+    if (options & ~FCM_OPT_RECOMPUTE) return ctx_invalid(h, "fcm_run_stream takes no option but FCM_OPT_RECOMPUTE");
+
+    DeviceGuard g(h->device);
+    int rc = ensure_single_workspace(h);
+    if (rc) return rc;
+    if (!h->coop) return ctx_invalid(h, "fcm_run_stream needs cooperative launch");
+    const size_t xb = sizeof(float) * (size_t)n, Ub = sizeof(float) * (size_t)n * C;
+    constexpr int NS = fcm_ctx::PIPE_SETS;
+    for (int b = 0; b < NS; ++b) {
+        if ((rc = ctx_grow(h, (void**)&h->d_pipe_x[b], &h->pipe_x_cap[b], xb, "stream staging x"))) return rc;
+        if ((rc = ctx_grow(h, (void**)&h->d_pipe_U[b], &h->pipe_U_cap[b], Ub, "stream staging U"))) return rc;
+    }
+    if (h->pipe_st_cap < n_images) {
+        if (h->h_pipe_st) cudaFreeHost(h->h_pipe_st);
+        h->h_pipe_st = nullptr;
+        h->pipe_st_cap = 0;
+        CK(cudaMallocHost(&h->h_pipe_st, sizeof(RunState) * (size_t)n_images));
+        h->pipe_st_cap = n_images;
+    }
+    if (!h->pipe_in) {
+        CK(cudaStreamCreateWithFlags(&h->pipe_in, cudaStreamNonBlocking));
+        CK(cudaStreamCreateWithFlags(&h->pipe_out, cudaStreamNonBlocking));
+        for (cudaEvent_t& ev : h->pipe_ev) CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    }
+    cudaEvent_t* in_done = h->pipe_ev;
+    cudaEvent_t* run_done = h->pipe_ev + NS;
+    cudaEvent_t* out_done = h->pipe_ev + 2 * NS;
+    cudaEvent_t ev_start = h->pipe_ev[3 * NS], ev_end = h->pipe_ev[3 * NS + 1];
+
+    const int mk = mkind_of(m);
+    const bool recompute = (options & FCM_OPT_RECOMPUTE) != 0;
+    const void* krun = recompute ? (const void*)g_rc.run[C][mk][0] : (const void*)g_table.run[C][mk][0];
+    const int run_smem = recompute ? g_rc.smem[C][0] : g_table.run_smem[C];
+    const int bps = blocks_per_sm(h, krun, run_smem);
+    const int64_t want = (n + (int64_t)WARP_TILE * NWARP - 1) / ((int64_t)WARP_TILE * NWARP);
+    const int run_blocks = (int)std::min<int64_t>(want, (int64_t)h->num_sms * bps);
+    if (run_blocks < 1) return ctx_invalid(h, "the whole-run kernel does not fit on this device");
+
+    // the copy streams start behind the work already queued on the handle's stream
+    CK(cudaEventRecord(ev_start, h->stream));
+    CK(cudaStreamWaitEvent(h->pipe_in, ev_start, 0));
+    CK(cudaStreamWaitEvent(h->pipe_out, ev_start, 0));
+    cudaError_t e = cudaSuccess;
+    const char* what = "queueing the image sequence";
+    for (int i = 0; i < n_images && e == cudaSuccess; ++i) {
+        const int b = i % NS;
+        float* dx = h->d_pipe_x[b];
+        float* dU = h->d_pipe_U[b];
+        RunState* hs = h->h_pipe_st + i;
+        std::memset(hs, 0, sizeof(RunState));
+        hs->x = dx;
+        hs->Uprev = dU;  // U^0 is staged into the U set and updated in place
+        hs->U = dU;
+        hs->n = n;
+        hs->m = m;
+        hs->inv_m1 = (float)(1.0 / ((double)m - 1.0));
+        hs->eps = eps;
+        hs->max_iter = max_iter;
+        hs->C = C;
+        hs->status = STATUS_RUNNING;
+        const float* u0 = (U0 && U0[i]) ? U0[i] : U[i];
+        // upload, once the download of image i - NS has drained this set
+        if (i >= NS) e = cudaStreamWaitEvent(h->pipe_in, out_done[b], 0);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(dx, x[i], xb, cudaMemcpyDefault, h->pipe_in);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(dU, u0, Ub, cudaMemcpyDefault, h->pipe_in);
+        if (e == cudaSuccess) e = cudaEventRecord(in_done[b], h->pipe_in);
+        // the run, with its state uploaded before and read back after
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(h->stream, in_done[b], 0);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(h->d_st, hs, sizeof(RunState), cudaMemcpyHostToDevice, h->stream);
+        void* args[2] = {&h->d_st, &h->d_partials};
+        if (e == cudaSuccess)
+            e = cudaLaunchCooperativeKernel(krun, dim3(run_blocks), dim3(NT), args, run_smem, h->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(hs, h->d_st, sizeof(RunState), cudaMemcpyDeviceToHost, h->stream);
+        if (e == cudaSuccess) e = cudaEventRecord(run_done[b], h->stream);
+        // download
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(h->pipe_out, run_done[b], 0);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(U[i], dU, Ub, cudaMemcpyDefault, h->pipe_out);
+        if (e == cudaSuccess) e = cudaEventRecord(out_done[b], h->pipe_out);
+    }
+    // later work on the handle's stream follows the last download
+    if (e == cudaSuccess) e = cudaEventRecord(ev_end, h->pipe_out);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(h->stream, ev_end, 0);
+    // drain all three streams, also after an error, so no copy into a caller's
+    // buffer is still pending when the call returns
+    const cudaError_t s_in = cudaStreamSynchronize(h->pipe_in);
+    const cudaError_t s_run = cudaStreamSynchronize(h->stream);
+    const cudaError_t s_out = cudaStreamSynchronize(h->pipe_out);
+    if (e == cudaSuccess) {
+        e = s_in != cudaSuccess ? s_in : s_run != cudaSuccess ? s_run : s_out;
+        what = "running the image sequence";
+    }
+    if (e != cudaSuccess) return ctx_fail(h, e, what);
+
+    h->last_blocks = run_blocks;
+    h->last_path = 2;
+    h->last_C = C;
+    h->last_trace_iters = 0;
+    int worst = FCM_OK;
+    for (int i = 0; i < n_images; ++i) {
+        RunState* hs = h->h_pipe_st + i;
+        if (hs->status == STATUS_RUNNING) {
+            hs->status = FCM_ERR_CUDA;
+            h->last_error = "a run of the sequence ended without a status";
+        }
+        for (int j = 0; j < C; ++j) V[(size_t)i * C + j] = hs->V[j];
+        if (reps) {
+            fcm_report* rep = reps + i;
+            std::memset(rep, 0, sizeof(*rep));
+            rep->iters = hs->iters;
+            rep->status = hs->status;
+            rep->flags = hs->flags;
+            rep->C = C;
+            rep->delta = hs->delta;
+            rep->J = hs->J;
+            for (int j = 0; j < C; ++j) rep->V64[j] = hs->V64[j];
+            rep->launches = 1;
+        }
+        if (hs->status < 0 && worst >= 0) worst = hs->status;
+        if (hs->status == FCM_NOT_CONVERGED && worst == FCM_OK) worst = FCM_NOT_CONVERGED;
+    }
+    return worst;
 }
 
 int fcm_time_pass(fcm_handle h, const float* x, int64_t n, int C, float m, float* U, const float* V,

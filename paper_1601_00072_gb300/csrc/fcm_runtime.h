@@ -60,6 +60,20 @@ struct fcm_ctx {
     std::map<fcm::GraphKey, fcm::GraphEntry> graphs;
     std::map<const void*, int> occupancy;   // blocks per SM of each kernel (smem attribute set)
 
+    // pipelined image sequences (fcm_run_stream): PIPE_SETS staging sets, a
+    // pinned run state per image, an upload and a download stream, and per
+    // set the events upload done, run done and download done, then start/end
+    static constexpr int PIPE_SETS = 3;
+    float* d_pipe_x[PIPE_SETS] = {};
+    float* d_pipe_U[PIPE_SETS] = {};
+    size_t pipe_x_cap[PIPE_SETS] = {};
+    size_t pipe_U_cap[PIPE_SETS] = {};
+    fcm::RunState* h_pipe_st = nullptr;
+    int pipe_st_cap = 0;
+    cudaStream_t pipe_in = nullptr;
+    cudaStream_t pipe_out = nullptr;
+    cudaEvent_t pipe_ev[3 * PIPE_SETS + 2] = {};
+
     // other paths
     fcm::BatchedWorkspace* batched = nullptr;
     fcm::MlpWorkspace* mlp = nullptr;

@@ -213,6 +213,58 @@ class FCM:
         return FCMResult(U=U, V=V, iters=rep.iters, status=st, delta=rep.delta, J=rep.J,
                          V64=np.array(rep.V64[:C]), flags=rep.flags, launches=rep.launches, trace=tr)
 
+    def run_stream(self, xs, C: int, m: float = 2.0, eps: float = 1e-5, max_iter: int = 300, *,
+                   U0s=None, Us=None, V=None, recompute: bool = False,
+                   raise_on_error: bool = True) -> list[FCMResult]:
+        """Algorithm 1 on a sequence of same-sized images in host memory
+        (``fcm_run_stream``): the upload of the next image and the download
+        of the previous one overlap the current run.
+
+        ``xs``: list of n float32 pixels each (pinned CPU tensors copy
+        fastest; numpy arrays work). ``U0s``: list of [C, n] initial
+        memberships (read only), or None with each ``Us[i]`` holding U^0.
+        ``Us`` (allocated like ``xs[0]`` when None) receives each U^k; ``V``
+        ([len(xs), C], allocated when None) receives each V^k.
+        """
+        import torch
+        k = len(xs)
+        if k < 1:
+            raise ValueError("give at least one image")
+        n = _numel(xs[0])
+        if any(_numel(x) != n for x in xs):
+            raise ValueError("every image must hold the same number of pixels")
+
+        def alloc(shape, like):
+            if isinstance(like, torch.Tensor):
+                t = torch.empty(shape, dtype=torch.float32)
+                return t.pin_memory() if like.is_pinned() else t
+            return np.empty(shape, dtype=np.float32)
+
+        if U0s is None and Us is None:
+            raise ValueError("give U0s, or Us holding U^0")
+        if U0s is not None and (len(U0s) != k or any(_numel(u) != C * n for u in U0s)):
+            raise ValueError("U0s must hold one [C, n] array per image")
+        if Us is None:
+            Us = [alloc((C, n), xs[0]) for _ in range(k)]
+        if len(Us) != k or any(_numel(u) != C * n for u in Us):
+            raise ValueError("Us must hold one [C, n] array per image")
+        if V is None:
+            V = np.empty((k, C), dtype=np.float32)
+        if _numel(V) != k * C or (isinstance(V, torch.Tensor) and V.is_cuda):
+            raise ValueError("V must be a host array of len(xs) x C floats")
+        ptrs = lambda arrs: (_lib._vp * k)(*[_ptr(a) for a in arrs])
+        xp, up = ptrs(xs), ptrs(Us)
+        u0p = ptrs(U0s) if U0s is not None else None
+        reps = (_lib.fcm_report * k)()
+        self._bind_stream()
+        st = self._lib.fcm_run_stream(self._h, k, xp, n, int(C), float(m), float(eps), int(max_iter),
+                                      u0p, up, _ptr(V), _lib.FCM_OPT_RECOMPUTE if recompute else 0, reps)
+        if raise_on_error:
+            _lib.check(st, self._h)
+        return [FCMResult(U=Us[i], V=V[i], iters=reps[i].iters, status=reps[i].status, delta=reps[i].delta,
+                          J=reps[i].J, V64=np.array(reps[i].V64[:C]), flags=reps[i].flags,
+                          launches=reps[i].launches) for i in range(k)]
+
     def run_hist(self, x, C: int, m: float = 2.0, eps: float = 1e-5, max_iter: int = 300, *,
                  U0=None, V0=None, U=None, V=None, raise_on_error: bool = True) -> FCMResult:
         """Algorithm 1 on the 256-bin histogram (``fcm_run_hist``) for x that
