@@ -138,22 +138,31 @@ __device__ __forceinline__ void slice_reduce(BatchShared& sh, SliceAcc<C>& a, un
         // sums in rank order
         for (int t = threadIdx.x; t < (int)K * S; t += NTB) sh.xch[t / S][t % S] = ld_dsmem_f64(&sh.red[parity][t % S], t / S);
         __syncthreads();
+        // thread s sums value s in rank order; thread j < C also sums den_j
+        // the same way (equal to total C + j) and forms v_j = num_j / den_j
         if (threadIdx.x < S) {
             const int s = threadIdx.x;
             double t = sh.xch[0][s];
             for (unsigned q = 1; q < K; ++q) t = (s < NS) ? t + sh.xch[q][s] : fmax(t, sh.xch[q][s]);
             sh.tot[s] = t;
+            if (s < C) {
+                double den = sh.xch[0][C + s];
+                for (unsigned q = 1; q < K; ++q) den += sh.xch[q][C + s];
+                sh.vq[s] = den > 0.0 ? t / den : 0.0;
+            }
         }
     } else {
         __syncthreads();
-        if (threadIdx.x < S) sh.tot[threadIdx.x] = sh.red[parity][threadIdx.x];
+        if (threadIdx.x < S) {
+            const int s = threadIdx.x;
+            sh.tot[s] = sh.red[parity][s];
+            if (s < C) {
+                const double den = sh.red[parity][C + s];
+                sh.vq[s] = den > 0.0 ? sh.red[parity][s] / den : 0.0;
+            }
+        }
     }
     parity ^= 1;
-    __syncthreads();
-    if (threadIdx.x < C) {
-        const double den = sh.tot[C + threadIdx.x];
-        sh.vq[threadIdx.x] = den > 0.0 ? sh.tot[threadIdx.x] / den : 0.0;
-    }
     __syncthreads();
 }
 
