@@ -16,7 +16,10 @@ Sources of truth:
 * special cases: C = 1 gives the mean; point masses are fixed points;
 * metamorphic relations: translating, scaling or reflecting x moves V the
   same way and leaves U unchanged; permuting pixels permutes U;
-* monotone descent of J along the iteration (alternating minimisation).
+* monotone descent of J along the iteration (alternating minimisation);
+* a naive nested-loop Algorithm 1 on tiny inputs, with Eq. 4 in its
+  ratio-of-distances form and real powers;
+* the fixed-point property of a run stopped at a tight tolerance.
 """
 from __future__ import annotations
 
@@ -294,6 +297,80 @@ def pin_multi_feature(L):
     return fails
 
 
+def _naive_fcm(x, C, m, eps, max_iter, U0):
+    """Algorithm 1 written as literal nested loops over tiny inputs, for
+    pixels that sit on no center: Eq. 4 in the ratio-of-distances form with a
+    real power (u_ij = 1 / sum_l (|x_i - v_j| / |x_i - v_l|)^(2/(m-1))), Eq. 3
+    with u^m, Eq. 1 for J and the L-inf stopping test."""
+    n = len(x)
+    p = 2.0 / (m - 1.0)
+
+    def centers(U):
+        V = []
+        for j in range(C):
+            num = den = 0.0
+            for i in range(n):
+                w = U[j][i] ** m
+                num += w * x[i]
+                den += w
+            V.append(num / den)
+        return V
+
+    Uprev = [[float(U0[j][i]) for i in range(n)] for j in range(C)]
+    V = centers(Uprev)
+    for k in range(1, max_iter + 1):
+        U = [[0.0] * n for _ in range(C)]
+        for i in range(n):
+            for j in range(C):
+                s = 0.0
+                for l in range(C):
+                    s += (abs(x[i] - V[j]) / abs(x[i] - V[l])) ** p
+                U[j][i] = 1.0 / s
+        delta = max(abs(U[j][i] - Uprev[j][i]) for j in range(C) for i in range(n))
+        J = sum(U[j][i] ** m * (x[i] - V[j]) ** 2 for j in range(C) for i in range(n))
+        if delta < eps or k == max_iter:  # V^k is the set that produced U^k
+            return np.array(U), np.array(V), k, J
+        V = centers(U)
+        Uprev = U
+
+
+def pin_brute_force(L):
+    """The oracle agrees with the naive loop to 1e-12 on tiny random inputs
+    (n <= 64, several C and m)."""
+    fails = []
+    g = np.random.default_rng(11)
+    for n, C, m in [(7, 2, 2.0), (33, 3, 1.5), (64, 4, 2.7), (48, 3, 3.0), (64, 2, 2.0)]:
+        x = g.uniform(0.0, 100.0, n)
+        u0 = g.dirichlet(np.ones(C), n).T.copy()
+        U, V, k, J = _naive_fcm(x, C, m, 1e-6, 40, u0)
+        r = oracle.fcm(x, C, m, 1e-6, 40, U0=u0, L=L)
+        _check(fails, r["iters"] == k, f"brute force n={n} C={C} m={m}: iters {r['iters']} vs {k}")
+        if r["iters"] == k:
+            _check(fails, np.max(np.abs(r["U"] - U)) < 1e-12, f"brute force n={n} C={C} m={m}: U")
+            _check(fails, np.max(np.abs(r["V"] - V) / np.maximum(np.abs(V), 1.0)) < 1e-12,
+                   f"brute force n={n} C={C} m={m}: V")
+            _check(fails, abs(r["J"][-1] - J) <= 1e-12 * abs(J), f"brute force n={n} C={C} m={m}: J")
+    return fails
+
+
+def pin_converged_fixed_point(L):
+    """A run stopped at a tight tolerance is a fixed point: one more center
+    update (Eq. 3 from the returned U) moves no center by more than 1e-6."""
+    fails = []
+    img, _ = phantom.phantom2d(17, 40, 40, 8.0)
+    x = img.reshape(-1).astype(np.float64)
+    for C, m in [(4, 2.0), (3, 1.5)]:
+        u0 = phantom.dirichlet_u0((17, C), C, x.size).astype(np.float64)
+        r = oracle.fcm(x, C, m, 1e-10, 5000, U0=u0, L=L)
+        _check(fails, r["status"] == 0, f"fixed point C={C} m={m}: not converged")
+        W = r["U"] ** m
+        Vn = (W @ x) / W.sum(1)
+        _check(fails, np.max(np.abs(Vn - r["V"])) < 1e-6,
+               f"fixed point C={C} m={m}: center moved {np.max(np.abs(Vn - r['V']))}")
+    return fails
+
+
 ALL_PINS = [pin_toy_rationals, pin_singular_points, pin_closed_form_objective,
             pin_optimality, pin_special_cases, pin_descent_and_invariants,
-            pin_metamorphic, pin_quantized_matches_plain, pin_dsc, pin_multi_feature]
+            pin_metamorphic, pin_quantized_matches_plain, pin_dsc, pin_multi_feature,
+            pin_brute_force, pin_converged_fixed_point]
