@@ -52,7 +52,7 @@ using namespace fcm;
 namespace {
 
 constexpr int HNT = 256;
-constexpr int HCHUNK = 8;
+constexpr int HCHUNK = 4;  // pixels per thread whose loads are issued together in the first pass
 
 __device__ __forceinline__ bool grey_level(float v) {
     return v >= 0.0f && v <= 255.0f && v == rintf(v);  // false for NaN
@@ -60,8 +60,10 @@ __device__ __forceinline__ bool grey_level(float v) {
 
 // Pass over the pixels: histogram, input checks, and (from U^0) the
 // numerators and denominators of V^1 (Eq. 3) as per-block FP64 slots.
+// Up to C = 4, four blocks per SM fit in 64 registers without spills: twice
+// the warps of an unbounded build to cover the loads' latency.
 template <int C, int MK, bool FROM_U>
-__global__ void __launch_bounds__(HNT) k_hist_pass0(const float* __restrict__ x, const float* __restrict__ U0,
+__global__ void __launch_bounds__(HNT, C <= 4 ? 4 : 2) k_hist_pass0(const float* __restrict__ x, const float* __restrict__ U0,
                                                    int64_t n, float m, HistState* st, double* __restrict__ part) {
     __shared__ unsigned hs[HNT / 32][256];  // one sub-histogram per warp
     __shared__ float w[HNT / 32][4 * C];
@@ -75,7 +77,7 @@ __global__ void __launch_bounds__(HNT) k_hist_pass0(const float* __restrict__ x,
     const int lane_id = threadIdx.x & 31;
     unsigned* hw = hs[threadIdx.x >> 5];
     // the loop bounds are the same for all lanes of a warp (its first lane's
-    // index), so every lane reaches the warp-wide match below
+    // index); lanes past n load nothing and count nothing
     for (int64_t i0 = (int64_t)blockIdx.x * HNT + threadIdx.x; i0 - lane_id < n; i0 += stride * HCHUNK) {
         // the chunk's loads are all issued before any is used
         float xc[HCHUNK], uc[HCHUNK][FROM_U ? C : 1];
@@ -100,10 +102,9 @@ __global__ void __launch_bounds__(HNT) k_hist_pass0(const float* __restrict__ x,
             const float xi = xc[q];
             const bool good = in && grey_level(xi);
             bad |= in && !good;
-            // lanes that hold the same grey level add once, through their leader
-            const int key = good ? (int)xi : -1;
-            const unsigned same = __match_any_sync(0xffffffffu, key);
-            if (good && lane_id == __ffs(same) - 1) atomicAdd(&hw[key], (unsigned)__popc(same));
+            // shared-memory atomics: lanes of a warp on the same grey level are
+            // serialised by the hardware; counts are exact in any order
+            if (good) atomicAdd(&hw[(int)xi], 1u);
             if (FROM_U && good) {
 #pragma unroll
                 for (int j = 0; j < C; ++j) {
