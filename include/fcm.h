@@ -28,7 +28,9 @@
  *     else V^{k+1} = centers(U^k). V^1 comes from the initial U^0, or from
  *     U^0 = membership(V^0) when initial centers are given.
  *   - Arithmetic: memberships and per-thread sums in FP32; the sums across
- *     thread blocks (center numerators/denominators and J) in FP64.
+ *     threads and blocks (center numerators/denominators and J) in
+ *     compensated FP32 (double-float, about 44 bits) or FP64, in a fixed
+ *     order, so a run is deterministic.
  *   - Ownership: the caller owns x, U, V and every output array; the library
  *     never frees them. A handle owns its device workspace, CUDA graphs and
  *     autotuning cache, and frees them in fcm_destroy.
@@ -81,8 +83,9 @@ extern "C" {
 
 typedef struct fcm_ctx* fcm_handle;
 
-/* Result of one run. V64 holds the final centers as the FP64 quotients of the
- * combined sums (V holds the same values rounded to float). */
+/* Result of one run. V64 holds the final centers as the quotients of the
+ * combined sums, to about 44 bits or better, in FP64 (V holds the same values
+ * rounded to float). */
 typedef struct {
     int iters;      /* k of the returned (U^k, V^k)                         */
     int status;     /* FCM_OK, FCM_NOT_CONVERGED or a negative FCM_ERR_*     */

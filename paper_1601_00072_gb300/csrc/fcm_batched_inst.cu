@@ -20,9 +20,11 @@
 // is read in the first two passes; U^k is written once, after the last
 // iteration. All per-pixel arithmetic is the single-image pass's (Eq. 4 in
 // packed FP32x2 pairs); sums run in FP32 over chunks of a few pixels, then in
-// compensated FP32 per thread and warp, and in FP64 across warps and CTAs.
+// compensated FP32 per thread, warp, CTA and cluster (no FP64 instruction in
+// the iteration loop).
 #include "fcm_batched.h"
 #include "fcm_device.cuh"
+#include "fcm_df.cuh"
 
 #ifndef FCM_BATCH_NT
 #error "compile with -DFCM_BATCH_NT=<threads per CTA>"
@@ -60,9 +62,10 @@ __device__ __forceinline__ uint32_t dsmem_addr(const void* local, unsigned rank)
     asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
     return r;
 }
-__device__ __forceinline__ double ld_dsmem_f64(const double* local, unsigned rank) {
-    double v;
-    asm volatile("ld.shared::cluster.f64 %0, [%1];" : "=d"(v) : "r"(dsmem_addr(local, rank)) : "memory");
+__device__ __forceinline__ float2 ld_dsmem_f2(const float2* local, unsigned rank) {
+    float2 v;
+    asm volatile("ld.shared::cluster.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(dsmem_addr(local, rank))
+                 : "memory");
     return v;
 }
 __device__ __forceinline__ int ld_dsmem_s32(const int* local, unsigned rank) {
@@ -73,10 +76,12 @@ __device__ __forceinline__ int ld_dsmem_s32(const int* local, unsigned rank) {
 
 struct BatchShared {
     float w[NWB][2 * SBMAX];  // warp totals: (hi, lo) of each sum, then the maxima
-    double red[2][SBMAX];     // block totals, double-buffered for the cluster exchange
-    double xch[8][SBMAX];     // every rank's block totals, gathered for the rank-order sum
-    double tot[SBMAX];        // slice totals (the same on every rank)
-    double vq[FCM_MAX_CLUSTERS];  // next centers, FP64 quotients
+    // block totals (sums as hi/lo double-floats, maxima in x), double-buffered
+    // for the cluster exchange, and every rank's, gathered for the rank-order sum
+    float2 red[2][SBMAX];
+    float2 xch[8][SBMAX];
+    DF tot[SBMAX];            // slice totals (the same on every rank); maxima in .hi
+    DF vq[FCM_MAX_CLUSTERS];  // next centers, double-float quotients
     float vcur[FCM_MAX_CLUSTERS], vprev[FCM_MAX_CLUSTERS];  // centers, for the scalar path
     int idx;
 };
@@ -101,8 +106,10 @@ struct SliceAcc {
 };
 
 // Totals of one pass over the slice: double-float warp sums, the CTA's warps
-// in FP64, then (K > 1) the K CTAs in rank order through distributed shared
-// memory. Leaves sh.tot and the FP64 quotients sh.vq = num / den.
+// merged in warp order, then (K > 1) the K CTAs in rank order through
+// distributed shared memory, all in compensated FP32 (no FP64 instruction:
+// a few threads would run a long FP64 chain while the rest wait at the
+// barrier). Leaves sh.tot and the double-float quotients sh.vq = num / den.
 template <int C>
 __device__ __forceinline__ void slice_reduce(BatchShared& sh, SliceAcc<C>& a, unsigned K, int& parity) {
     constexpr int S = 2 * C + 3;
@@ -124,42 +131,40 @@ __device__ __forceinline__ void slice_reduce(BatchShared& sh, SliceAcc<C>& a, un
     __syncthreads();
     if (threadIdx.x < S) {
         const int s = threadIdx.x;
-        double t = 0.0;
+        float2 t;
         if (s < NS) {
-            for (int w = 0; w < NWB; ++w) t += (double)sh.w[w][2 * s] + (double)sh.w[w][2 * s + 1];
+            DF d{sh.w[0][2 * s], sh.w[0][2 * s + 1]};
+            for (int w = 1; w < NWB; ++w) d = df_merge(d, DF{sh.w[w][2 * s], sh.w[w][2 * s + 1]});
+            t = make_float2(d.hi, d.lo);
         } else {
-            for (int w = 0; w < NWB; ++w) t = fmax(t, (double)sh.w[w][2 * NS + (s - NS)]);
+            float mx = sh.w[0][2 * NS + (s - NS)];
+            for (int w = 1; w < NWB; ++w) mx = fmaxf(mx, sh.w[w][2 * NS + (s - NS)]);
+            t = make_float2(mx, 0.0f);
         }
         sh.red[parity][s] = t;
     }
     if (K > 1) {
         cluster_sync();
-        // all remote reads at once (one thread per rank and value), then the
-        // sums in rank order
-        for (int t = threadIdx.x; t < (int)K * S; t += NTB) sh.xch[t / S][t % S] = ld_dsmem_f64(&sh.red[parity][t % S], t / S);
-        __syncthreads();
-        // thread s sums value s in rank order; thread j < C also sums den_j
-        // the same way (equal to total C + j) and forms v_j = num_j / den_j
-        if (threadIdx.x < S) {
-            const int s = threadIdx.x;
-            double t = sh.xch[0][s];
-            for (unsigned q = 1; q < K; ++q) t = (s < NS) ? t + sh.xch[q][s] : fmax(t, sh.xch[q][s]);
-            sh.tot[s] = t;
-            if (s < C) {
-                double den = sh.xch[0][C + s];
-                for (unsigned q = 1; q < K; ++q) den += sh.xch[q][C + s];
-                sh.vq[s] = den > 0.0 ? t / den : 0.0;
-            }
-        }
-    } else {
-        __syncthreads();
-        if (threadIdx.x < S) {
-            const int s = threadIdx.x;
-            sh.tot[s] = sh.red[parity][s];
-            if (s < C) {
-                const double den = sh.red[parity][C + s];
-                sh.vq[s] = den > 0.0 ? sh.red[parity][s] / den : 0.0;
-            }
+        // all remote reads at once (one thread per rank and value)
+        for (int t = threadIdx.x; t < (int)K * S; t += NTB) sh.xch[t / S][t % S] = ld_dsmem_f2(&sh.red[parity][t % S], t / S);
+    }
+    __syncthreads();
+    // thread s combines value s in rank order; thread j < C also combines
+    // den_j the same way (equal to total C + j) and forms v_j = num_j / den_j
+    const int par = parity;
+    auto at = [&](unsigned q, int s) {
+        const float2 v = K > 1 ? sh.xch[q][s] : sh.red[par][s];
+        return DF{v.x, v.y};
+    };
+    if (threadIdx.x < S) {
+        const int s = threadIdx.x;
+        DF t = at(0, s);
+        for (unsigned q = 1; q < K; ++q) t = (s < NS) ? df_merge(t, at(q, s)) : DF{fmaxf(t.hi, at(q, s).hi), 0.0f};
+        sh.tot[s] = t;
+        if (s < C) {
+            DF den = at(0, C + s);
+            for (unsigned q = 1; q < K; ++q) den = df_merge(den, at(q, C + s));
+            sh.vq[s] = den.hi > 0.0f ? df_div(t, den) : DF{0.0f, 0.0f};
         }
     }
     parity ^= 1;
@@ -230,13 +235,19 @@ __device__ __noinline__ void process_slice(const SliceDesc& d, SliceResult& res,
     int parity = 0, flags = resume ? res.flags : 0;
     SliceAcc<C> a;
     int status = FCM_NOT_CONVERGED, iters = 0;
-    double delta = 0.0, Jk = 0.0;
-    double v64[C];
+    // delta, J and the centers behind V (double-floats) in FP32 arithmetic;
+    // FP64 only when the result is written
+    float delta = 0.0f;
+    DF Jk{0.0f, 0.0f};
+    DF v64[C];
     bool ok0 = true;
     if (resume) {
         // a parked slice: V^k and V^{k-1} as saved, iteration k = iters + 1 next
 #pragma unroll
-        for (int j = 0; j < C; ++j) v64[j] = res.V64[j];
+        for (int j = 0; j < C; ++j) {
+            const float hi = (float)res.V64[j];
+            v64[j] = DF{hi, (float)(res.V64[j] - (double)hi)};
+        }
         iters = res.iters;
     } else {
     // ---- pass 0: V^1 from U^0 (Eq. 3), or U^0 = membership(V^0) (Eq. 4) ----
@@ -302,8 +313,8 @@ __device__ __noinline__ void process_slice(const SliceDesc& d, SliceResult& res,
     }
     slice_reduce<C>(sh, a, K, parity);
 #pragma unroll
-    for (int j = 0; j < C; ++j) v64[j] = d.V0[j];
-    ok0 = sh.tot[2 * C + 2] == 0.0;
+    for (int j = 0; j < C; ++j) v64[j] = DF{d.V0[j], 0.0f};
+    ok0 = sh.tot[2 * C + 2].hi == 0.0f;
     }
     bool parked = false;
     if (!ok0) {
@@ -313,13 +324,13 @@ __device__ __noinline__ void process_slice(const SliceDesc& d, SliceResult& res,
         if (!resume) {
 #pragma unroll
         for (int j = 0; j < C; ++j) {
-            if (sh.tot[C + j] > 0.0) {
+            if (sh.tot[C + j].hi > 0.0f) {
                 v64[j] = sh.vq[j];
-                vn[j] = (float)sh.vq[j];
+                vn[j] = sh.vq[j].hi;
             } else {
                 flags |= FCM_FLAG_EMPTY_CLUSTER;  // V^0 kept, or 0 from a U^0
                 vn[j] = from_u ? 0.0f : d.V0[j];
-                v64[j] = vn[j];
+                v64[j] = DF{vn[j], 0.0f};
             }
             v2[j] = pack2(vn[j], vn[j]);
         }
@@ -390,7 +401,7 @@ __device__ __noinline__ void process_slice(const SliceDesc& d, SliceResult& res,
                 }
             }
             slice_reduce<C>(sh, a, K, parity);
-            delta = sh.tot[2 * C + 1];
+            delta = sh.tot[2 * C + 1].hi;
             Jk = sh.tot[2 * C];
             iters = k;
             if (delta < d.eps) {
@@ -405,9 +416,9 @@ __device__ __noinline__ void process_slice(const SliceDesc& d, SliceResult& res,
             for (int j = 0; j < C; ++j) {
                 vp2[j] = v2[j];
                 vn[j] = v[j];
-                if (sh.tot[C + j] > 0.0) {
+                if (sh.tot[C + j].hi > 0.0f) {
                     v64[j] = sh.vq[j];
-                    vn[j] = (float)sh.vq[j];
+                    vn[j] = sh.vq[j].hi;
                     v2[j] = pack2(vn[j], vn[j]);
                 } else {
                     flags |= FCM_FLAG_EMPTY_CLUSTER;  // keep v_j
@@ -446,11 +457,11 @@ __device__ __noinline__ void process_slice(const SliceDesc& d, SliceResult& res,
         res.iters = iters;
         res.status = parked ? SLICE_PARKED : status;
         res.flags = flags;
-        res.delta = delta;
-        res.J = Jk;
+        res.delta = (double)delta;
+        res.J = (double)Jk.hi + (double)Jk.lo;
 #pragma unroll
         for (int j = 0; j < C; ++j) {
-            res.V64[j] = v64[j];
+            res.V64[j] = (double)v64[j].hi + (double)v64[j].lo;
             if (parked) {
                 res.vcur[j] = v[j];
                 res.vprev[j] = vp[j];

@@ -22,6 +22,7 @@
 
 #include "fcm.h"
 #include "fcm_device.cuh"
+#include "fcm_df.cuh"
 #include "fcm_runtime.h"
 
 namespace fcm {
@@ -285,18 +286,6 @@ __global__ void __launch_bounds__(HNT) k_hist_delta1(const float* __restrict__ x
         for (int u = 0; u < HNT / 32; ++u) t = fmaxf(t, wm[u]);
         atomicMax(&st->d1bits, __float_as_uint(t));  // non-negative floats order as their bits
     }
-}
-
-// Quotient of two double-float values, as a double-float (one FP32 division
-// and a residual correction): accurate to about 2^-44 relative.
-__device__ __forceinline__ DF df_div(DF a, DF b) {
-    const float q0 = a.hi / b.hi;
-    const float p = q0 * b.hi;
-    const float e = fmaf(q0, b.hi, -p);  // q0 * b.hi = p + e exactly
-    const float r = ((a.hi - p) - e + a.lo) - q0 * b.lo;
-    const float q1 = r / b.hi;
-    const float s = q0 + q1;
-    return DF{s, q1 - (s - q0)};
 }
 
 // Algorithm 1 on the bins, one CTA, thread b = grey level b. Sums over the
