@@ -394,17 +394,21 @@ def bench_batched(h, dev, steps, warmup, plan=None):
     #   next batch of a stream;
     # - separate: a cold batch of only these slices, through the autotuned
     #   path, the cost of an immediate rerun.
-    if plan:
-        h.set_batched_plan()  # back to the autotuner for the subsets
     bad_i = np.flatnonzero(~ok)
     ms_marginal = ms_separate = 0.0
     if bad_i.size:
         good = Batch([Slice(x=xs[i], C=Cs[i], U0=u0s[i]) for i in np.flatnonzero(ok)])
         bad = Batch([Slice(x=xs[i], C=Cs[i], U0=u0s[i]) for i in bad_i])
+        # the marginal pair runs with the cold batch's own launch shape, so the
+        # difference is the failed slices' work, not two autotuner choices
+        h.set_batched_plan(**{k: plan_used[k] for k in ("schedule", "block", "cluster", "big", "tile")})
         ms_rest = timed(lambda: h.run_batched(good, read_back=False), steps)
         ms_full = timed(lambda: h.run_batched(cold, read_back=False), steps)
         ms_marginal = max(0.0, ms_full - ms_rest)
+        h.set_batched_plan()  # the separate rerun is a batch of its own: autotuned
         ms_separate = timed(lambda: h.run_batched(bad, read_back=False), steps)
+        if plan:
+            h.set_batched_plan(**plan)
     ms_charge = ms_marginal
     it_c = np.array([s.iters for s in cold.slices])
     it_w = np.array([s.iters for s in warm.slices])
