@@ -36,7 +36,9 @@
  *     autotuning cache, and frees them in fcm_destroy.
  *   - Streams: work is issued on the handle's stream. Entry points that fill
  *     host-side results (iters, reports, statuses) synchronise that stream
- *     before returning.
+ *     before returning. fcm_run_stream also uses an upload and a download
+ *     stream of the handle's own, ordered after the work already queued on
+ *     the handle's stream, and returns after all three have drained.
  *   - Errors: every entry point returns an int status (FCM_OK or
  *     FCM_NOT_CONVERGED on success, a negative FCM_ERR_* otherwise);
  *     fcm_status_string names it. A handle is not thread-safe.
