@@ -414,6 +414,14 @@ def bench_batched(h, dev, steps, warmup, plan=None):
     it_w = np.array([s.iters for s in warm.slices])
     cold_ips = n_img / (ms_cold / 1e3)
     warm_ips = n_img / ((ms_warm + ms_charge) / 1e3)
+    # the same cold batch on each slice's 256-bin histogram (one CTA per
+    # slice): the same iterates up to rounding, compared with the cold run
+    hist = Batch([Slice(x=x, C=c, U0=u) for x, c, u in zip(xs, Cs, u0s)])
+    ms_hist = timed(lambda: h.run_batched_hist(hist, read_back=False), steps)
+    hist.read_back()
+    it_h = np.array([s.iters for s in hist.slices])
+    verr = np.array([np.max(np.abs(np.asarray(a.V64) - np.asarray(c.V64)) / np.maximum(np.abs(np.asarray(c.V64)), 1.0))
+                     for a, c in zip(hist.slices, cold.slices)])
     return {
         "workload": "512 phantom slices, sides log-uniform 64..512, C in {3,4,5}, m=2, eps=1e-5, max_iter=300",
         "pixels": px, "steps": steps,
@@ -429,6 +437,12 @@ def bench_batched(h, dev, steps, warmup, plan=None):
         "warm_over_cold": warm_ips / cold_ips,
         "warm_over_cold_separate_rerun": (ms_cold / (ms_warm + ms_separate)),
         "plan": plan_used,
+        "histogram_domain": {
+            "kernel": "k_bhist: one CTA per slice, three pixel passes and the iterations on 256 bins",
+            "images_per_s": n_img / (ms_hist / 1e3), "ms": ms_hist, "speedup_vs_cold": ms_cold / ms_hist,
+            "mean_iters": float(it_h.mean()), "max_iters": int(it_h.max()),
+            "iters_within_1_of_cold": float(np.mean(np.abs(it_h - it_c) <= 1)),
+            "center_rel_err_vs_cold": {"max": float(verr.max()), "fraction_within_1e-5": float(np.mean(verr <= 1e-5))}},
     }
 
 

@@ -349,6 +349,24 @@ typedef struct {
  */
 int fcm_run_batched(fcm_handle h, fcm_slice* slices, int n_slices, int options);
 
+/*
+ * fcm_run_batched_hist — the histogram-domain run (as fcm_run_hist: the
+ * grey-level reduction of brFCM, cited in Sec. 3) for each slice of a batch
+ * of 8-bit slices, one CTA per slice, largest slices first, in one launch.
+ * Per slice: a pass over the pixels builds its 256-bin histogram (and from
+ * U^0 the sums of V^1), a second pass takes the first stopping quantity
+ * against the pixels' U^0, Algorithm 1 then iterates on the bins, and a last
+ * pass writes U^k by table lookup. The iterates equal fcm_run_batched's up to
+ * the order of rounding.
+ *
+ * Slices as for fcm_run_batched (device x, U0, U and V; x 16-byte aligned),
+ * with n < 2^31. A slice whose x holds anything but integer grey levels
+ * 0..255, or whose U^0 has a negative or non-finite value, or whose V^0 a
+ * non-finite one, gets FCM_ERR_BAD_INPUT and V = V^0 (0 from a U^0); its U
+ * is not written. Returns as fcm_run_batched.
+ */
+int fcm_run_batched_hist(fcm_handle h, fcm_slice* slices, int n_slices);
+
 /* The plan the last batched run used. */
 int fcm_batched_plan(fcm_handle h, fcm_batch_plan* plan);
 

@@ -84,6 +84,7 @@ SIGNATURES = [
     ("fcm_run_multi", _i, [_vp, _vp, _i64, _i, _i, _f, _f, _i, _i, _vp, _vp, _vp,
                            ctypes.POINTER(ctypes.c_double), ctypes.POINTER(fcm_report)]),
     ("fcm_run_batched", _i, [_vp, ctypes.POINTER(fcm_slice), _i, _i]),
+    ("fcm_run_batched_hist", _i, [_vp, ctypes.POINTER(fcm_slice), _i]),
     ("fcm_batched_plan", _i, [_vp, ctypes.POINTER(fcm_batch_plan)]),
     ("fcm_batched_set_plan", _i, [_vp, ctypes.POINTER(fcm_batch_plan)]),
     ("fcm_model_init", _i, [_vp, ctypes.c_uint64]),

@@ -485,26 +485,32 @@ int time_plan(fcm_ctx* h, const fcm_slice* slices, const fcm_batch_plan& p, int 
 
 }  // namespace
 
-extern "C" {
+namespace {
 
-int fcm_run_batched(fcm_handle h, fcm_slice* slices, int n_slices, int options) {
-    if (!h) return FCM_ERR_INVALID_ARG;
+// Argument checks shared by the batch entry points: sizes below n_limit,
+// x 16-byte aligned. in_place: some slice updates its U^0 in place.
+int check_slices(fcm_ctx* h, const fcm_slice* slices, int n_slices, int64_t n_limit, bool* in_place) {
     if (!slices || n_slices < 1) return ctx_invalid(h, "no slices");
-    bool in_place = false;
+    *in_place = false;
     for (int i = 0; i < n_slices; ++i) {
         const fcm_slice& s = slices[i];
-        const bool ok = s.n >= 1 && s.n < ((int64_t)1 << 40) && s.C >= 1 && s.C <= FCM_MAX_CLUSTERS &&
-                        s.m > 1.0f && std::isfinite(s.m) && s.eps >= 0.0f && std::isfinite(s.eps) &&
-                        s.max_iter >= 1 && (s.init_mode == FCM_INIT_U || s.init_mode == FCM_INIT_V) &&
-                        s.x && s.U && s.V && ((uintptr_t)s.x % 16 == 0);
+        const bool ok = s.n >= 1 && s.n < n_limit && s.C >= 1 && s.C <= FCM_MAX_CLUSTERS && s.m > 1.0f &&
+                        std::isfinite(s.m) && s.eps >= 0.0f && std::isfinite(s.eps) && s.max_iter >= 1 &&
+                        (s.init_mode == FCM_INIT_U || s.init_mode == FCM_INIT_V) && s.x && s.U && s.V &&
+                        ((uintptr_t)s.x % 16 == 0);
         if (!ok) {
             char buf[96];
             std::snprintf(buf, sizeof(buf), "slice %d: bad size, C, m, eps, max_iter, mode or pointer", i);
             return ctx_invalid(h, buf);
         }
-        if (s.init_mode == FCM_INIT_U && (!s.U0 || s.U0 == s.U)) in_place = true;
+        if (s.init_mode == FCM_INIT_U && (!s.U0 || s.U0 == s.U)) *in_place = true;
     }
-    DeviceGuard g(h->device);
+    return FCM_OK;
+}
+
+// The device descriptors of a batch in the pinned host array, and its LPT
+// work order (largest slices first).
+int fill_descs(fcm_ctx* h, const fcm_slice* slices, int n_slices) {
     int rc = ensure_batched(h, n_slices);
     if (rc) return rc;
     BatchedWorkspace* w = h->batched;
@@ -547,6 +553,41 @@ int fcm_run_batched(fcm_handle h, fcm_slice* slices, int n_slices, int options) 
     std::iota(w->h_order, w->h_order + n_slices, 0);
     std::stable_sort(w->h_order, w->h_order + n_slices,
                      [&](int a, int b) { return slices[a].n > slices[b].n; });
+    return FCM_OK;
+}
+
+// Each slice's results from the pinned result array; the aggregate status.
+int collect_results(fcm_ctx* h, fcm_slice* slices, int n_slices) {
+    BatchedWorkspace* w = h->batched;
+    int worst = FCM_OK;
+    for (int i = 0; i < n_slices; ++i) {
+        const SliceResult& r = w->h_res[i];
+        fcm_slice& s = slices[i];
+        s.iters = r.iters;
+        s.status = r.status;
+        s.flags = r.flags;
+        s.delta = r.delta;
+        s.J = r.J;
+        for (int j = 0; j < FCM_MAX_CLUSTERS; ++j) s.V64[j] = j < s.C ? r.V64[j] : 0.0;
+        if (r.status < 0 && worst >= 0) worst = r.status;
+        if (r.status == FCM_NOT_CONVERGED && worst == FCM_OK) worst = FCM_NOT_CONVERGED;
+    }
+    return worst;
+}
+
+}  // namespace
+
+extern "C" {
+
+int fcm_run_batched(fcm_handle h, fcm_slice* slices, int n_slices, int options) {
+    if (!h) return FCM_ERR_INVALID_ARG;
+    bool in_place = false;
+    int rc = check_slices(h, slices, n_slices, (int64_t)1 << 40, &in_place);
+    if (rc) return rc;
+    DeviceGuard g(h->device);
+    rc = fill_descs(h, slices, n_slices);
+    if (rc) return rc;
+    BatchedWorkspace* w = h->batched;
 
     fcm_batch_plan plan;
     if (w->forced) {
@@ -617,20 +658,25 @@ int fcm_run_batched(fcm_handle h, fcm_slice* slices, int n_slices, int options) 
     if (rc) return rc;
     w->last = plan;
 
-    int worst = FCM_OK;
-    for (int i = 0; i < n_slices; ++i) {
-        const SliceResult& r = w->h_res[i];
-        fcm_slice& s = slices[i];
-        s.iters = r.iters;
-        s.status = r.status;
-        s.flags = r.flags;
-        s.delta = r.delta;
-        s.J = r.J;
-        for (int j = 0; j < FCM_MAX_CLUSTERS; ++j) s.V64[j] = j < s.C ? r.V64[j] : 0.0;
-        if (r.status < 0 && worst >= 0) worst = r.status;
-        if (r.status == FCM_NOT_CONVERGED && worst == FCM_OK) worst = FCM_NOT_CONVERGED;
-    }
-    return worst;
+    return collect_results(h, slices, n_slices);
+}
+
+int fcm_run_batched_hist(fcm_handle h, fcm_slice* slices, int n_slices) {
+    if (!h) return FCM_ERR_INVALID_ARG;
+    bool in_place = false;
+    // 32-bit bin counters per slice
+    int rc = check_slices(h, slices, n_slices, (int64_t)1 << 31, &in_place);
+    if (rc) return rc;
+    DeviceGuard g(h->device);
+    rc = fill_descs(h, slices, n_slices);
+    if (rc) return rc;
+    BatchedWorkspace* w = h->batched;
+    CK(cudaMemcpyAsync(w->d_desc, w->h_desc, sizeof(SliceDesc) * n_slices, cudaMemcpyHostToDevice, h->stream));
+    CK(cudaMemcpyAsync(w->d_order, w->h_order, sizeof(int) * n_slices, cudaMemcpyHostToDevice, h->stream));
+    CK(launch_bhist(w->d_desc, w->d_order, n_slices, w->d_res, h->stream));
+    CK(cudaMemcpyAsync(w->h_res, w->d_res, sizeof(SliceResult) * n_slices, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return collect_results(h, slices, n_slices);
 }
 
 int fcm_batched_plan(fcm_handle h, fcm_batch_plan* plan) {

@@ -68,6 +68,11 @@ struct BatchKernel {
 BatchKernel batched_kernel_256();
 BatchKernel batched_kernel_512();
 
+// Histogram-domain runs of 8-bit slices, one CTA per slice in the given order
+// (fcm_bhist.cu).
+cudaError_t launch_bhist(const SliceDesc* descs, const int* order, int n_slices, SliceResult* results,
+                         cudaStream_t s);
+
 // ---- round-synchronous schedule (every slice steps in every round) ----
 
 constexpr int ROUND_SUMS = 2 * FCM_MAX_CLUSTERS + 3;  // values per slot: num[C], den[C], J, max|dU|, bad

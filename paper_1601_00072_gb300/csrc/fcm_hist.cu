@@ -23,6 +23,7 @@
 #include "fcm.h"
 #include "fcm_device.cuh"
 #include "fcm_df.cuh"
+#include "fcm_hist_bins.cuh"
 #include "fcm_runtime.h"
 
 namespace fcm {
@@ -52,12 +53,7 @@ using namespace fcm;
 
 namespace {
 
-constexpr int HNT = 256;
 constexpr int HCHUNK = 4;  // pixels per thread whose loads are issued together in the first pass
-
-__device__ __forceinline__ bool grey_level(float v) {
-    return v >= 0.0f && v <= 255.0f && v == rintf(v);  // false for NaN
-}
 
 // Pass over the pixels: histogram, input checks, and (from U^0) the
 // numerators and denominators of V^1 (Eq. 3) as per-block FP64 slots.
@@ -174,16 +170,6 @@ __device__ __forceinline__ void block_sums(double (&v)[S], float& mx, double (*r
     __syncthreads();
 }
 
-// w * (hh + hl) as a double-float pair: the exact product w * hh (TwoProd by
-// FMA) plus the small w * hl.
-__device__ __forceinline__ DF weighted(float w, float hh, float hl) {
-    const float p = w * hh;
-    const float e = fmaf(w, hh, -p);
-    DF d{p, 0.0f};
-    df_add(d, fmaf(w, hl, e));
-    return d;
-}
-
 // V^1: from the pass-0 slots (U^0 given), or from the bins with
 // U^0 = f(grey level, V^0) (Eq. 4 then Eq. 3). One CTA.
 template <int C, int MK, bool FROM_U>
@@ -288,29 +274,20 @@ __global__ void __launch_bounds__(HNT) k_hist_delta1(const float* __restrict__ x
     }
 }
 
-// Algorithm 1 on the bins, one CTA, thread b = grey level b. Sums over the
-// bins run in compensated FP32 (per-bin exact products, double-float warp
-// trees, the eight warp totals merged in a fixed order by warp 0), so the
-// loop needs no FP64 arithmetic; V64 is formed once at the end.
+// Algorithm 1 on the bins, one CTA, thread b = grey level b (solve_bins);
+// V64 is formed once at the end.
 template <int C, int MK, bool FROM_U>
 __global__ void __launch_bounds__(HNT) k_hist_solve(HistState* st, float* __restrict__ table, float m, float inv_m1,
                                                    float eps, int max_iter) {
-    constexpr int S = 2 * C + 1;
-    __shared__ DF wtot[HNT / 32][S];
-    __shared__ float wmax[HNT / 32];
-    __shared__ DF tot[S];
-    __shared__ float s_v[C], s_delta;
-    __shared__ double s_v64[C];
-    __shared__ int s_empty;
+    __shared__ BinScratch sc;
     if (st->bad) return;
-    const int b = threadIdx.x, lane = b & 31, warp = b >> 5;
-    const unsigned long long cnt = st->hist[b];
-    const bool present = cnt > 0ull;
-    // the count as an unevaluated float pair (exact below 2^48)
-    const float hh = (float)cnt, hl = (float)((double)cnt - (double)hh);
-    float v[C], up[C], u[C], um[C];
+    const int b = threadIdx.x;
+    float v[C], up[C], u[C];
 #pragma unroll
-    for (int j = 0; j < C; ++j) v[j] = st->V[j];
+    for (int j = 0; j < C; ++j) {
+        v[j] = st->V[j];
+        up[j] = 0.0f;
+    }
     if (!FROM_U) {
         float v0[C], um0[C];
 #pragma unroll
@@ -318,73 +295,11 @@ __global__ void __launch_bounds__(HNT) k_hist_solve(HistState* st, float* __rest
         membership<C, MK>((float)b, v0, m, inv_m1, up, um0);
     }
     int flags = st->flags;
-    double v64 = b < C ? st->V64[b] : 0.0;  // thread j keeps the FP64 quotient behind v_j
-    int status = FCM_NOT_CONVERGED, k = 1;
-    float delta = 0.0f;
-    for (k = 1;; ++k) {
-        const float Ji = membership<C, MK>((float)b, v, m, inv_m1, u, um);
-        DF s[S];
-        float mx = 0.0f;
-#pragma unroll
-        for (int j = 0; j < C; ++j) {
-            s[j] = weighted(um[j] * (float)b, hh, hl);
-            s[C + j] = weighted(um[j], hh, hl);
-            if (present && !(FROM_U && k == 1)) mx = fmaxf(mx, fabsf(u[j] - up[j]));
-        }
-        s[2 * C] = weighted(Ji, hh, hl);
-#pragma unroll
-        for (int q = 0; q < S; ++q) s[q] = warp_sum_df(s[q]);
-        mx = warp_max(mx);
-        if (lane == 0) {
-#pragma unroll
-            for (int q = 0; q < S; ++q) wtot[warp][q] = s[q];
-            wmax[warp] = mx;
-        }
-        __syncthreads();
-        if (warp == 0) {
-            // lane q merges sum q over the warps, in warp order
-            if (lane < S) {
-                DF t = wtot[0][lane];
-                for (int w = 1; w < HNT / 32; ++w) t = df_merge(t, wtot[w][lane]);
-                tot[lane] = t;
-            }
-            float dm = lane < HNT / 32 ? wmax[lane] : 0.0f;
-            dm = warp_max(dm);
-            __syncwarp();
-            if (lane == 0) s_delta = (FROM_U && k == 1) ? __uint_as_float(st->d1bits) : dm;
-            // V^{k+1} (Eq. 3), computed by lane j; an empty cluster keeps v_j
-            bool empty = false;
-            if (lane < C) {
-                const DF den = tot[C + lane];
-                if (den.hi > 0.0f) {
-                    const DF q = df_div(tot[lane], den);
-                    s_v[lane] = q.hi;
-                    s_v64[lane] = (double)q.hi + (double)q.lo;
-                } else {
-                    s_v[lane] = v[lane];
-                    s_v64[lane] = v64;
-                    empty = true;
-                }
-            }
-            const unsigned em = __ballot_sync(0xffffffffu, empty);
-            if (lane == 0) s_empty = em != 0u;
-        }
-        __syncthreads();
-        delta = s_delta;
-        if (delta < eps) {
-            status = FCM_OK;
-            break;
-        }
-        if (k >= max_iter) break;
-#pragma unroll
-        for (int j = 0; j < C; ++j) {
-            up[j] = u[j];
-            v[j] = s_v[j];
-        }
-        if (b < C) v64 = s_v64[b];
-        if (s_empty) flags |= FCM_FLAG_EMPTY_CLUSTER;
-        __syncthreads();  // s_v and the totals are reused by the next iteration
-    }
+    double v64 = b < C ? st->V64[b] : 0.0;  // thread j keeps the quotient behind v_j
+    int k, status;
+    float delta;
+    solve_bins<C, MK>(sc, st->hist[b], FROM_U, FROM_U ? __uint_as_float(st->d1bits) : 0.0f, v, up, u, v64, m, inv_m1,
+                      eps, max_iter, flags, k, status, delta);
 #pragma unroll
     for (int j = 0; j < C; ++j) table[b * C + j] = u[j];
     if (b == 0) {
@@ -392,7 +307,7 @@ __global__ void __launch_bounds__(HNT) k_hist_solve(HistState* st, float* __rest
         st->status = status;
         st->flags = flags;
         st->delta = (double)delta;
-        st->J = (double)tot[2 * C].hi + (double)tot[2 * C].lo;
+        st->J = (double)sc.tot[2 * C].hi + (double)sc.tot[2 * C].lo;
 #pragma unroll
         for (int j = 0; j < C; ++j) st->V[j] = v[j];
     }

@@ -431,6 +431,19 @@ class FCM:
             b.read_back()
         return st
 
+    def run_batched_hist(self, slices, raise_on_error: bool = False, read_back: bool = True) -> int:
+        """Algorithm 1 on the 256-bin histogram of every slice of a batch of
+        8-bit slices, one CTA per slice (see ``fcm_run_batched_hist``). Same
+        slices, fields and return value as ``run_batched``."""
+        b = _as_batch(slices)
+        self._bind_stream()
+        st = self._lib.fcm_run_batched_hist(self._h, self._arr_ptr(b.arr), len(b))
+        if st in (_lib.FCM_ERR_INVALID_ARG, _lib.FCM_ERR_CUDA, _lib.FCM_ERR_OOM) or raise_on_error:
+            _lib.check(st, self._h)
+        if read_back or not isinstance(slices, Batch):
+            b.read_back()
+        return st
+
     def run_batched_warm(self, slices, tune: bool = True, retune: bool = False, graph: bool = True,
                          read_back: bool = True):
         """Warm-started batch (``fcm_run_batched_warm``): predicted V^0, with the
