@@ -22,7 +22,8 @@ network predicts V^0), each with inputs resident in HBM. A warm slice that
 fails the acceptance rule (centers within 1e-4 of the cold start's, or a final
 J no larger) is charged its cold start on top: the time it adds to a cold
 batch (headline), and, reported beside it, the time of rerunning the failed
-slices as a batch of their own.
+slices as a batch of their own. ``batched.histogram_domain`` times the same
+cold batch through the histogram-domain path (one CTA per slice).
 
 ``--impl reference`` times the FP64 CPU oracle instead, on a bounded sample of
 the same workload (rank 0 only).
