@@ -74,3 +74,13 @@ def test_kernels_are_sm103a(libpath):
     flags the library was linked with, not by disassembling it)."""
     from paper_1601_00072_gb300 import _build
     assert "arch=compute_103a,code=sm_103a" in _build.ARCH
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    """Without the built CUDA library the binding raises; nothing falls back
+    to a CPU path."""
+    from paper_1601_00072_gb300 import _lib
+    monkeypatch.setattr(_lib, "_lib", None)
+    monkeypatch.setattr(_lib, "library_path", lambda: str(tmp_path / "libfcm_gb300.so"))
+    with pytest.raises(RuntimeError, match="not built"):
+        _lib.load()
