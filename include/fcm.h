@@ -113,6 +113,42 @@ int fcm_set_stream(fcm_handle h, void* cuda_stream);
 void fcm_destroy(fcm_handle h);
 
 /*
+ * Bounds of the device-side waits, and fault injection for tests. Not in the
+ * paper: its kernels never wait on one another (Sec. 4); here a whole run is
+ * one cooperative launch whose blocks meet at a grid-wide barrier after every
+ * pass, and passes wait for TMA copies. Every such wait polls a bounded number
+ * of times and then gives up: the run ends with FCM_ERR_TIMEOUT (U and V
+ * unspecified) and the handle stays usable.
+ *
+ *   grid_wait_spins   polls, about 128 ns apart, of a grid-wide barrier
+ *                     (whole-run, U-free, multi-feature and round-schedule
+ *                     kernels). 0 = the default 2^23 (about 1 s). The
+ *                     environment variable FCM_TIMEOUT_SPINS sets the default
+ *                     of new handles.
+ *   tma_wait_polls    suspensions, up to about 1 ms each, of a wait for a TMA
+ *                     copy to land. 0 = the default 2048.
+ *   barrier_phantoms  for tests: every grid-wide barrier also waits for this
+ *                     many arrivals that never come, so it gives up after
+ *                     grid_wait_spins polls. 0 (normal use) to 1024.
+ *   fail_alloc_in     for tests: when > 0, the handle's allocation that many
+ *                     calls from now (1 = the next) fails as if the device
+ *                     were out of memory, once: the entry point that made it
+ *                     returns FCM_ERR_OOM and a later call completes the
+ *                     workspace. 0 = off.
+ */
+typedef struct {
+    uint32_t grid_wait_spins;
+    uint32_t tma_wait_polls;
+    uint32_t barrier_phantoms;
+    int32_t fail_alloc_in;
+} fcm_limits;
+
+/* Set the limits (NULL restores every default and turns injection off). */
+int fcm_set_limits(fcm_handle h, const fcm_limits* lim);
+/* The limits in force (defaults filled in). */
+int fcm_get_limits(fcm_handle h, fcm_limits* lim);
+
+/*
  * fcm_run — Algorithm 1 on one image (Sec. 2.1, Eqs. 1, 3, 4; the paper's
  * center kernels of Sec. 4.2 and membership kernel of Sec. 4.3 are one fused
  * pass here, and its host-side convergence check of Sec. 4.3 runs on the
@@ -466,8 +502,10 @@ int fcm_time_pass(fcm_handle h, const float* x, int64_t n, int C, float m, float
  *
  * The first call on each device looks up the scratch address and the kernels'
  * launch limits on that device; make that first call before capturing any
- * stream into a CUDA graph. Every call shares the one scratch array and
- * resets it as needed, so calls must not overlap on the GPU: calls from
+ * stream into a CUDA graph. Every call copies its run state through host
+ * memory and synchronises its stream, so a stream that is being captured is
+ * refused with FCM_ERR_INVALID_ARG. Every call shares the one scratch array
+ * and resets it as needed, so calls must not overlap on the GPU: calls from
  * several host threads, or on streams not ordered with one another, race.
  */
 #define FCM_NOALLOC_MAX_BLOCKS 512

@@ -18,9 +18,17 @@ histogram to initial centers V^0:
   loss    = sum_{b, j < C_b} (y_bj - t_bj)^2 / sum_b C_b   (masked MSE)
   targets t_bj = (sorted converged centers of slice b) / 255 for j < C_b.
 
+Training takes Adam steps (Kingma & Ba 2015, Algorithm 1) with bias
+correction: for step t with gradient g,
+  m <- b1 m + (1 - b1) g,  v <- b2 v + (1 - b2) g^2,
+  w <- w - lr (m / (1 - b1^t)) / (sqrt(v / (1 - b2^t)) + eps).
+
 Weights are stored as W[out, in]. ``params`` is a dict of FP64 arrays W1, b1,
-W2, b2, W3, b3. Pinned by ``tests/test_oracle_mlp.py`` (finite differences,
-closed values of GELU, a zero network's loss, histogram invariants).
+W2, b2, W3, b3. Pinned by ``tests/test_oracle_mlp.py``: finite differences of
+the loss, closed values of GELU, a zero network's loss, a network with
+hand-set weights whose outputs are exact (each pre-activation is 0, +-1 or far
+into GELU's linear or zero regime), histogram invariants, and the closed forms
+of the first two Adam steps.
 """
 from __future__ import annotations
 
@@ -116,3 +124,29 @@ def unflat(v):
 
 
 N_PARAMS = sum(int(np.prod(s)) for s in PARAM_SHAPES.values())
+
+
+ADAM_B1 = 0.9
+ADAM_B2 = 0.999
+ADAM_EPS = 1e-8
+
+
+def adam_step(params, grads, m, v, t, lr, b1=ADAM_B1, b2=ADAM_B2, eps=ADAM_EPS):
+    """Adam step t (1-based) on every parameter, FP64; returns the new
+    (params, m, v). ``m`` and ``v`` are dicts like ``params`` (zero before the
+    first step)."""
+    c1 = 1.0 - b1 ** t
+    c2 = 1.0 - b2 ** t
+    out_p, out_m, out_v = {}, {}, {}
+    for k in PARAM_ORDER:
+        g = np.asarray(grads[k], dtype=np.float64)
+        mk = b1 * np.asarray(m[k], dtype=np.float64) + (1.0 - b1) * g
+        vk = b2 * np.asarray(v[k], dtype=np.float64) + (1.0 - b2) * g * g
+        out_p[k] = np.asarray(params[k], dtype=np.float64) - lr * (mk / c1) / (np.sqrt(vk / c2) + eps)
+        out_m[k] = mk
+        out_v[k] = vk
+    return out_p, out_m, out_v
+
+
+def zeros_like_params():
+    return {k: np.zeros(PARAM_SHAPES[k]) for k in PARAM_ORDER}

@@ -48,6 +48,11 @@ class fcm_slice(ctypes.Structure):
                 ("V64", ctypes.c_double * FCM_MAX_CLUSTERS)]
 
 
+class fcm_limits(ctypes.Structure):
+    _fields_ = [("grid_wait_spins", ctypes.c_uint32), ("tma_wait_polls", ctypes.c_uint32),
+                ("barrier_phantoms", ctypes.c_uint32), ("fail_alloc_in", ctypes.c_int32)]
+
+
 class fcm_batch_plan(ctypes.Structure):
     _fields_ = [("block", ctypes.c_int), ("cluster", ctypes.c_int), ("big", ctypes.c_int64),
                 ("ms", ctypes.c_double), ("schedule", ctypes.c_int), ("tile", ctypes.c_int)]
@@ -75,6 +80,8 @@ SIGNATURES = [
     ("fcm_create", _i, [ctypes.POINTER(_vp), _i, _vp]),
     ("fcm_set_stream", _i, [_vp, _vp]),
     ("fcm_destroy", None, [_vp]),
+    ("fcm_set_limits", _i, [_vp, ctypes.POINTER(fcm_limits)]),
+    ("fcm_get_limits", _i, [_vp, ctypes.POINTER(fcm_limits)]),
     ("fcm_run", _i, [_vp, _vp, _i64, _i, _f, _f, _i, _i, _vp, _vp, _vp, _i,
                      ctypes.POINTER(fcm_report)]),
     ("fcm_run_stream", _i, [_vp, _i, ctypes.POINTER(_vp), _i64, _i, _f, _f, _i, ctypes.POINTER(_vp),

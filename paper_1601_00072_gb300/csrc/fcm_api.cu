@@ -17,6 +17,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -58,6 +59,17 @@ void init_table() {
     register_single_c8(g_table);
 }
 
+// Default wait bounds of a handle; FCM_TIMEOUT_SPINS overrides the grid
+// barrier's.
+WaitLimits default_limits() {
+    WaitLimits w{DEFAULT_GRID_SPINS, DEFAULT_TMA_POLLS, 0u, 0u};
+    if (const char* e = std::getenv("FCM_TIMEOUT_SPINS")) {
+        const long long v = std::atoll(e);
+        if (v > 0 && v <= 0xffffffffll) w.grid_spins = (uint32_t)v;
+    }
+    return w;
+}
+
 bool is_device_pointer(const void* p) {
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
@@ -90,12 +102,35 @@ int ctx_invalid(fcm_ctx* h, const char* what) {
     return FCM_ERR_INVALID_ARG;
 }
 
+// Counts down the injected failure of fcm_set_limits: true when this
+// allocation is the one to fail.
+static bool injected_failure(fcm_ctx* h) {
+    if (!h || h->alloc_fail_in <= 0) return false;
+    return --h->alloc_fail_in == 0;
+}
+
+cudaError_t dev_malloc_raw(fcm_ctx* h, void** p, size_t bytes) {
+    if (injected_failure(h)) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    return cudaMalloc(p, bytes);
+}
+
+cudaError_t host_malloc_raw(fcm_ctx* h, void** p, size_t bytes) {
+    if (injected_failure(h)) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    return cudaMallocHost(p, bytes);
+}
+
 int ctx_grow(fcm_ctx* h, void** p, size_t* cap, size_t bytes, const char* what) {
     if (*cap >= bytes) return 0;
     if (*p) cudaFree(*p);
     *p = nullptr;
     *cap = 0;
-    cudaError_t e = cudaMalloc(p, bytes);
+    cudaError_t e = dev_malloc_raw(h, p, bytes);
     if (e != cudaSuccess) {
         *p = nullptr;
         return ctx_fail(h, e, what);
@@ -114,13 +149,18 @@ int ctx_grow(fcm_ctx* h, void** p, size_t* cap, size_t bytes, const char* what) 
 
 namespace {
 
+// Each buffer is allocated when missing, so a call after a failed allocation
+// completes the workspace.
 int ensure_single_workspace(fcm_ctx* h) {
-    if (h->d_st) return 0;
-    CK(cudaMalloc(&h->d_st, sizeof(RunState)));
-    CK(cudaMemset(h->d_st, 0, sizeof(RunState)));
-    CK(cudaMallocHost(&h->h_st, sizeof(RunState)));
-    h->partial_blocks = h->num_sms * 32;
-    CK(cudaMalloc(&h->d_partials, sizeof(double) * SLOTS_MAX * h->partial_blocks));
+    if (!h->d_st) {
+        CK(dev_malloc(h, &h->d_st, sizeof(RunState)));
+        CK(cudaMemset(h->d_st, 0, sizeof(RunState)));
+    }
+    if (!h->h_st) CK(host_malloc(h, &h->h_st, sizeof(RunState)));
+    if (!h->d_partials) {
+        h->partial_blocks = h->num_sms * 32;
+        CK(dev_malloc(h, &h->d_partials, sizeof(double) * SLOTS_MAX * h->partial_blocks));
+    }
     return 0;
 }
 
@@ -275,7 +315,35 @@ int fcm_create(fcm_handle* out, int device, void* cuda_stream) {
     h->coop = coop != 0;
     h->max_smem_optin = (int)prop.sharedMemPerBlockOptin;
     h->device_name = prop.name;
+    h->limits = default_limits();
     *out = h;
+    return FCM_OK;
+}
+
+int fcm_set_limits(fcm_handle h, const fcm_limits* lim) {
+    if (!h) return FCM_ERR_INVALID_ARG;
+    const WaitLimits dflt = default_limits();
+    if (!lim) {
+        h->limits = dflt;
+        h->alloc_fail_in = 0;
+        return FCM_OK;
+    }
+    if (lim->barrier_phantoms > 1024u || lim->fail_alloc_in < 0)
+        return ctx_invalid(h, "limits: barrier_phantoms <= 1024 and fail_alloc_in >= 0");
+    h->limits.grid_spins = lim->grid_wait_spins ? lim->grid_wait_spins : dflt.grid_spins;
+    h->limits.tma_polls = lim->tma_wait_polls ? lim->tma_wait_polls : DEFAULT_TMA_POLLS;
+    h->limits.phantoms = lim->barrier_phantoms;
+    h->alloc_fail_in = lim->fail_alloc_in;
+    return FCM_OK;
+}
+
+int fcm_get_limits(fcm_handle h, fcm_limits* lim) {
+    if (!h || !lim) return FCM_ERR_INVALID_ARG;
+    std::memset(lim, 0, sizeof(*lim));
+    lim->grid_wait_spins = h->limits.grid_spins;
+    lim->tma_wait_polls = h->limits.tma_polls;
+    lim->barrier_phantoms = h->limits.phantoms;
+    lim->fail_alloc_in = h->alloc_fail_in;
     return FCM_OK;
 }
 
@@ -400,6 +468,7 @@ int fcm_run(fcm_handle h, const float* x, int64_t n, int C, float m, float eps, 
     hs->max_iter = max_iter;
     hs->C = C;
     hs->status = STATUS_RUNNING;
+    hs->lim = h->limits;
     if (init_mode == FCM_INIT_V && !V_dev) std::memcpy(hs->V0, V, sizeof(float) * C);
     CK(cudaMemcpyAsync(h->d_st, hs, sizeof(RunState), cudaMemcpyHostToDevice, h->stream));
     if (init_mode == FCM_INIT_V && V_dev)
@@ -506,7 +575,7 @@ int fcm_run_stream(fcm_handle h, int n_images, const float* const* x, int64_t n,
         if (h->h_pipe_st) cudaFreeHost(h->h_pipe_st);
         h->h_pipe_st = nullptr;
         h->pipe_st_cap = 0;
-        CK(cudaMallocHost(&h->h_pipe_st, sizeof(RunState) * (size_t)n_images));
+        CK(host_malloc(h, &h->h_pipe_st, sizeof(RunState) * (size_t)n_images));
         h->pipe_st_cap = n_images;
     }
     if (!h->pipe_in) {
@@ -550,6 +619,7 @@ int fcm_run_stream(fcm_handle h, int n_images, const float* const* x, int64_t n,
         hs->max_iter = max_iter;
         hs->C = C;
         hs->status = STATUS_RUNNING;
+        hs->lim = h->limits;
         const float* u0 = (U0 && U0[i]) ? U0[i] : U[i];
         // upload, once the download of image i - NS has drained this set
         if (i >= NS) e = cudaStreamWaitEvent(h->pipe_in, out_done[b], 0);
@@ -636,6 +706,7 @@ int fcm_time_pass(fcm_handle h, const float* x, int64_t n, int C, float m, float
     hs->C = C;
     hs->k = 1;
     hs->status = STATUS_RUNNING;
+    hs->lim = h->limits;
     const bool V_dev = is_device_pointer(V);
     if (!V_dev)
         for (int j = 0; j < C; ++j) {

@@ -96,10 +96,10 @@ int ensure_batched(fcm_ctx* h, int n) {
     if (!h->batched) h->batched = new BatchedWorkspace();
     BatchedWorkspace* w = h->batched;
     if (!w->cap_stream) CK(cudaStreamCreateWithFlags(&w->cap_stream, cudaStreamNonBlocking));
-    if (!w->d_ctl) CK(cudaMalloc(&w->d_ctl, sizeof(BatchCtl)));
-    if (!w->d_rctl) CK(cudaMalloc(&w->d_rctl, sizeof(RoundCtl)));
-    if (!w->d_rhdr) CK(cudaMalloc(&w->d_rhdr, sizeof(RoundsHdr)));
-    if (!w->h_rhdr) CK(cudaMallocHost(&w->h_rhdr, sizeof(RoundsHdr)));
+    if (!w->d_ctl) CK(dev_malloc(h, &w->d_ctl, sizeof(BatchCtl)));
+    if (!w->d_rctl) CK(dev_malloc(h, &w->d_rctl, sizeof(RoundCtl)));
+    if (!w->d_rhdr) CK(dev_malloc(h, &w->d_rhdr, sizeof(RoundsHdr)));
+    if (!w->h_rhdr) CK(host_malloc(h, &w->h_rhdr, sizeof(RoundsHdr)));
     if (w->cap >= n) return 0;
     free_graphs(w);  // graphs point at the old buffers
     void* dev[] = {w->d_desc, w->d_res, w->d_order, w->d_rstate, w->d_slot_base};
@@ -117,15 +117,15 @@ int ensure_batched(fcm_ctx* h, int n) {
     w->h_slot_base = nullptr;
     w->cap = 0;
     const int cap = std::max(n, 64);
-    CK(cudaMalloc(&w->d_desc, sizeof(SliceDesc) * cap));
-    CK(cudaMalloc(&w->d_res, sizeof(SliceResult) * cap));
-    CK(cudaMalloc(&w->d_order, sizeof(int) * cap));
-    CK(cudaMalloc(&w->d_rstate, sizeof(RoundSlice) * cap));
-    CK(cudaMalloc(&w->d_slot_base, sizeof(int) * (cap + 1)));
-    CK(cudaMallocHost(&w->h_desc, sizeof(SliceDesc) * cap));
-    CK(cudaMallocHost(&w->h_res, sizeof(SliceResult) * cap));
-    CK(cudaMallocHost(&w->h_order, sizeof(int) * cap));
-    CK(cudaMallocHost(&w->h_slot_base, sizeof(int) * (cap + 1)));
+    CK(dev_malloc(h, &w->d_desc, sizeof(SliceDesc) * cap));
+    CK(dev_malloc(h, &w->d_res, sizeof(SliceResult) * cap));
+    CK(dev_malloc(h, &w->d_order, sizeof(int) * cap));
+    CK(dev_malloc(h, &w->d_rstate, sizeof(RoundSlice) * cap));
+    CK(dev_malloc(h, &w->d_slot_base, sizeof(int) * (cap + 1)));
+    CK(host_malloc(h, &w->h_desc, sizeof(SliceDesc) * cap));
+    CK(host_malloc(h, &w->h_res, sizeof(SliceResult) * cap));
+    CK(host_malloc(h, &w->h_order, sizeof(int) * cap));
+    CK(host_malloc(h, &w->h_slot_base, sizeof(int) * (cap + 1)));
     w->cap = cap;
     return 0;
 }
@@ -152,7 +152,7 @@ int fill_slots(fcm_ctx* h, const fcm_slice* slices, int n, int min_chunk) {
         w->d_rpart = nullptr;
         w->slot_cap = 0;
         const int64_t cap = std::max<int64_t>(total + total / 4, 4096);
-        CK(cudaMalloc(&w->d_rpart, sizeof(double) * ROUND_SUMS * cap));
+        CK(dev_malloc(h, &w->d_rpart, sizeof(double) * ROUND_SUMS * cap));
         w->slot_cap = cap;
     }
     return 0;
@@ -231,6 +231,8 @@ int launch_rounds(fcm_ctx* h, cudaStream_t s, const fcm_batch_plan& p, int n_sli
     a.slot_base = w->d_slot_base;
     a.partials = w->d_rpart;
     a.min_chunk = p.tile;
+    a.wait_spins = h->limits.grid_spins;
+    a.phantoms = h->limits.phantoms;
     cudaLaunchConfig_t cfg;
     std::memset(&cfg, 0, sizeof(cfg));
     cudaLaunchAttribute attr[1];

@@ -115,6 +115,8 @@ struct RoundsArgs {
     double* partials;      // [slots * ROUND_SUMS], sum-major within a slice
     int min_chunk;         // fewest pixels a CTA takes in a round (even)
     int pad;
+    uint32_t wait_spins;   // polls of the round barrier before it gives up
+    uint32_t phantoms;     // extra arrivals the barrier waits for (fault injection; 0 normally)
 };
 
 // Slots a slice needs: at most ceil(n / min_chunk) + 1 CTAs share it in a round.

@@ -1,19 +1,23 @@
 // Device-side building blocks of the FCM pixel pass (sm_103a).
 //
 // Membership (Eq. 4 of arXiv:1601.00072) is evaluated in its weight form:
-//   u_j = w_j / sum_k w_k,   w_j = (q_j)^(1/(m-1)),   q_j = d2min / d2_j,
+//   u_j = w_j / sum_k w_k,   w_j = (r_j)^(2/(m-1)),   r_j = |d|min / |d_j|,
 // which equals 1 / sum_k (d_j / d_k)^(2/(m-1)) after dividing numerator and
-// denominator by sum_k w_k; the common factor d2min^(1/(m-1)) keeps every
-// weight in (0, 1], so no weight or sum can overflow even for tiny distances.
-// A pixel at distance exactly 0 from one or more centers gives those clusters
-// equal shares and the others 0 (Bezdek's rule; the paper leaves d = 0 open).
-// "Exactly 0" means (x - v)^2 == 0 in FP32 with flush-to-zero.
+// denominator by sum_k w_k; the common factor keeps every weight in (0, 1], so
+// no weight or sum can overflow. The ratio is taken of the distances
+// |x - v_j| themselves, not of their squares, so it stays exact for distances
+// down to the smallest normal float (2^-126) even where their squares would
+// underflow.
+// A pixel at distance 0 from one or more centers gives those clusters equal
+// shares and the others 0 (Bezdek's rule; the paper leaves d = 0 open).
+// "Distance 0" means |x - v| below 2^-126, i.e. zero once the FP32
+// approximate instructions flush subnormal operands to zero.
 //
 // Specialisations of the fuzzifier avoid general powers on the hot path:
-//   m = 2    w = q                u^m = u*u
-//   m = 3    w = sqrt(q)          u^m = u*u*u
-//   m = 1.5  w = q*q              u^m = u*sqrt(u)
-//   other m  w = 2^((log2 q)/(m-1))   u^m = 2^(m log2 u)
+//   m = 2    w = r*r              u^m = u*u
+//   m = 3    w = r                u^m = u*u*u
+//   m = 1.5  w = (r*r)^2          u^m = u*sqrt(u)
+//   other m  w = 2^(2 log2(r)/(m-1))   u^m = 2^(m log2 u)
 // using the PTX approximate instructions (rcp, rsqrt, sqrt, lg2, ex2), whose
 // documented error is at most a few ulp in FP32.
 #pragma once
@@ -64,38 +68,38 @@ __device__ __forceinline__ float pow_m(float u, float m) {
     return ex2_approx(m * lg2_approx(u));  // lg2(0) = -inf -> ex2(-inf) = 0
 }
 
+// Smallest normal FP32 value: distances (and sums of products of distances)
+// below it count as zero, as the .ftz instructions would read them.
+__device__ __forceinline__ float flt_min() { return __int_as_float(0x00800000); }
+
 // Memberships of one pixel x against C centers v (Eq. 4). Writes u[j] and
 // um[j] = u[j]^m; returns this pixel's term of J_m, sum_j u_j^m d_j^2 (Eq. 1),
 // through its closed form under Eq. 4: with u_j = w_j / S and
 // w_j = (d2min / d2_j)^(1/(m-1)), u_j^m d2_j = d2min w_j / S^m, so the term is
 // d2min * S^(1-m) (and 0 when the pixel sits on a center).
 template <int C, int MK>
-__device__ __forceinline__ float membership(float x, const float (&v)[C], float m,
-                                            float inv_m1, float (&u)[C], float (&um)[C]) {
-    float d2[C];
-    float dmin = __int_as_float(0x7f800000);
+__device__ __forceinline__ float membership(float x, const float (&v)[C], float m, float inv_m1,
+                                            float (&u)[C], float (&um)[C]) {
+    float ad[C];
+    float amin = __int_as_float(0x7f800000);
 #pragma unroll
     for (int j = 0; j < C; ++j) {
-        const float d = x - v[j];
-        d2[j] = __fmul_rn(d, d);
-        dmin = fminf(dmin, d2[j]);
+        ad[j] = fabsf(x - v[j]);
+        amin = fminf(amin, ad[j]);
     }
     float Ji = 0.0f;
-    if (dmin > 0.0f) {
+    if (amin >= flt_min()) {
         float w[C];
         if (MK == M_GENERIC) {
-            const float l0 = lg2_approx(dmin);
+            const float l0 = lg2_approx(amin), e = 2.0f * inv_m1;
 #pragma unroll
-            for (int j = 0; j < C; ++j) w[j] = ex2_approx(inv_m1 * (l0 - lg2_approx(d2[j])));
-        } else if (MK == M_THREE) {
-            const float s0 = sqrt_approx(dmin);
-#pragma unroll
-            for (int j = 0; j < C; ++j) w[j] = s0 * rsqrt_approx(d2[j]);
+            for (int j = 0; j < C; ++j) w[j] = ex2_approx(e * (l0 - lg2_approx(ad[j])));
         } else {
 #pragma unroll
             for (int j = 0; j < C; ++j) {
-                const float q = dmin * rcp_approx(d2[j]);
-                w[j] = (MK == M_ONE_HALF) ? q * q : q;
+                const float r = amin * rcp_approx(ad[j]);
+                const float q = r * r;
+                w[j] = (MK == M_THREE) ? r : (MK == M_ONE_HALF) ? q * q : q;
             }
         }
         float S = 0.0f;
@@ -104,6 +108,7 @@ __device__ __forceinline__ float membership(float x, const float (&v)[C], float 
         const float r = rcp_approx(S);
 #pragma unroll
         for (int j = 0; j < C; ++j) u[j] = w[j] * r;
+        const float dmin = amin * amin;  // may underflow for tiny distances: the J term is then 0
         if (MK == M_TWO) Ji = dmin * r;
         else if (MK == M_THREE) Ji = dmin * r * r;
         else if (MK == M_ONE_HALF) Ji = dmin * sqrt_approx(r);
@@ -111,10 +116,10 @@ __device__ __forceinline__ float membership(float x, const float (&v)[C], float 
     } else {
         int nz = 0;
 #pragma unroll
-        for (int j = 0; j < C; ++j) nz += (d2[j] == 0.0f);
+        for (int j = 0; j < C; ++j) nz += (ad[j] < flt_min());
         const float share = __fdiv_rn(1.0f, (float)nz);
 #pragma unroll
-        for (int j = 0; j < C; ++j) u[j] = (d2[j] == 0.0f) ? share : 0.0f;
+        for (int j = 0; j < C; ++j) u[j] = (ad[j] < flt_min()) ? share : 0.0f;
     }
 #pragma unroll
     for (int j = 0; j < C; ++j) um[j] = pow_m<MK>(u[j], m);
@@ -170,9 +175,10 @@ __device__ __forceinline__ f2 abs2(f2 a) { return a & 0x7fffffff7fffffffull; }
 // one reciprocal per pixel; a pixel equal to exactly one center gets u = 1
 // there and 0 elsewhere without a special case. The J term is u_j b_j for any
 // j when m = 2 (both equal 1 / sum_k 1/d_k^2), and (u_j b_j)^2 when m = 3.
-// A pixel whose sum_k P_k is 0 (two or more centers hit exactly) or not
-// finite (products out of FP32 range) takes the scalar weight form above,
-// as do the other fuzzifiers.
+// A pixel whose sum_k P_k is 0 (two or more centers hit exactly), below the
+// smallest normal float (products of tiny distances), or not finite (products
+// out of FP32 range) takes the scalar weight form above, as do the other
+// fuzzifiers.
 template <int C, int MK>
 __device__ __forceinline__ f2 membership_pair(f2 x2, const f2 (&v2)[C], float m, float inv_m1,
                                               const float (&v)[C], f2 (&u2)[C], f2 (&um2)[C]) {
@@ -200,8 +206,10 @@ __device__ __forceinline__ f2 membership_pair(f2 x2, const f2 (&v2)[C], float m,
         for (int j = 1; j < C; ++j) S = add2(S, P[j]);
         float s0, s1;
         unpack2(S, s0, s1);
+        // a sum below the smallest normal float would be flushed to zero by
+        // the reciprocal: those pixels take the scalar form
         const float inf = __int_as_float(0x7f800000);
-        if (s0 > 0.0f && s0 < inf && s1 > 0.0f && s1 < inf) {
+        if (s0 >= flt_min() && s0 < inf && s1 >= flt_min() && s1 < inf) {
             const f2 r = pack2(rcp_approx(s0), rcp_approx(s1));
 #pragma unroll
             for (int j = 0; j < C; ++j) {

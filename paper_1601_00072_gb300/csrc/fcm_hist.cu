@@ -423,18 +423,16 @@ extern "C" int fcm_run_hist(fcm_handle h, const float* x, int64_t n, int C, floa
     DeviceGuard g(h->device);
     if (!h->hist) h->hist = new HistWorkspace();
     HistWorkspace* w = h->hist;
-    if (!w->d_st) {
-        CK(cudaMalloc(&w->d_st, sizeof(HistState)));
-        CK(cudaMallocHost(&w->h_st, sizeof(HistState)));
-        CK(cudaMalloc(&w->table, sizeof(float) * 256 * FCM_MAX_CLUSTERS));
-    }
+    if (!w->d_st) CK(dev_malloc(h, &w->d_st, sizeof(HistState)));
+    if (!w->h_st) CK(host_malloc(h, &w->h_st, sizeof(HistState)));
+    if (!w->table) CK(dev_malloc(h, &w->table, sizeof(float) * 256 * FCM_MAX_CLUSTERS));
     const int64_t want = (n + (int64_t)HNT * HCHUNK - 1) / ((int64_t)HNT * HCHUNK);
     const int nblocks = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)h->num_sms * 8));
     if (w->part_blocks < nblocks) {
         cudaFree(w->part);
         w->part = nullptr;
         w->part_blocks = 0;
-        CK(cudaMalloc(&w->part, sizeof(double) * 2 * FCM_MAX_CLUSTERS * nblocks));
+        CK(dev_malloc(h, &w->part, sizeof(double) * 2 * FCM_MAX_CLUSTERS * nblocks));
         w->part_blocks = nblocks;
     }
     HistState* hs = w->h_st;

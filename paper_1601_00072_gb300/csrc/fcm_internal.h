@@ -14,6 +14,20 @@ constexpr int WARP_TILE = 128;                           // pixels per warp tile
 constexpr int SLOTS_MAX = 2 * FCM_MAX_CLUSTERS + 4;      // num[C], den[C], J, delta, 2 flags
 constexpr int STATUS_RUNNING = 2;
 
+// Bounds of the device-side waits of one run, set per handle from the host
+// (fcm_set_limits). Every spin or suspension loop counts against one of them
+// and, when it runs out, the kernel records FCM_ERR_TIMEOUT and returns.
+struct WaitLimits {
+    uint32_t grid_spins;  // polls, about 128 ns apart, of a grid-wide barrier
+    uint32_t tma_polls;   // suspensions, up to about 1 ms each, of a wait for TMA bytes
+    uint32_t phantoms;    // arrivals every grid-wide barrier waits for beyond the
+                          // grid's own: 0 in normal use; a test sets 1 to make
+                          // every barrier give up (fault injection on the host side)
+    uint32_t pad;
+};
+constexpr uint32_t DEFAULT_GRID_SPINS = 1u << 23;  // about 1 s
+constexpr uint32_t DEFAULT_TMA_POLLS = 2048;       // about 2 s
+
 // Which half-step a launch of the pass performs.
 enum Pass : int {
     P_ACCUM0 = 0,  // V^1 from a given U^0 (Eq. 3); validates x and U^0
@@ -52,6 +66,7 @@ struct alignas(128) RunState {
     int iters;
     unsigned int ticket;  // last-block-done counter of the current pass
     int launches;         // passes started in this run (loop guard)
+    WaitLimits lim;
 };
 
 typedef void (*PassFn)(RunState*, double*, cudaGraphConditionalHandle, int);

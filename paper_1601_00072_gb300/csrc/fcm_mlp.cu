@@ -293,25 +293,26 @@ dim3 tiles(int M, int N) { return dim3((N + TT - 1) / TT, (M + TT - 1) / TT); }
 int ensure_mlp(fcm_ctx* h, int bcap) {
     if (!h->mlp) h->mlp = new MlpWorkspace();
     MlpWorkspace* w = h->mlp;
-    if (!w->master) {
-        CK(cudaMalloc(&w->master, sizeof(float) * N_PARAMS));
-        CK(cudaMalloc(&w->wbf, sizeof(__nv_bfloat16) * N_PARAMS));
-        CK(cudaMalloc(&w->adam_m, sizeof(float) * N_PARAMS));
-        CK(cudaMalloc(&w->adam_v, sizeof(float) * N_PARAMS));
-        CK(cudaMalloc(&w->grad, sizeof(float) * N_PARAMS));
-        CK(cudaMalloc(&w->loss, sizeof(float)));
-    }
+    // each buffer is allocated when missing, so a call after a failed
+    // allocation completes the workspace
+    if (!w->master) CK(dev_malloc(h, &w->master, sizeof(float) * N_PARAMS));
+    if (!w->wbf) CK(dev_malloc(h, &w->wbf, sizeof(__nv_bfloat16) * N_PARAMS));
+    if (!w->adam_m) CK(dev_malloc(h, &w->adam_m, sizeof(float) * N_PARAMS));
+    if (!w->adam_v) CK(dev_malloc(h, &w->adam_v, sizeof(float) * N_PARAMS));
+    if (!w->grad) CK(dev_malloc(h, &w->grad, sizeof(float) * N_PARAMS));
+    if (!w->loss) CK(dev_malloc(h, &w->loss, sizeof(float)));
     if (w->bcap < bcap) {
         float** bufs[] = {&w->xb, &w->tb, &w->z1, &w->a1, &w->z2, &w->a2, &w->y, &w->dy, &w->dz2, &w->dz1};
         const int64_t sizes[] = {D_IN, D_OUT, D_H, D_H, D_H, D_H, D_OUT, D_OUT, D_H, D_H};
+        w->bcap = 0;  // stays 0 until every buffer below is in place
         for (int i = 0; i < 10; ++i) {
             cudaFree(*bufs[i]);
             *bufs[i] = nullptr;
-            CK(cudaMalloc(bufs[i], sizeof(float) * sizes[i] * bcap));
+            CK(dev_malloc(h, bufs[i], sizeof(float) * sizes[i] * bcap));
         }
         cudaFree(w->cb);
         w->cb = nullptr;
-        CK(cudaMalloc(&w->cb, sizeof(int) * bcap));
+        CK(dev_malloc(h, &w->cb, sizeof(int) * bcap));
         w->bcap = bcap;
     }
     return 0;
@@ -427,7 +428,8 @@ int fcm_features_impl(fcm_ctx* h, const fcm_slice* slices, int n, float* feats) 
     if (w->hdesc_cap < n) {
         cudaFree(w->hdesc_dev);
         w->hdesc_dev = nullptr;
-        CK(cudaMalloc(&w->hdesc_dev, sizeof(HistDesc) * n));
+        w->hdesc_cap = 0;
+        CK(dev_malloc(h, &w->hdesc_dev, sizeof(HistDesc) * n));
         w->hdesc_cap = n;
     }
     CK(cudaMemcpyAsync(w->hdesc_dev, d.data(), sizeof(HistDesc) * n, cudaMemcpyHostToDevice, h->stream));
@@ -435,7 +437,7 @@ int fcm_features_impl(fcm_ctx* h, const fcm_slice* slices, int n, float* feats) 
         cudaFree(w->counts);
         w->counts = nullptr;
         w->counts_cap = 0;
-        CK(cudaMalloc(&w->counts, sizeof(unsigned) * D_HIST * n));
+        CK(dev_malloc(h, &w->counts, sizeof(unsigned) * D_HIST * n));
         CK(cudaMemsetAsync(w->counts, 0, sizeof(unsigned) * D_HIST * n, h->stream));
         w->counts_cap = n;
     }
@@ -464,8 +466,8 @@ int predict_v0(fcm_ctx* h, fcm_slice* slices, int n, std::vector<unsigned char>*
         w->feats = nullptr;
         w->v0 = nullptr;
         w->feat_cap = 0;
-        CK(cudaMalloc(&w->feats, sizeof(float) * D_IN * n));
-        CK(cudaMalloc(&w->v0, sizeof(float) * (D_OUT + 1) * n));
+        CK(dev_malloc(h, &w->feats, sizeof(float) * D_IN * n));
+        CK(dev_malloc(h, &w->v0, sizeof(float) * (D_OUT + 1) * n));
         w->feat_cap = n;
     }
     if ((rc = fcm_features_impl(h, slices, n, w->feats))) return rc;
@@ -601,7 +603,8 @@ int fcm_model_train(fcm_handle h, const float* feats, const float* targets, cons
     if (w->idx_cap < n) {
         cudaFree(w->idx);
         w->idx = nullptr;
-        CK(cudaMalloc(&w->idx, sizeof(int) * n));
+        w->idx_cap = 0;
+        CK(dev_malloc(h, &w->idx, sizeof(int) * n));
         w->idx_cap = n;
     }
     std::vector<int> perm(n);

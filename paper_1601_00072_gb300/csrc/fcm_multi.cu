@@ -89,10 +89,8 @@ extern "C" int fcm_run_multi(fcm_handle h, const float* x, int64_t n, int D, int
     DeviceGuard g(h->device);
     if (!h->multi) h->multi = new MultiWorkspace();
     MultiWorkspace* w = h->multi;
-    if (!w->d_st) {
-        CK(cudaMalloc(&w->d_st, sizeof(MultiState)));
-        CK(cudaMallocHost(&w->h_st, sizeof(MultiState)));
-    }
+    if (!w->d_st) CK(dev_malloc(h, &w->d_st, sizeof(MultiState)));
+    if (!w->h_st) CK(host_malloc(h, &w->h_st, sizeof(MultiState)));
     const MultiTable& t = multi_table();
     const MultiFn fn = t.run[D][C][m == 2.0f ? 0 : 1][from_u ? 0 : 1];
     int per_sm = 0;
@@ -112,7 +110,7 @@ extern "C" int fcm_run_multi(fcm_handle h, const float* x, int64_t n, int D, int
         cudaFree(w->partials);
         w->partials = nullptr;
         w->partial_floats = 0;
-        CK(cudaMalloc(&w->partials, sizeof(float) * need));
+        CK(dev_malloc(h, &w->partials, sizeof(float) * need));
         w->partial_floats = need;
     }
     MultiState* hs = w->h_st;
@@ -126,6 +124,7 @@ extern "C" int fcm_run_multi(fcm_handle h, const float* x, int64_t n, int D, int
     hs->eps = eps;
     hs->max_iter = max_iter;
     hs->status = FCM_ERR_TIMEOUT;
+    hs->lim = h->limits;
     if (!from_u && !V_dev) std::memcpy(hs->V0, V, sizeof(float) * C * D);
     CK(cudaMemcpyAsync(w->d_st, hs, sizeof(MultiState), cudaMemcpyHostToDevice, h->stream));
     if (!from_u && V_dev)

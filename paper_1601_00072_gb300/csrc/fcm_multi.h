@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include "fcm.h"
+#include "fcm_internal.h"
 
 namespace fcm {
 
@@ -23,6 +24,7 @@ struct alignas(128) MultiState {
     double delta, J;
     int iters, status, flags;
     unsigned ticket;  // grid barrier arrivals
+    WaitLimits lim;
 };
 
 typedef void (*MultiFn)(MultiState*, float*);

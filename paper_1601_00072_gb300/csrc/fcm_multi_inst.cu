@@ -28,7 +28,6 @@ constexpr int D = FCM_MULTI_D;
 constexpr int MNT = 256;
 constexpr int MNW = MNT / 32;
 constexpr int MCHUNK = 4;
-constexpr uint32_t GRID_WAIT_LIMIT = 1u << 23;  // about 1 s of 128 ns sleeps
 
 __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
     unsigned v;
@@ -38,7 +37,9 @@ __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
 
 // Memberships of one pixel from its squared distances d2[j] (Eq. 4 in the
 // weight form w_j = (d2min / d2_j)^(1/(m-1)), u_j = w_j / sum_k w_k, with the
-// zero-distance rule). Returns the pixel's J term, d2min * S^(1-m).
+// zero-distance rule). A squared distance below the smallest normal float
+// (2^-126) counts as zero, as the .ftz reciprocal and logarithm would read
+// it. Returns the pixel's J term, d2min * S^(1-m).
 template <int C, int MK>
 __device__ __forceinline__ float membership_d2(const float (&d2)[C], float m, float inv_m1, float (&u)[C],
                                                float (&um)[C]) {
@@ -46,7 +47,7 @@ __device__ __forceinline__ float membership_d2(const float (&d2)[C], float m, fl
 #pragma unroll
     for (int j = 0; j < C; ++j) dmin = fminf(dmin, d2[j]);
     float Ji = 0.0f;
-    if (dmin > 0.0f) {
+    if (dmin >= flt_min()) {
         float w[C];
         if (MK == M_TWO) {
 #pragma unroll
@@ -66,10 +67,10 @@ __device__ __forceinline__ float membership_d2(const float (&d2)[C], float m, fl
     } else {
         int nz = 0;
 #pragma unroll
-        for (int j = 0; j < C; ++j) nz += (d2[j] == 0.0f);
+        for (int j = 0; j < C; ++j) nz += (d2[j] < flt_min());
         const float share = __fdiv_rn(1.0f, (float)nz);
 #pragma unroll
-        for (int j = 0; j < C; ++j) u[j] = (d2[j] == 0.0f) ? share : 0.0f;
+        for (int j = 0; j < C; ++j) u[j] = (d2[j] < flt_min()) ? share : 0.0f;
     }
 #pragma unroll
     for (int j = 0; j < C; ++j) um[j] = (MK == M_TWO) ? u[j] * u[j] : ex2_approx(m * lg2_approx(u[j]));
@@ -225,10 +226,14 @@ __global__ void __launch_bounds__(MNT) k_fcm_run_multi(MultiState* __restrict__ 
         if (threadIdx.x == 0) {
             __threadfence();
             atomicAdd(&st->ticket, 1u);
-            const unsigned target = (unsigned)(p + 1) * gridDim.x;
+            // bounded by st->lim: grid_spins polls 128 ns apart, for the
+            // grid's arrivals plus st->lim.phantoms (0 unless a test injects
+            // a barrier that never fills)
+            const unsigned target = (unsigned)(p + 1) * gridDim.x + st->lim.phantoms;
+            const uint32_t limit = st->lim.grid_spins;
             uint32_t spins = 0;
             while (ld_acquire_u32(&st->ticket) < target) {
-                if (++spins > GRID_WAIT_LIMIT) {
+                if (++spins > limit) {
                     s_err = 1;
                     break;
                 }

@@ -109,6 +109,15 @@ extern "C" int fcm_run_noalloc(const float* x, int64_t n, int C, float m, float 
     if (!(m > 1.0f) || !std::isfinite(m) || !(eps >= 0.0f) || !std::isfinite(eps) || max_iter < 1)
         return FCM_ERR_INVALID_ARG;
     if (init_mode != FCM_INIT_U && init_mode != FCM_INIT_V) return FCM_ERR_INVALID_ARG;
+    // the call copies through host memory and synchronises its stream, which a
+    // stream under capture cannot do: refuse such a stream before any other
+    // runtime call
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing((cudaStream_t)cuda_stream, &cap) != cudaSuccess) {
+        cudaGetLastError();
+        return FCM_ERR_INVALID_ARG;
+    }
+    if (cap != cudaStreamCaptureStatusNone) return FCM_ERR_INVALID_ARG;
     if (init_mode == FCM_INIT_U && !U0) U0 = U;
     const float* Uin = init_mode == FCM_INIT_U ? U0 : U;
     if (!on_device(x) || !on_device(U) || !on_device(Uin)) return FCM_ERR_INVALID_ARG;
@@ -149,6 +158,7 @@ extern "C" int fcm_run_noalloc(const float* x, int64_t n, int C, float m, float 
     hs.max_iter = max_iter;
     hs.C = C;
     hs.status = STATUS_RUNNING;
+    hs.lim = WaitLimits{DEFAULT_GRID_SPINS, DEFAULT_TMA_POLLS, 0u, 0u};
     const bool V_dev = on_device(V);
     if (init_mode == FCM_INIT_V && !V_dev) std::memcpy(hs.V0, V, sizeof(float) * C);
 

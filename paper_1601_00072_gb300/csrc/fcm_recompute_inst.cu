@@ -28,8 +28,10 @@ namespace fcm {
 namespace {
 
 constexpr int WTILE = WARP_TILE;
-constexpr uint32_t WAIT_LIMIT = 2048;          // mbarrier waits of about 2 s (suspend hint 1 ms)
-constexpr uint32_t GRID_WAIT_LIMIT = 1u << 23;  // grid barrier: about 1 s of 128 ns sleeps
+// Wait bounds come from st->lim: mbarrier waits of tma_polls suspensions of
+// about 1 ms; the grid barrier polls grid_spins times, 128 ns apart, for the
+// grid's arrivals plus st->lim.phantoms (0 unless a test injects a barrier
+// that never fills).
 
 __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
     unsigned v;
@@ -178,6 +180,8 @@ __global__ void __launch_bounds__(NT, (C <= 4 ? 3 : 2)) k_fcm_run_rc(RunState* _
     const int look = nk < Sh::STAGES ? nk : Sh::STAGES;
     const int64_t tile_stride = nwarps * (int64_t)WTILE;
     const int npass = 2 + max_iter;  // INIT, max_iter iterations, the U write
+    const uint32_t wait_limit = st->lim.tma_polls, grid_spins = st->lim.grid_spins;
+    const unsigned phantoms = st->lim.phantoms;
     const uint64_t pol_x = policy_evict_last();
     const uint64_t pol_u = policy_evict_first();
 
@@ -231,7 +235,7 @@ __global__ void __launch_bounds__(NT, (C <= 4 ? 3 : 2)) k_fcm_run_rc(RunState* _
         // ---- the pass over this warp's tiles ----
         int64_t i0 = gw * (int64_t)WTILE;
         for (int k = 0; k < nk; ++k, i0 += tile_stride) {
-            const bool ok = mbar_wait_bounded(&full[cs], parity, WAIT_LIMIT);
+            const bool ok = mbar_wait_bounded(&full[cs], parity, wait_limit);
             if (__any_sync(0xffffffffu, !ok)) {
                 err = true;
                 break;
@@ -292,10 +296,10 @@ __global__ void __launch_bounds__(NT, (C <= 4 ? 3 : 2)) k_fcm_run_rc(RunState* _
         if (threadIdx.x == 0) {
             __threadfence();
             atomicAdd(gbar, 1u);
-            const unsigned target = (unsigned)(p + 1) * gridDim.x;
+            const unsigned target = (unsigned)(p + 1) * gridDim.x + phantoms;
             uint32_t spins = 0;
             while (ld_acquire_u32(gbar) < target) {
-                if (++spins > GRID_WAIT_LIMIT) {
+                if (++spins > grid_spins) {
                     s_err = 1;
                     break;
                 }
@@ -407,7 +411,7 @@ __global__ void __launch_bounds__(NT, (C <= 4 ? 3 : 2)) k_fcm_run_rc(RunState* _
         int ds = cs;
         uint32_t dp = parity;
         for (int64_t q = consumed; q < issued; ++q) {
-            mbar_wait_bounded(&full[ds], dp, WAIT_LIMIT);
+            mbar_wait_bounded(&full[ds], dp, wait_limit);
             if (++ds == Sh::STAGES) {
                 ds = 0;
                 dp ^= 1u;

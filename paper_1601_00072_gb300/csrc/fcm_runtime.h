@@ -43,6 +43,12 @@ struct fcm_ctx {
     std::string device_name;
     std::string last_error;
 
+    // bounds of the device-side waits (fcm_set_limits), copied into every
+    // run's state; alloc_fail_in > 0 makes the allocation that many calls
+    // from now fail once (fault injection for tests, 0 = off)
+    fcm::WaitLimits limits{fcm::DEFAULT_GRID_SPINS, fcm::DEFAULT_TMA_POLLS, 0u, 0u};
+    int alloc_fail_in = 0;
+
     // single-image path
     fcm::RunState* d_st = nullptr;
     fcm::RunState* h_st = nullptr;   // pinned
@@ -95,6 +101,19 @@ struct DeviceGuard {
         if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
     }
 };
+
+// Every device and pinned-host allocation of a handle goes through these, so
+// that a test can make one fail (fcm_set_limits) without a real shortage.
+cudaError_t dev_malloc_raw(fcm_ctx* h, void** p, size_t bytes);
+cudaError_t host_malloc_raw(fcm_ctx* h, void** p, size_t bytes);
+template <typename T>
+cudaError_t dev_malloc(fcm_ctx* h, T** p, size_t bytes) {
+    return dev_malloc_raw(h, reinterpret_cast<void**>(p), bytes);
+}
+template <typename T>
+cudaError_t host_malloc(fcm_ctx* h, T** p, size_t bytes) {
+    return host_malloc_raw(h, reinterpret_cast<void**>(p), bytes);
+}
 
 int ctx_fail(fcm_ctx* h, cudaError_t e, const char* what);
 int ctx_invalid(fcm_ctx* h, const char* what);

@@ -40,9 +40,8 @@
 namespace fcm {
 namespace {
 
-// Bound of every mbarrier wait: 2048 suspensions of about 1 ms (about 2 s);
-// TMA tiles land in microseconds.
-constexpr uint32_t WAIT_LIMIT = 2048;
+// Every mbarrier wait is bounded by st->lim.tma_polls suspensions of about
+// 1 ms (2048 by default, about 2 s); TMA tiles land in microseconds.
 
 __device__ __forceinline__ double warp_max_d(double v) {
 #pragma unroll
@@ -453,17 +452,18 @@ __global__ void __launch_bounds__(NT, 2) k_fcm_pass_tma(RunState* __restrict__ s
     bool tmo = false;
     int s = 0;
     uint32_t parity = 0;
+    const uint32_t wait_limit = st->lim.tma_polls;
     int64_t i0 = gw * (int64_t)WTILE;
     const int64_t tile_stride = nwarps * (int64_t)WTILE;
     for (int64_t k = 0; k < nk; ++k, i0 += tile_stride) {
-        const bool ok = mbar_wait_bounded(&full[s], parity, WAIT_LIMIT);
+        const bool ok = mbar_wait_bounded(&full[s], parity, wait_limit);
         if (__any_sync(0xffffffffu, !ok)) {
             tmo = true;
             if (lane == 0) {
                 // let the copies still in flight land before the warp leaves
                 const int64_t last = min(nk, k + (int64_t)Sh::STAGES);
                 for (int64_t kk = k; kk < last; ++kk)
-                    mbar_wait_bounded(&full[kk % Sh::STAGES], (uint32_t)((kk / Sh::STAGES) & 1), WAIT_LIMIT);
+                    mbar_wait_bounded(&full[kk % Sh::STAGES], (uint32_t)((kk / Sh::STAGES) & 1), wait_limit);
             }
             break;
         }
@@ -490,8 +490,9 @@ __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
     return v;
 }
 
-// Grid barrier spin bound: about 1 s of 128 ns sleeps.
-constexpr uint32_t GRID_WAIT_LIMIT = 1u << 23;
+// The grid barrier polls at most st->lim.grid_spins times, 128 ns apart
+// (2^23, about 1 s, by default), and waits for st->lim.phantoms arrivals
+// beyond the grid's own (0 unless a test injects a barrier that never fills).
 
 // Every warp keeps the same tiles in every pass, so the U tile a warp reads in
 // pass p + 1 is the one it wrote in pass p. Its ring therefore streams one
@@ -549,6 +550,8 @@ __global__ void __launch_bounds__(NT, 2) k_fcm_run_tma(RunState* __restrict__ st
     const int look = nk < Sh::STAGES ? nk : Sh::STAGES;
     const int64_t tile_stride = nwarps * (int64_t)WTILE;
     const int npass = 1 + max_iter;  // passes the run can take
+    const uint32_t wait_limit = st->lim.tma_polls, grid_spins = st->lim.grid_spins;
+    const unsigned phantoms = st->lim.phantoms;
     const uint64_t pol_x = policy_evict_last();
     const uint64_t pol_u = policy_evict_first();
 
@@ -603,7 +606,7 @@ __global__ void __launch_bounds__(NT, 2) k_fcm_run_tma(RunState* __restrict__ st
         // ---- the pass over this warp's tiles ----
         int64_t i0 = gw * (int64_t)WTILE;
         for (int k = 0; k < nk; ++k, i0 += tile_stride) {
-            const bool ok = mbar_wait_bounded(&full[cs], parity, WAIT_LIMIT);
+            const bool ok = mbar_wait_bounded(&full[cs], parity, wait_limit);
             if (__any_sync(0xffffffffu, !ok)) {
                 err = true;
                 break;
@@ -659,10 +662,10 @@ __global__ void __launch_bounds__(NT, 2) k_fcm_run_tma(RunState* __restrict__ st
         if (threadIdx.x == 0) {
             __threadfence();
             atomicAdd(gbar, 1u);
-            const unsigned target = (unsigned)(p + 1) * gridDim.x;
+            const unsigned target = (unsigned)(p + 1) * gridDim.x + phantoms;
             uint32_t spins = 0;
             while (ld_acquire_u32(gbar) < target) {
-                if (++spins > GRID_WAIT_LIMIT) {
+                if (++spins > grid_spins) {
                     s_err = 1;
                     break;
                 }
@@ -773,7 +776,7 @@ __global__ void __launch_bounds__(NT, 2) k_fcm_run_tma(RunState* __restrict__ st
         int ds = cs;
         uint32_t dp = parity;
         for (int64_t q = consumed; q < issued; ++q) {
-            mbar_wait_bounded(&full[ds], dp, WAIT_LIMIT);
+            mbar_wait_bounded(&full[ds], dp, wait_limit);
             if (++ds == Sh::STAGES) {
                 ds = 0;
                 dp ^= 1u;

@@ -144,6 +144,21 @@ class FCM:
     def handle(self):
         return self._h
 
+    def set_limits(self, grid_wait_spins: int = 0, tma_wait_polls: int = 0, barrier_phantoms: int = 0,
+                   fail_alloc_in: int = 0, defaults: bool = False):
+        """Bounds of the device-side waits and test-only fault injection
+        (fcm_set_limits); ``defaults=True`` restores every default."""
+        if defaults:
+            _lib.check(self._lib.fcm_set_limits(self._h, None), self._h)
+            return
+        lim = _lib.fcm_limits(grid_wait_spins, tma_wait_polls, barrier_phantoms, fail_alloc_in)
+        _lib.check(self._lib.fcm_set_limits(self._h, ctypes.byref(lim)), self._h)
+
+    def limits(self) -> dict:
+        lim = _lib.fcm_limits()
+        _lib.check(self._lib.fcm_get_limits(self._h, ctypes.byref(lim)), self._h)
+        return {k: getattr(lim, k) for k, _ in lim._fields_}
+
     def _bind_stream(self):
         import torch
         s = torch.cuda.current_stream(self.device).cuda_stream
