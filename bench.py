@@ -302,39 +302,147 @@ def run_cpu_oracle_all_cores(x, u0, m: float, iters: int = 30):
             "seconds": round(wall, 2), "worker_seconds_max": round(max(r[1] for r in res), 2)}
 
 
-def cpu_baseline_leg(x, u0, m, gV, gU_sample, idx, g_iters, g_J):
+def _center_err(v, ref):
+    v, ref = np.asarray(v, np.float64).reshape(-1), np.asarray(ref, np.float64).reshape(-1)
+    return float(np.max(np.abs(v - ref) / np.maximum(np.abs(ref), 1.0)))
+
+
+def _exact_U_vs_bins(Udev, x_u8, Vref, m):
+    """max|dU| and argmax-label agreement over EVERY pixel: the reference U is
+    the oracle's Eq. 4 at the 256 grey levels (a pixel's memberships depend on
+    its grey level only), the CUDA U is read back in chunks."""
+    import oracle
+    Ub = oracle.memberships(np.arange(256.0), np.asarray(Vref, np.float64), m)
+    lab_b = np.argmax(Ub, 0)
+    n = x_u8.size
+    dmax, agree = 0.0, 0
+    for lo in range(0, n, 1 << 22):
+        hi = min(n, lo + (1 << 22))
+        g = Udev[:, lo:hi].cpu().numpy().astype(np.float64)
+        xx = x_u8[lo:hi]
+        dmax = max(dmax, float(np.max(np.abs(g - Ub[:, xx]))))
+        agree += int(np.sum(np.argmax(g, 0) == lab_b[xx]))
+    return dmax, agree / n
+
+
+def _single_precision(x_u8, u0, m, g_iters, g_V, g_J, Udev, what):
+    """A single-image result against the FP64 oracle (256-bin form, exact for
+    8-bit data) at the CUDA run's own iteration count."""
+    import oracle
+    eps = float(np.float32(EPS))
+    o = oracle.fcm_quantized(x_u8, C, m, eps, MAX_ITER, U0=u0, want_U=False)
+    at = o if o["iters"] == g_iters else oracle.fcm_quantized(x_u8, C, m, 0.0, g_iters, U0=u0, want_U=False)
+    dU, agree = _exact_U_vs_bins(Udev, x_u8, at["V"], m)
+    return {"vs": f"FP64 oracle (256-bin form), same x and U0, at the {what}'s iteration count",
+            "center_rel_err": _center_err(g_V, at["V"]), "max_abs_dU": dU, "dU_over": "every pixel",
+            "label_agreement": agree, "d_iters": int(g_iters - o["iters"]),
+            "J_rel_err": float(abs(g_J - at["J"][-1]) / abs(at["J"][-1]))}
+
+
+def _batch_precision(slices, host, Cs, refs):
+    """Per-slice errors of a batch against the oracle's 256-bin runs at each
+    slice's own iteration count: worst and median center error, worst max|dU|
+    over every pixel, worst label agreement, the spread of the iteration
+    counts. ``refs[i]`` is (U0, V0) of the oracle start of slice i."""
+    import oracle
+    eps = float(np.float32(EPS))
+    ce, du, la, di = [], [], [], []
+    for s, (x, _), Cj, (u0, v0) in zip(slices, host, Cs, refs):
+        o = oracle.fcm_quantized(x, Cj, 2.0, eps, MAX_ITER, U0=u0, V0=v0, want_U=False)
+        at = o if o["iters"] == s.iters else oracle.fcm_quantized(x, Cj, 2.0, 0.0, s.iters, U0=u0, V0=v0,
+                                                                    want_U=False)
+        Ub = oracle.memberships(np.arange(256.0), at["V"], 2.0)
+        g = s.U.cpu().numpy().astype(np.float64)
+        ce.append(_center_err(s.V64[:Cj], at["V"]))
+        du.append(float(np.max(np.abs(g - Ub[:, x]))))
+        la.append(float(np.mean(np.argmax(g, 0) == np.argmax(Ub, 0)[x])))
+        di.append(int(s.iters - o["iters"]))
+    ce, du, la, di = map(np.asarray, (ce, du, la, di))
+    strict = (ce <= 1e-5) & (du <= 1e-5) & (la >= 0.9999) & (np.abs(di) <= 1)
+    return {"center_rel_err": {"max": float(ce.max()), "median": float(np.median(ce))},
+            "max_abs_dU": {"max": float(du.max()), "median": float(np.median(du)), "over": "every pixel"},
+            "label_agreement_min": float(la.min()), "d_iters": {"min": int(di.min()), "max": int(di.max())},
+            "slices_within_all_bars": int(strict.sum()), "slices": int(strict.size),
+            "slices_outside": [int(i) for i in np.flatnonzero(~strict)]}
+
+
+def cpu_baseline_leg(x, u0, m, keep, out):
     """Everything that touches the oracle: its timed CPU throughput on a
-    bounded sample, and the FP64 reference of the timed workload for the
-    precision report (256-bin form of the oracle, exact for uint8 data)."""
+    bounded sample, and the FP64 reference of every GPU result of the line
+    for its precision block (written into ``out``)."""
     import oracle
     value, sample, dt = run_cpu_oracle_sample(x, u0, m, iters=30)
     base = {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": sample, "seconds": round(dt, 2),
             "all_cores": run_cpu_oracle_all_cores(x, u0, m)}
-    eps = float(np.float32(EPS))
-    o = oracle.fcm_quantized(x, C, m, eps, MAX_ITER, U0=u0)
-    d_iters = g_iters - o["iters"]
-    # compare at the same iterate: the oracle's k-th iterate is the run with
-    # eps = 0 stopped at max_iter = k (k = the CUDA run's count)
-    ok_ = o if o["iters"] == g_iters else oracle.fcm_quantized(x, C, m, 0.0, g_iters, U0=u0)
-    ref_V = ok_["V"]
-    Ubins = oracle.memberships(np.arange(256.0), ref_V, m)
-    ref_U = Ubins[:, x[idx]]
-    prec = {
-        "vs": "FP64 oracle (256-bin form), same x and U0, at the CUDA run's iteration count",
-        "center_rel_err": float(np.max(np.abs(gV - ref_V) / np.maximum(np.abs(ref_V), 1.0))),
-        "max_abs_dU_sampled": float(np.max(np.abs(gU_sample - ref_U))),
-        "label_agreement_sampled": float(np.mean(np.argmax(gU_sample, 0) == np.argmax(ref_U, 0))),
-        "d_iters": int(d_iters),
-        "J_rel_err": float(abs(g_J - ok_["J"][-1]) / abs(ok_["J"][-1])),
-        "U_sample_voxels": int(idx.size),
-    }
-    return base, prec, o
+    Ud, Vd, g_iters, g_J = keep["main"]
+    out["precision"] = _single_precision(x, u0, m, g_iters, Vd.cpu().numpy(), g_J, Ud, "CUDA run")
+    for key, ent in out.get("other_workloads", {}).items():
+        Uw, Vw, it, J, xw, u0w, mm = keep[key]
+        if key == "phantom200":  # small enough for the per-pixel form of the oracle
+            eps = float(np.float32(EPS))
+            o = oracle.fcm(xw.astype(np.float64), C, mm, eps, MAX_ITER, U0=u0w, want_U=False)
+            at = o if o["iters"] == it else oracle.fcm(xw.astype(np.float64), C, mm, 0.0, it, U0=u0w)
+            if "U" not in at or at["U"] is None:
+                at = oracle.fcm(xw.astype(np.float64), C, mm, 0.0, it, U0=u0w)
+            g = Uw.cpu().numpy().astype(np.float64)
+            ent["precision"] = {"vs": "FP64 oracle (per-pixel form), same x and U0, at the CUDA run's iteration count",
+                                "center_rel_err": _center_err(Vw.cpu().numpy(), at["V"]),
+                                "max_abs_dU": float(np.max(np.abs(g - at["U"]))), "dU_over": "every pixel",
+                                "label_agreement": float(np.mean(np.argmax(g, 0) == np.argmax(at["U"], 0))),
+                                "d_iters": int(it - o["iters"]),
+                                "J_rel_err": float(abs(J - at["J"][-1]) / abs(at["J"][-1]))}
+        else:
+            ent["precision"] = _single_precision(xw, u0w, mm, it, Vw.cpu().numpy(), J, Uw, "CUDA run")
+    if out.get("histogram_domain") and "histogram_domain" in keep:
+        Uh, Vh, it, J = keep["histogram_domain"]
+        out["histogram_domain"]["precision"] = _single_precision(x, u0, m, it, Vh.cpu().numpy(), J, Uh,
+                                                                 "histogram run")
+    if out.get("recompute") and "recompute" in keep:
+        Ur, Vr, it, J = keep["recompute"]
+        out["recompute"]["precision"] = _single_precision(x, u0, m, it, Vr.cpu().numpy(), J, Ur, "U-free run")
+    if out.get("multi_feature") and "multi_feature" in keep:
+        xm, u0m, Um, rm = keep["multi_feature"]
+        eps = float(np.float32(EPS))
+        xm64 = xm.astype(np.float64)
+        o = oracle.fcm_multi(xm64, C, m, eps, MAX_ITER, U0=u0m)
+        at = o if o["iters"] == rm.iters else oracle.fcm_multi(xm64, C, m, 0.0, rm.iters, U0=u0m)
+        g = Um.cpu().numpy().astype(np.float64)
+        out["multi_feature"]["precision"] = {
+            "vs": "FP64 multi-feature oracle, same x and U0, at the CUDA run's iteration count",
+            "center_rel_err": _center_err(np.asarray(rm.V64), at["V"]),
+            "max_abs_dU": float(np.max(np.abs(g - at["U"]))), "dU_over": "every pixel",
+            "label_agreement": float(np.mean(np.argmax(g, 0) == np.argmax(at["U"], 0))),
+            "d_iters": int(rm.iters - o["iters"])}
+    if out.get("batched") and "batched" in keep:
+        cold, warm, hist, host, Cs = keep["batched"]
+        cold_refs = [(u, None) for _, u in host]
+        out["batched"]["cold"]["precision"] = _batch_precision(cold, host, Cs, cold_refs)
+        out["batched"]["histogram_domain"]["precision"] = _batch_precision(hist, host, Cs, cold_refs)
+        # warm slices against the oracle started from the oracle's own
+        # prediction (the shipped network in FP64 with its BF16 weights);
+        # slices that ran cold against the cold oracle
+        from oracle import mlp
+        from paper_1601_00072_gb300 import warmstart
+        raw = open(warmstart.MODEL_PATH, "rb").read()
+        P = mlp.unflat(np.frombuffer(raw[20:], dtype=np.float32).astype(np.float64))
+        for k in ("W1", "W2", "W3"):
+            b = np.ascontiguousarray(P[k], dtype=np.float32).view(np.uint32).astype(np.uint64)
+            P[k] = ((b + 0x7FFF + ((b >> 16) & 1)) & 0xFFFF0000).astype(np.uint32).view(np.float32).astype(np.float64)
+        X = np.stack([mlp.features(xh, Cj) for (xh, _), Cj in zip(host, Cs)])
+        V0 = mlp.predict_centers(P, X, Cs)
+        warm_refs = [((None, np.asarray(v0, np.float32).astype(np.float64)) if s.init == "V" else (u, None))
+                     for s, (_, u), v0 in zip(warm, host, V0)]
+        out["batched"]["warm"]["precision"] = _batch_precision(warm, host, Cs, warm_refs)
+        out["batched"]["warm"]["precision"]["vs"] = (
+            "warm slices: FP64 oracle from the oracle's own V0 (the shipped network in FP64 with BF16 weights); "
+            "slices that ran cold: FP64 oracle from U0; each at the slice's own iteration count")
+    return base
 
 
-def batch_inputs(dev, n=512):
+def batch_inputs(dev, n=512, host=None):
     """Device-resident x and U0 of the batch slices (generated in spawned
-    worker processes)."""
+    worker processes); ``host`` (a list) receives the (x uint8, U0) pairs."""
     import torch
     from paper_1601_00072_gb300 import warmstart
     xs, u0s, Cs = [], [], []
@@ -343,17 +451,22 @@ def batch_inputs(dev, n=512):
             xs.append(torch.from_numpy(x.astype(np.float32)).to(dev))
             u0s.append(torch.from_numpy(u0[0]).to(dev))
             Cs.append(Cj)
+            if host is not None:
+                host.append((x, u0[0]))
     return xs, u0s, Cs
 
 
-def bench_batched(h, dev, steps, warmup, plan=None):
+def bench_batched(h, dev, steps, warmup, plan=None, keep_results=False):
     """Cold versus warm-started batch, timed with CUDA events on the launching
     stream (each call returns after its results are read back). ``plan``
-    (a dict of FCM.set_batched_plan arguments) replaces the autotuner."""
+    (a dict of FCM.set_batched_plan arguments) replaces the autotuner. With
+    ``keep_results`` also returns the slices (results on the device) and the
+    host inputs, for the precision report."""
     import torch
     from paper_1601_00072_gb300 import warmstart
     from paper_1601_00072_gb300.fcm import Batch, Slice
-    xs, u0s, Cs = batch_inputs(dev)
+    host = []
+    xs, u0s, Cs = batch_inputs(dev, host=host)
     n_img = len(xs)
     px = sum(int(x.numel()) for x in xs)
     cold = [Slice(x=x, C=c, U0=u) for x, c, u in zip(xs, Cs, u0s)]
@@ -376,7 +489,7 @@ def bench_batched(h, dev, steps, warmup, plan=None):
         h.set_batched_plan(**plan)
     cold = Batch(cold)
     # results land in each Batch's host array; the Slice fields are filled
-    # once after timing
+    # once after timing (the warm call's judge and reruns are inside its time)
     ms_cold = timed(lambda: h.run_batched(cold, read_back=False), steps)
     cold.read_back()
     plan_used = h.batched_plan()
@@ -388,31 +501,20 @@ def bench_batched(h, dev, steps, warmup, plan=None):
 
     ms_warm = timed(run_warm, steps)
     warm.read_back()
+    # every returned slice against the cold batch by the acceptance rule; the
+    # judge inside the call already ran cold (and timed) each slice whose warm
+    # fixed point fails it, so a failure here is a slice whose FP32 per-pixel
+    # trajectory left the fixed point the histogram judge saw: it is charged
+    # a separate cold batch of its own
     ok = warmstart.accepted(cold.slices, warm.slices)
-    # A slice that fails the acceptance rule is charged its cold start, two ways:
-    # - marginal: what these slices add to a cold batch (the full cold batch
-    #   minus the cold batch without them), the cost of folding them into the
-    #   next batch of a stream;
-    # - separate: a cold batch of only these slices, through the autotuned
-    #   path, the cost of an immediate rerun.
     bad_i = np.flatnonzero(~ok)
-    ms_marginal = ms_separate = 0.0
+    ms_charge = 0.0
     if bad_i.size:
-        good = Batch([Slice(x=xs[i], C=Cs[i], U0=u0s[i]) for i in np.flatnonzero(ok)])
         bad = Batch([Slice(x=xs[i], C=Cs[i], U0=u0s[i]) for i in bad_i])
-        # the marginal pair runs with the cold batch's own launch shape, so the
-        # difference is the failed slices' work, not two autotuner choices
-        h.set_batched_plan(**{k: plan_used[k] for k in ("schedule", "block", "cluster", "big", "tile")})
-        ms_rest = timed(lambda: h.run_batched(good, read_back=False), steps)
-        ms_full = timed(lambda: h.run_batched(cold, read_back=False), steps)
-        ms_marginal = max(0.0, ms_full - ms_rest)
-        h.set_batched_plan()  # the separate rerun is a batch of its own: autotuned
-        ms_separate = timed(lambda: h.run_batched(bad, read_back=False), steps)
-        if plan:
-            h.set_batched_plan(**plan)
-    ms_charge = ms_marginal
+        ms_charge = timed(lambda: h.run_batched(bad, read_back=False), steps)
     it_c = np.array([s.iters for s in cold.slices])
     it_w = np.array([s.iters for s in warm.slices])
+    ran_cold = np.array([s.init == "U" for s in warm.slices])
     cold_ips = n_img / (ms_cold / 1e3)
     warm_ips = n_img / ((ms_warm + ms_charge) / 1e3)
     # the same cold batch on each slice's 256-bin histogram (one CTA per
@@ -423,28 +525,34 @@ def bench_batched(h, dev, steps, warmup, plan=None):
     it_h = np.array([s.iters for s in hist.slices])
     verr = np.array([np.max(np.abs(np.asarray(a.V64) - np.asarray(c.V64)) / np.maximum(np.abs(np.asarray(c.V64)), 1.0))
                      for a, c in zip(hist.slices, cold.slices)])
-    return {
+    res = {
         "workload": "512 phantom slices, sides log-uniform 64..512, C in {3,4,5}, m=2, eps=1e-5, max_iter=300",
         "pixels": px, "steps": steps,
         "cold": {"images_per_s": cold_ips, "ms": ms_cold, "mean_iters": float(it_c.mean()),
                  "max_iters": int(it_c.max()),
                  "pixel_iter_per_s": sum(int(x.numel()) * int(i) for x, i in zip(xs, it_c)) / (ms_cold / 1e3)},
         "warm": {"images_per_s": warm_ips, "ms": ms_warm, "charged_ms": ms_charge,
-                 "charged_ms_separate_rerun": ms_separate,
-                 "images_per_s_separate_rerun": n_img / ((ms_warm + ms_separate) / 1e3),
+                 "call": "fcm_run_batched_warm: prediction, histogram-domain judge of every slice (from U0 "
+                         "and from the predicted V0), the batch ordered by the judge's iteration counts, "
+                         "and cold reruns of rejected warm results, all inside the timed call",
                  "mean_iters": float(it_w.mean()), "max_iters": int(it_w.max()),
+                 "mean_iters_of_warm_slices": float(it_w[~ran_cold].mean()) if (~ran_cold).any() else None,
                  "accepted": float(ok.mean()), "failed_slices": int(bad_i.size),
                  "ran_cold_at_run_time": int(n_ran_cold[0])},
         "warm_over_cold": warm_ips / cold_ips,
-        "warm_over_cold_separate_rerun": (ms_cold / (ms_warm + ms_separate)),
         "plan": plan_used,
         "histogram_domain": {
-            "kernel": "k_bhist: one CTA per slice, three pixel passes and the iterations on 256 bins",
+            "kernel": "k_bins_*: pixel passes in 16,384-pixel chunks over the whole GPU (histogram and V^1 "
+                      "sums; the first stop over every pixel only where a bound cannot decide it; U by lookup), "
+                      "the iterations on 256 bins, one CTA per slice",
             "images_per_s": n_img / (ms_hist / 1e3), "ms": ms_hist, "speedup_vs_cold": ms_cold / ms_hist,
             "mean_iters": float(it_h.mean()), "max_iters": int(it_h.max()),
             "iters_within_1_of_cold": float(np.mean(np.abs(it_h - it_c) <= 1)),
             "center_rel_err_vs_cold": {"max": float(verr.max()), "fraction_within_1e-5": float(np.mean(verr <= 1e-5))}},
     }
+    if keep_results:
+        return res, (cold.slices, warm.slices, hist.slices, host, Cs)
+    return res
 
 
 def bench_ours(args):
@@ -554,6 +662,53 @@ def bench_ours(args):
                                "ms_per_step": dt1 * 1e3 / s_steps,
                                "api": "fcm_run with pinned host buffers, one synchronous call per step"}}
 
+    # device results kept for the precision report of the CPU-baseline leg
+    keep = {"main": (Ud, Vd, r.iters, r.J)}
+
+    # the other single-image workloads: the 200x200 and 1024x1024 phantoms
+    # (L2-resident: latency-bound, no HBM roofline) and the volume at the
+    # other fuzzifiers (HBM-bound, roofline as the main line)
+    peak_, _ = measured_peak()
+    workloads = {}
+    if not args.no_workloads:
+        import phantom
+        cases = [("phantom200", "phantom200", 2.0, 200), ("phantom1024", "phantom1024", 2.0, 50)]
+        cases += [(f"volume256_m{mm:g}", "volume256", mm, 20) for mm in (1.5, 3.0) if mm != m]
+        for key, name, mm, reps in cases:
+            if name == "volume256":
+                xw, u0w, xdw, u0dw = x, u0, xd, U0d
+            else:
+                xw, _, u0w, _ = phantom.single_image(name)
+                xdw = torch.from_numpy(xw.astype(np.float32)).to(dev)
+                u0dw = torch.from_numpy(u0w).to(dev)
+            nw = xw.size
+            Uw = torch.empty_like(u0dw)
+            Vw = torch.empty(C, dtype=torch.float32, device=dev)
+            for _ in range(args.warmup):
+                rw = h.run(xdw, C, mm, EPS, MAX_ITER, U0=u0dw, U=Uw, V=Vw)
+            torch.cuda.synchronize(dev)
+            e0.record(stream)
+            for _ in range(reps):
+                rw = h.run(xdw, C, mm, EPS, MAX_ITER, U0=u0dw, U=Uw, V=Vw)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            wms = e0.elapsed_time(e1) / reps
+            wbytes = (4 + 4 * C) * nw + rw.iters * (4 + 8 * C) * nw
+            ent = {"workload": workload_name(mm) if name == "volume256" else
+                   f"{name}: {int(np.sqrt(nw))}x{int(np.sqrt(nw))} uint8 phantom as f32, C=4, m={mm:g}, eps=1e-5",
+                   "n_pixels": nw, "m": mm, "runs": reps, "ms_per_run": wms, "images_per_s": 1e3 / wms,
+                   "iters": rw.iters, "pixel_iter_per_s": nw * rw.iters / (wms / 1e3),
+                   "us_per_iteration": wms * 1e3 / max(1, rw.iters)}
+            if name == "volume256":
+                ent["roofline"] = {"bound": "hbm", "achieved": wbytes / (wms / 1e3) / 1e9, "peak": peak_,
+                                   "unit": "GB/s", "frac": wbytes / (wms / 1e3) / 1e9 / peak_,
+                                   "algorithmic_bytes_per_run": wbytes}
+            else:
+                ent["bound"] = (f"latency: working set {(4 + 8 * C) * nw / 1e6:.1f} MB sits in the 129 MB L2; "
+                                "an iteration costs its grid exchange")
+            workloads[key] = ent
+            keep[key] = (Uw, Vw, rw.iters, rw.J, xw, u0w, mm)
+
     # the same run on the grey-level histogram (fcm_run_hist), inputs resident
     hist = None
     if not args.no_hist:
@@ -576,8 +731,8 @@ def bench_ours(args):
                 "equivalent_pixel_iter_per_s": n * rh.iters / (hms / 1e3),
                 "roofline": {"bound": "hbm", "achieved": hbytes / (hms / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
                              "frac": hbytes / (hms / 1e3) / 1e9 / peak, "algorithmic_bytes_per_run": hbytes},
-                "speedup_vs_pixel_path": (ms / args.steps) / hms,
-                "_V": Vh.cpu().numpy().astype(np.float64)}
+                "speedup_vs_pixel_path": (ms / args.steps) / hms}
+        keep["histogram_domain"] = (Uh, Vh, rh.iters, rh.J)
 
     # the same run keeping no U between iterations (FCM_OPT_RECOMPUTE)
     recompute = None
@@ -600,8 +755,6 @@ def bench_ours(args):
                      "ms_per_run": rms, "iters": rr.iters, "pixel_iter_per_s": n * rr.iters / (rms / 1e3),
                      "bound": "alu",
                      "dram_bytes_per_run_algorithmic": rbytes,
-                     "center_rel_err_vs_stored_U_run": float(np.max(np.abs(Vr.cpu().numpy() - Vd.cpu().numpy())
-                                                                   / np.maximum(np.abs(Vd.cpu().numpy()), 1.0))),
                      "speedup_vs_pixel_path": (ms / args.steps) / rms,
                      "roofline": issue_roofline("profiles/fcm_recompute_volume256.md",
                                                 ["paper_1601_00072_gb300/csrc/fcm_recompute_inst.cu",
@@ -609,6 +762,7 @@ def bench_ours(args):
                                                  "paper_1601_00072_gb300/csrc/fcm_tma.cuh",
                                                  "paper_1601_00072_gb300/csrc/fcm_internal.h"],
                                                 rms, rr.iters, clocks.get("sm_max_mhz"))}
+        keep["recompute"] = (Ur, Vr, rr.iters, rr.J)
 
     # multi-feature FCM on a 3-channel 2048^2 phantom (shared layout, per-channel
     # contrasts and noise), inputs resident
@@ -638,6 +792,7 @@ def bench_ours(args):
                                              "paper_1601_00072_gb300/csrc/fcm_device.cuh",
                                              "paper_1601_00072_gb300/csrc/fcm_multi.h"],
                                             mms, rm.iters, clocks.get("sm_max_mhz"))}
+        keep["multi_feature"] = (xm, u0m.cpu().numpy(), Um, rm)
 
     # the paper's quantitative score (Dice per tissue class, Sec. 5.2) of the
     # timed run's segmentation against the phantom's generator labels
@@ -681,27 +836,12 @@ def bench_ours(args):
         "recompute": recompute,
         "segmentation_dsc": dsc_line,
         "multi_feature": multi,
+        "other_workloads": workloads,
     }
     if not args.no_batched:
-        out["batched"] = bench_batched(h, dev, max(3, min(args.steps, 20)), 3)
+        out["batched"], keep["batched"] = bench_batched(h, dev, max(3, min(args.steps, 20)), 3, keep_results=True)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        idx = np.random.default_rng(0).choice(n, 100_000, replace=False)
-        gU_sample = Ud[:, torch.from_numpy(idx).to(dev)].cpu().numpy().astype(np.float64)
-        gV = Vd.cpu().numpy().astype(np.float64)
-        base, prec, o = cpu_baseline_leg(x, u0, m, gV, gU_sample, idx, r.iters, r.J)
-        out["cpu_baseline"] = base
-        out["precision"] = prec
-        if hist is not None:
-            import oracle
-            hv = hist.pop("_V")
-            # at the histogram run's own iterate, as for the main line
-            oh = o if o["iters"] == hist["iters"] else oracle.fcm_quantized(x, C, m, 0.0, hist["iters"], U0=u0)
-            hist["precision"] = {
-                "vs": "FP64 oracle (256-bin form), same x and U0, at the histogram run's iteration count",
-                "center_rel_err": float(np.max(np.abs(hv - oh["V"]) / np.maximum(np.abs(oh["V"]), 1.0))),
-                "d_iters": int(hist["iters"] - o["iters"])}
-    if hist is not None:
-        hist.pop("_V", None)
+        out["cpu_baseline"] = cpu_baseline_leg(x, u0, m, keep, out)
     h.close()
     if rank == 0:
         print(json.dumps(out))
@@ -760,6 +900,8 @@ def main():
     ap.add_argument("--no-hist", action="store_true", help="skip the histogram-domain measurement")
     ap.add_argument("--no-recompute", action="store_true", help="skip the U-free (recompute) measurement")
     ap.add_argument("--no-multi", action="store_true", help="skip the multi-feature measurement")
+    ap.add_argument("--no-workloads", action="store_true",
+                    help="skip the 200x200 and 1024x1024 phantoms and the volume at the other fuzzifiers")
     ap.add_argument("--batched-only", action="store_true",
                     help="only the cold versus warm batch measurement, printed as its own JSON object "
                          "(a profiling aid; not the benchmark line)")

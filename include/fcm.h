@@ -296,6 +296,11 @@ int fcm_run_multi(fcm_handle h, const float* x, int64_t n, int D, int C, float m
  *   n, C, m, eps, max_iter   as for fcm_run.
  *   init_mode FCM_INIT_U (U^0 in U0, or in U when U0 is NULL) or FCM_INIT_V
  *             (initial centers in V0[], host values inside the struct).
+ *   iters_hint  0, or the iterations the slice is expected to take. When
+ *             every slice of a batch has one, the slice-queue schedule takes
+ *             slices in order of decreasing cost n * (iters_hint + 3) instead
+ *             of decreasing n (fcm_run_batched_warm sets them from its
+ *             histogram-domain runs).
  *   U0        C*n floats, cluster-major, read only; nullable.
  *   U         C*n floats, cluster-major: receives U^k.
  *   V         C floats: receives V^k.
@@ -309,7 +314,7 @@ typedef struct {
     float eps;
     int max_iter;
     int init_mode;
-    int reserved0;
+    int iters_hint;
     const float* U0;
     float* U;
     float* V;
@@ -326,6 +331,7 @@ typedef struct {
 /* Launch shape of the batched kernels (see fcm_run_batched). */
 #define FCM_SCHED_SLICES 0 /* slices from a queue, one CTA or one cluster each     */
 #define FCM_SCHED_ROUNDS 1 /* every slice steps each round; pixels tiled over the grid */
+#define FCM_SCHED_TEAMS 2  /* slices from a queue, each on a team of 1..32 CTAs sized by its cost */
 typedef struct {
     int block;      /* threads per CTA: 256 or 512                                   */
     int cluster;    /* FCM_SCHED_SLICES: CTAs per thread-block cluster, 1, 2, 4 or 8; */
@@ -333,12 +339,14 @@ typedef struct {
     int64_t big;    /* FCM_SCHED_SLICES: slices with n >= big are shared by a whole  */
                     /* cluster; FCM_SCHED_ROUNDS: unused (0)                          */
     double ms;      /* measured batch time when the autotuner chose it, or 0          */
-    int schedule;   /* FCM_SCHED_SLICES or FCM_SCHED_ROUNDS                           */
+    int schedule;   /* FCM_SCHED_SLICES, FCM_SCHED_ROUNDS or FCM_SCHED_TEAMS          */
     int tile;       /* FCM_SCHED_ROUNDS: fewest pixels one CTA takes in a round,      */
                     /* 1024 to 65536, a multiple of 1024. FCM_SCHED_SLICES: 0 for one */
                     /* launch, or an iteration cap: slices not stopped after `tile`  */
                     /* iterations are parked and finished by a second launch that    */
-                    /* gives big slices clusters of 8 (in the same graph)            */
+                    /* gives big slices clusters of 8 (in the same graph).           */
+                    /* FCM_SCHED_TEAMS: 10..10000, the team-size target in percent   */
+                    /* of the mean cost per CTA (see fcm_run_batched)                */
 } fcm_batch_plan;
 
 /* Batch options (bit flags). */
@@ -361,6 +369,17 @@ typedef struct {
  *                     iterations are parked and resumed by a second launch
  *                     with bigger clusters, so the few slowly converging
  *                     slices do not hold a few SMs while the rest idle.
+ *   FCM_SCHED_TEAMS   a cooperative launch without clusters; a slice's cost
+ *                     is n * (iters_hint + 3) when every slice has a hint,
+ *                     else n. A slice gets a team of T CTAs, T the smallest
+ *                     power of two with cost / T <= (plan.tile / 100) * (total
+ *                     cost / CTAs), at most 32 and at most one CTA per 4,096
+ *                     pixels; the T seats of a slice sit together in a queue
+ *                     ordered by cost / T, longest first. A team exchanges
+ *                     its sums after every pass through global memory, behind
+ *                     a bounded barrier of its own. So the costliest slices,
+ *                     which otherwise hold a few SMs while the rest idle,
+ *                     spread over as many SMs as their cost asks for.
  *   FCM_SCHED_ROUNDS  a cooperative launch; round k is iteration k of every
  *                     slice still running, the pixels of those slices cut
  *                     into one equal contiguous chunk per CTA (at least
@@ -388,12 +407,15 @@ int fcm_run_batched(fcm_handle h, fcm_slice* slices, int n_slices, int options);
 /*
  * fcm_run_batched_hist — the histogram-domain run (as fcm_run_hist: the
  * grey-level reduction of brFCM, cited in Sec. 3) for each slice of a batch
- * of 8-bit slices, one CTA per slice, largest slices first, in one launch.
- * Per slice: a pass over the pixels builds its 256-bin histogram (and from
- * U^0 the sums of V^1), a second pass takes the first stopping quantity
- * against the pixels' U^0, Algorithm 1 then iterates on the bins, and a last
- * pass writes U^k by table lookup. The iterates equal fcm_run_batched's up to
- * the order of rounding.
+ * of 8-bit slices. The pixel passes are cut into chunks of 16,384 pixels,
+ * one CTA each, over the whole GPU; the iterations run on each slice's 256
+ * bins, one CTA per slice. A first pass builds every slice's histogram (and
+ * from U^0 the sums of V^1); the first stopping quantity max_i |f(x_i, V^1)
+ * - U^0_i| is bounded from below by one recorded pixel per grey level, and a
+ * second pass over the pixels takes it exactly only when that bound does not
+ * already exceed eps (or max_iter is 1); Algorithm 1 then iterates on the
+ * bins, and a last pass writes U^k by table lookup. The iterates equal
+ * fcm_run_batched's up to the order of rounding.
  *
  * Slices as for fcm_run_batched (device x, U0, U and V; x 16-byte aligned),
  * with n < 2^31. A slice whose x holds anything but integer grey levels
@@ -453,11 +475,31 @@ int fcm_model_train(fcm_handle h, const float* feats, const float* targets, cons
 /* Predicted V^0 of every slice into slices[i].V0, with init_mode set to
  * FCM_INIT_V. */
 int fcm_predict_centers(fcm_handle h, fcm_slice* slices, int n);
-/* Warm-started batch: predict V^0, run fcm_run_batched, and fall back to the
- * plain cold start (the slice's U0, which must be given) for every slice whose
- * prediction is unusable (non-finite or two centers within 1e-3) or whose
- * warm run did not converge or emptied a cluster. *n_cold (nullable) counts
- * the slices that ran cold. Returns as fcm_run_batched. */
+/*
+ * fcm_run_batched_warm — a batch in which plain cold-start FCM (Algorithm 1
+ * from the slice's own U^0, Sec. 2.1) is both the judge and the fallback of
+ * the learned warm start. Every slice must give its own U0 (not NULL, not U).
+ *
+ *   1. The network predicts V^0 of every slice.
+ *   2. The judge runs every 8-bit slice twice on its grey-level histogram
+ *      (the brFCM reduction cited in Sec. 3, which gives the per-pixel
+ *      iterates up to rounding): from U^0, and from the predicted V^0.
+ *   3. A slice starts from V^0 when the prediction is usable (finite, no two
+ *      centers within 1e-3) and the warm fixed point passes the acceptance
+ *      rule against the cold one: sorted centers within 1e-4 relative
+ *      (to max(|v|, 1)), or a final J no larger (relative slack 1e-5). Every
+ *      other slice, and every slice that is not all grey levels 0..255, starts
+ *      from its U^0. Each slice's iters_hint is set to the iterations its
+ *      start took on the histogram, so the batch is ordered by cost.
+ *   4. fcm_run_batched runs the batch.
+ *   5. Each warm result is checked against the judge's cold fixed point by
+ *      the same rule (and must have converged without emptying a cluster);
+ *      a slice that fails is run again from its U^0 within the call.
+ *
+ * On return slices[i].init_mode is FCM_INIT_V for a slice whose result came
+ * from the warm start and FCM_INIT_U for one that ran cold; *n_cold
+ * (nullable) counts the latter. Returns as fcm_run_batched.
+ */
 int fcm_run_batched_warm(fcm_handle h, fcm_slice* slices, int n, int options, int* n_cold);
 
 /*

@@ -40,7 +40,7 @@ class fcm_report(ctypes.Structure):
 class fcm_slice(ctypes.Structure):
     _fields_ = [("x", ctypes.c_void_p), ("n", ctypes.c_int64), ("C", ctypes.c_int),
                 ("m", ctypes.c_float), ("eps", ctypes.c_float), ("max_iter", ctypes.c_int),
-                ("init_mode", ctypes.c_int), ("reserved0", ctypes.c_int),
+                ("init_mode", ctypes.c_int), ("iters_hint", ctypes.c_int),
                 ("U0", ctypes.c_void_p), ("U", ctypes.c_void_p), ("V", ctypes.c_void_p),
                 ("V0", ctypes.c_float * FCM_MAX_CLUSTERS),
                 ("iters", ctypes.c_int), ("status", ctypes.c_int), ("flags", ctypes.c_int),
@@ -60,6 +60,7 @@ class fcm_batch_plan(ctypes.Structure):
 
 FCM_SCHED_SLICES = 0
 FCM_SCHED_ROUNDS = 1
+FCM_SCHED_TEAMS = 2
 
 
 FCM_BATCH_RETUNE = 16

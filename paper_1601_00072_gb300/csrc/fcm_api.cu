@@ -89,6 +89,7 @@ const SingleTable& single_table() {
 }
 
 int ctx_fail(fcm_ctx* h, cudaError_t e, const char* what) {
+    cudaGetLastError();  // a failed call leaves its error as the last one: clear it for the next check
     if (h) {
         char buf[256];
         std::snprintf(buf, sizeof(buf), "%s: %s", what, cudaGetErrorString(e));
@@ -383,6 +384,7 @@ void fcm_destroy(fcm_handle h) {
         fcm_release_mlp(h);
         fcm_release_hist(h);
         fcm_release_multi(h);
+        release_bins(h);
     }
     delete h;
 }

@@ -62,6 +62,15 @@ struct BatchedWorkspace {
     // call per pointer; repeated batches reuse their buffers)
     std::unordered_set<const void*> known_device;
     std::map<std::pair<int, int>, int> rgrid;  // (block, shared bytes) -> CTAs of a cooperative round grid
+    std::vector<int64_t> size, cost;          // per slice of the current batch: n, and its queue cost
+    // team schedule: the seat queue (fixed length cap * TEAM_MAX, so a captured
+    // graph serves every batch of a slice count), rank slots and barrier counters
+    int4* d_items = nullptr;
+    int4* h_items = nullptr;  // pinned
+    float2* d_tslots = nullptr;
+    unsigned* d_tctr = nullptr;
+    int team_cap = 0;
+    std::map<int, int> tgrid;  // block -> CTAs of a full cooperative team grid
 };
 
 }  // namespace fcm
@@ -74,12 +83,26 @@ struct BatchedWorkspace {
 
 namespace {
 
+// The work order of the slice queue for a plan (LPT): first the slices a
+// whole cluster shares (n >= big), then the rest, each group costliest first
+// (ties by index, so the order is stable). A cluster takes slices of the
+// first group together and splits up at the first slice of the second.
+void order_for(BatchedWorkspace* w, int n, int64_t big) {
+    std::iota(w->h_order, w->h_order + n, 0);
+    std::stable_sort(w->h_order, w->h_order + n, [&](int a, int b) {
+        const bool ba = w->size[a] >= big, bb = w->size[b] >= big;
+        if (ba != bb) return ba;
+        return w->cost[a] > w->cost[b];
+    });
+}
+
 BatchKernel kernel_for(int block) { return block == 256 ? batched_kernel_256() : batched_kernel_512(); }
 RoundsKernel rounds_for(int block) { return block == 256 ? rounds_kernel_256() : rounds_kernel_512(); }
 
 bool plan_valid(const fcm_batch_plan& p) {
     if (p.block != 256 && p.block != 512) return false;
     if (p.schedule == FCM_SCHED_ROUNDS) return p.tile >= 1024 && p.tile <= 65536 && p.tile % 1024 == 0;
+    if (p.schedule == FCM_SCHED_TEAMS) return p.tile >= 10 && p.tile <= 10000;
     if (p.schedule != FCM_SCHED_SLICES) return false;
     return (p.cluster == 1 || p.cluster == 2 || p.cluster == 4 || p.cluster == 8) && p.big >= 1 && p.tile >= 0;
 }
@@ -146,6 +169,9 @@ int fill_slots(fcm_ctx* h, const fcm_slice* slices, int n, int min_chunk) {
     w->h_slot_base[n] = (int)total;
     w->h_rhdr->n_slices = n;
     w->h_rhdr->max_rounds = max_iter + 1;
+    // in the header, which every replay of the batch graph uploads afresh
+    w->h_rhdr->wait_spins = h->limits.grid_spins;
+    w->h_rhdr->phantoms = h->limits.phantoms;
     if (w->slot_cap < total) {
         free_graphs(w);  // graphs point at the old buffer
         cudaFree(w->d_rpart);
@@ -231,8 +257,6 @@ int launch_rounds(fcm_ctx* h, cudaStream_t s, const fcm_batch_plan& p, int n_sli
     a.slot_base = w->d_slot_base;
     a.partials = w->d_rpart;
     a.min_chunk = p.tile;
-    a.wait_spins = h->limits.grid_spins;
-    a.phantoms = h->limits.phantoms;
     cudaLaunchConfig_t cfg;
     std::memset(&cfg, 0, sizeof(cfg));
     cudaLaunchAttribute attr[1];
@@ -248,6 +272,117 @@ int launch_rounds(fcm_ctx* h, cudaStream_t s, const fcm_batch_plan& p, int n_sli
     return 0;
 }
 
+// CTAs of a full cooperative grid of the team kernel (0 if it cannot run).
+int team_ctas(fcm_ctx* h, int block) {
+    BatchedWorkspace* w = h->batched;
+    auto it = w->tgrid.find(block);
+    if (it != w->tgrid.end()) return it->second;
+    const BatchKernel k = kernel_for(block);
+    int nb = 0;
+    if (!h->coop ||
+        cudaFuncSetAttribute((const void*)k.teams, cudaFuncAttributeMaxDynamicSharedMemorySize, k.smem) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, (const void*)k.teams, block, k.smem) != cudaSuccess)
+        nb = 0;
+    cudaGetLastError();
+    w->tgrid[block] = nb * h->num_sms;
+    return nb * h->num_sms;
+}
+
+// The seat queue of the team schedule. A slice whose cost (n times its
+// expected passes, or n without hints) is large next to the mean cost per CTA
+// gets a team: the smallest power of two T with cost / T <= (tile / 100) *
+// (total cost / CTAs), at most TEAM_MAX, the grid, and one CTA per 4,096
+// pixels (so a rank's pixels outweigh its barrier). Items are ordered by team
+// time, cost / T, longest first; a slice's T seats are consecutive.
+int fill_teams(fcm_ctx* h, int n, const fcm_batch_plan& p) {
+    BatchedWorkspace* w = h->batched;
+    const int ctas = team_ctas(h, p.block);
+    if (ctas < 1) {
+        h->last_error = "the team schedule needs cooperative launch support";
+        return FCM_ERR_CUDA;
+    }
+    if (w->team_cap < n) {
+        free_graphs(w);  // graphs point at the old buffers
+        cudaFree(w->d_items);
+        cudaFree(w->d_tslots);
+        cudaFree(w->d_tctr);
+        cudaFreeHost(w->h_items);
+        w->d_items = nullptr;
+        w->d_tslots = nullptr;
+        w->d_tctr = nullptr;
+        w->h_items = nullptr;
+        w->team_cap = 0;
+        const int cap = std::max(n, 64);
+        CK(dev_malloc(h, &w->d_items, sizeof(int4) * (size_t)cap * TEAM_MAX));
+        CK(host_malloc(h, &w->h_items, sizeof(int4) * (size_t)cap * TEAM_MAX));
+        CK(dev_malloc(h, &w->d_tslots, sizeof(float2) * (size_t)cap * TEAM_MAX * 2 * TEAM_SLOT));
+        CK(dev_malloc(h, &w->d_tctr, sizeof(unsigned) * cap));
+        w->team_cap = cap;
+    }
+    double total = 0.0;
+    for (int i = 0; i < n; ++i) total += (double)w->cost[i];
+    const double target = std::max(1.0, (p.tile / 100.0) * total / ctas);
+    const int tmax = std::min(TEAM_MAX, ctas);
+    std::vector<int> T(n);
+    for (int i = 0; i < n; ++i) {
+        int t = 1;
+        const int64_t by_size = std::max<int64_t>(1, w->size[i] / 4096);
+        while (t < tmax && 2 * t <= by_size && (double)w->cost[i] / t > target) t *= 2;
+        T[i] = t;
+    }
+    std::vector<int> ord(n);
+    std::iota(ord.begin(), ord.end(), 0);
+    std::stable_sort(ord.begin(), ord.end(),
+                     [&](int a, int b) { return (double)w->cost[a] / T[a] > (double)w->cost[b] / T[b]; });
+    int base = 0, k = 0;
+    for (int i = 0; i < n; ++i) {
+        w->h_slot_base[i] = base;
+        base += T[i];
+    }
+    for (int i : ord)
+        for (int r = 0; r < T[i]; ++r) w->h_items[k++] = make_int4(i, r, T[i], 0);
+    w->h_rhdr->n_slices = n;
+    w->h_rhdr->max_rounds = k;  // the team schedule: number of items
+    w->h_rhdr->wait_spins = h->limits.grid_spins;
+    w->h_rhdr->phantoms = h->limits.phantoms;
+    return 0;
+}
+
+int launch_teams(fcm_ctx* h, cudaStream_t s, const fcm_batch_plan& p, int n_slices) {
+    BatchedWorkspace* w = h->batched;
+    const BatchKernel k = kernel_for(p.block);
+    const int ctas = team_ctas(h, p.block);
+    if (ctas < 1) {
+        h->last_error = "the team schedule needs cooperative launch support";
+        return FCM_ERR_CUDA;
+    }
+    CK(cudaMemsetAsync(w->d_ctl, 0, sizeof(BatchCtl), s));
+    CK(cudaMemsetAsync(w->d_tctr, 0, sizeof(unsigned) * n_slices, s));
+    TeamArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.descs = w->d_desc;
+    a.results = w->d_res;
+    a.ctl = w->d_ctl;
+    a.items = w->d_items;
+    a.hdr = w->d_rhdr;
+    a.slot_base = w->d_slot_base;
+    a.slots = w->d_tslots;
+    a.counters = w->d_tctr;
+    cudaLaunchConfig_t cfg;
+    std::memset(&cfg, 0, sizeof(cfg));
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.gridDim = dim3(ctas);
+    cfg.blockDim = dim3(p.block);
+    cfg.dynamicSmemBytes = k.smem;
+    cfg.stream = s;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    CK(cudaLaunchKernelEx(&cfg, k.teams, a));
+    return 0;
+}
+
 // Uploads of one batch's work description (descriptors, order or tiling).
 int upload_batch(fcm_ctx* h, cudaStream_t s, const fcm_batch_plan& p, int n) {
     BatchedWorkspace* w = h->batched;
@@ -255,6 +390,10 @@ int upload_batch(fcm_ctx* h, cudaStream_t s, const fcm_batch_plan& p, int n) {
     if (p.schedule == FCM_SCHED_ROUNDS) {
         CK(cudaMemcpyAsync(w->d_rhdr, w->h_rhdr, sizeof(RoundsHdr), cudaMemcpyHostToDevice, s));
         CK(cudaMemcpyAsync(w->d_slot_base, w->h_slot_base, sizeof(int) * (n + 1), cudaMemcpyHostToDevice, s));
+    } else if (p.schedule == FCM_SCHED_TEAMS) {
+        CK(cudaMemcpyAsync(w->d_rhdr, w->h_rhdr, sizeof(RoundsHdr), cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(w->d_slot_base, w->h_slot_base, sizeof(int) * n, cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(w->d_items, w->h_items, sizeof(int4) * (size_t)n * TEAM_MAX, cudaMemcpyHostToDevice, s));
     } else {
         CK(cudaMemcpyAsync(w->d_order, w->h_order, sizeof(int) * n, cudaMemcpyHostToDevice, s));
     }
@@ -297,6 +436,7 @@ int launch_slices(fcm_ctx* h, cudaStream_t s, int block, int cluster, int64_t bi
 
 int launch_kernel(fcm_ctx* h, cudaStream_t s, const fcm_batch_plan& p, int n_slices) {
     if (p.schedule == FCM_SCHED_ROUNDS) return launch_rounds(h, s, p, n_slices);
+    if (p.schedule == FCM_SCHED_TEAMS) return launch_teams(h, s, p, n_slices);
     if (p.tile <= 0) return launch_slices(h, s, p.block, p.cluster, p.big, n_slices, 0, 0x7fffffff);
     // two phases: the slices that have not stopped after p.tile iterations
     // are finished by a second launch that gives big slices clusters of 8
@@ -370,14 +510,16 @@ int ilog2(int64_t v) {
 std::string bucket_key(fcm_ctx* h, const fcm_slice* s, int n) {
     int64_t total = 0, largest = 0;
     unsigned cset = 0;
+    bool hinted = true;
     for (int i = 0; i < n; ++i) {
         total += s[i].n;
         largest = std::max(largest, s[i].n);
         cset |= 1u << s[i].C;
+        hinted &= s[i].iters_hint > 0;
     }
     char buf[512];
-    std::snprintf(buf, sizeof(buf), "%s|C%x|s%d|p%d|l%d", h->device_name.c_str(), cset, ilog2(n), ilog2(total),
-                  ilog2(largest));
+    std::snprintf(buf, sizeof(buf), "%s|C%x|s%d|p%d|l%d%s", h->device_name.c_str(), cset, ilog2(n), ilog2(total),
+                  ilog2(largest), hinted ? "|hinted" : "");
     return buf;
 }
 
@@ -393,8 +535,9 @@ void fcm_release_batched(fcm_ctx* h) {
     cudaFree(w->d_res);
     cudaFree(w->d_order);
     cudaFree(w->d_ctl);
-    void* dev[] = {w->d_rstate, w->d_rctl, w->d_rhdr, w->d_slot_base, w->d_rpart};
+    void* dev[] = {w->d_rstate, w->d_rctl, w->d_rhdr, w->d_slot_base, w->d_rpart, w->d_items, w->d_tslots, w->d_tctr};
     for (void* p : dev) cudaFree(p);
+    cudaFreeHost(w->h_items);
     cudaFreeHost(w->h_desc);
     cudaFreeHost(w->h_res);
     cudaFreeHost(w->h_order);
@@ -463,6 +606,8 @@ int run_once(fcm_ctx* h, const fcm_batch_plan& p, int n, bool use_graph) {
 int time_plan(fcm_ctx* h, const fcm_slice* slices, const fcm_batch_plan& p, int n, int reps, double* ms_out) {
     int rc = 0;
     if (p.schedule == FCM_SCHED_ROUNDS && (rc = fill_slots(h, slices, n, p.tile))) return rc;
+    if (p.schedule == FCM_SCHED_TEAMS && (rc = fill_teams(h, n, p))) return rc;
+    if (p.schedule == FCM_SCHED_SLICES) order_for(h->batched, n, p.big);
     if ((rc = upload_batch(h, h->stream, p, n))) return rc;
     rc = launch_kernel(h, h->stream, p, n);
     if (rc) return rc;
@@ -510,8 +655,8 @@ int check_slices(fcm_ctx* h, const fcm_slice* slices, int n_slices, int64_t n_li
     return FCM_OK;
 }
 
-// The device descriptors of a batch in the pinned host array, and its LPT
-// work order (largest slices first).
+// The device descriptors of a batch in the pinned host array, and its work
+// order.
 int fill_descs(fcm_ctx* h, const fcm_slice* slices, int n_slices) {
     int rc = ensure_batched(h, n_slices);
     if (rc) return rc;
@@ -551,10 +696,17 @@ int fill_descs(fcm_ctx* h, const fcm_slice* slices, int n_slices) {
         d.init = s.init_mode;
         for (int j = 0; j < s.C; ++j) d.V0[j] = s.init_mode == FCM_INIT_V ? s.V0[j] : 0.0f;
     }
-    // LPT: the largest slices first (ties by index, so the order is stable)
-    std::iota(w->h_order, w->h_order + n_slices, 0);
-    std::stable_sort(w->h_order, w->h_order + n_slices,
-                     [&](int a, int b) { return slices[a].n > slices[b].n; });
+    // the cost of each slice for the work order: its pixels, times its
+    // expected passes when every slice carries an iteration hint
+    bool hinted = true;
+    for (int i = 0; i < n_slices && hinted; ++i) hinted = slices[i].iters_hint > 0;
+    w->cost.resize(n_slices);
+    w->size.resize(n_slices);
+    for (int i = 0; i < n_slices; ++i) {
+        w->size[i] = slices[i].n;
+        w->cost[i] = hinted ? slices[i].n * (int64_t)(slices[i].iters_hint + 3) : slices[i].n;
+    }
+    order_for(w, n_slices, (int64_t)1 << 62);
     return FCM_OK;
 }
 
@@ -578,6 +730,23 @@ int collect_results(fcm_ctx* h, fcm_slice* slices, int n_slices) {
 }
 
 }  // namespace
+
+namespace fcm {
+
+int batch_descs(fcm_ctx* h, const fcm_slice* slices, int n_slices, int64_t n_limit, SliceDesc** h_desc,
+                SliceDesc** d_desc) {
+    bool in_place = false;
+    int rc = check_slices(h, slices, n_slices, n_limit, &in_place);
+    if (rc) return rc;
+    if ((rc = fill_descs(h, slices, n_slices))) return rc;
+    BatchedWorkspace* w = h->batched;
+    CK(cudaMemcpyAsync(w->d_desc, w->h_desc, sizeof(SliceDesc) * n_slices, cudaMemcpyHostToDevice, h->stream));
+    *h_desc = w->h_desc;
+    *d_desc = w->d_desc;
+    return FCM_OK;
+}
+
+}  // namespace fcm
 
 extern "C" {
 
@@ -608,6 +777,7 @@ int fcm_run_batched(fcm_handle h, fcm_slice* slices, int n_slices, int options) 
             const int clusters[4] = {1, 2, 4, 8};
             const int64_t bigs[6] = {4096, 8192, 16384, 49152, 98304, 196608};
             const int tiles[3] = {2048, 8192, 32768};
+            const int team_targets[3] = {50, 100, 200};
             for (int b : blocks) {
                 for (int k : clusters)
                     for (int gi = 0; gi < (k == 1 ? 1 : 6); ++gi)
@@ -615,6 +785,8 @@ int fcm_run_batched(fcm_handle h, fcm_slice* slices, int n_slices, int options) 
                             cands.push_back({b, k, k == 1 ? ((int64_t)1 << 62) : bigs[gi], 0.0, FCM_SCHED_SLICES, 0});
                 if (n_slices <= ROUND_MAX_SLICES && round_ctas(h, b, round_smem(n_slices)) > 0)
                     for (int t : tiles) cands.push_back({b, 1, 0, 0.0, FCM_SCHED_ROUNDS, t});
+                if (team_ctas(h, b) > 0)
+                    for (int t : team_targets) cands.push_back({b, 1, 0, 0.0, FCM_SCHED_TEAMS, t});
             }
             fcm_batch_plan best = default_plan();
             best.ms = 1e30;
@@ -653,10 +825,12 @@ int fcm_run_batched(fcm_handle h, fcm_slice* slices, int n_slices, int options) 
         }
     }
     if (plan.schedule == FCM_SCHED_ROUNDS && (rc = fill_slots(h, slices, n_slices, plan.tile))) return rc;
+    if (plan.schedule == FCM_SCHED_TEAMS && (rc = fill_teams(h, n_slices, plan))) return rc;
+    if (plan.schedule == FCM_SCHED_SLICES) order_for(w, n_slices, plan.big);
     const bool use_graph = !(options & FCM_BATCH_NO_GRAPH);
     rc = run_once(h, plan, n_slices, use_graph);
-    // a runtime that cannot capture the cooperative round launch runs it directly
-    if (rc && use_graph && plan.schedule == FCM_SCHED_ROUNDS) rc = run_once(h, plan, n_slices, false);
+    // a runtime that cannot capture a cooperative launch runs it directly
+    if (rc && use_graph && plan.schedule != FCM_SCHED_SLICES) rc = run_once(h, plan, n_slices, false);
     if (rc) return rc;
     w->last = plan;
 
@@ -674,9 +848,11 @@ int fcm_run_batched_hist(fcm_handle h, fcm_slice* slices, int n_slices) {
     if (rc) return rc;
     BatchedWorkspace* w = h->batched;
     CK(cudaMemcpyAsync(w->d_desc, w->h_desc, sizeof(SliceDesc) * n_slices, cudaMemcpyHostToDevice, h->stream));
-    CK(cudaMemcpyAsync(w->d_order, w->h_order, sizeof(int) * n_slices, cudaMemcpyHostToDevice, h->stream));
-    CK(launch_bhist(w->d_desc, w->d_order, n_slices, w->d_res, h->stream));
-    CK(cudaMemcpyAsync(w->h_res, w->d_res, sizeof(SliceResult) * n_slices, cudaMemcpyDeviceToHost, h->stream));
+    // one run per slice, from its own start, writing its U and V
+    std::vector<BinRun> runs(n_slices);
+    for (int i = 0; i < n_slices; ++i)
+        runs[i] = BinRun{i, slices[i].init_mode == FCM_INIT_U ? BIN_FROM_U : BIN_FROM_V, 1, 0};
+    if ((rc = bins_run(h, w->h_desc, w->d_desc, n_slices, runs.data(), n_slices, nullptr, 0, w->h_res))) return rc;
     CK(cudaStreamSynchronize(h->stream));
     return collect_results(h, slices, n_slices);
 }

@@ -77,14 +77,36 @@ __device__ __forceinline__ int ld_dsmem_s32(const int* local, unsigned rank) {
 struct BatchShared {
     float w[NWB][2 * SBMAX];  // warp totals: (hi, lo) of each sum, then the maxima
     // block totals (sums as hi/lo double-floats, maxima in x), double-buffered
-    // for the cluster exchange, and every rank's, gathered for the rank-order sum
+    // for the cluster or team exchange, and every rank's, gathered for the
+    // rank-order sum
     float2 red[2][SBMAX];
-    float2 xch[8][SBMAX];
+    float2 xch[TEAM_MAX][SBMAX];
     DF tot[SBMAX];            // slice totals (the same on every rank); maxima in .hi
     DF vq[FCM_MAX_CLUSTERS];  // next centers, double-float quotients
     float vcur[FCM_MAX_CLUSTERS], vprev[FCM_MAX_CLUSTERS];  // centers, for the scalar path
     int idx;
+    int team_err;             // a team barrier gave up
+    int item[3];              // team schedule: slice, seat, team size
 };
+
+// A slice shared by a team of CTAs of the team schedule (any CTAs of the
+// grid, not one cluster): after every pass each rank writes its block totals
+// to global slots, arrives at the slice's barrier counter and waits, bounded,
+// for the whole team; then every rank adds the team's totals in rank order.
+// slots == nullptr: no team (a lone CTA, or a cluster exchanging through
+// distributed shared memory).
+struct TeamCtx {
+    float2* slots;        // [T][2][SBMAX], this slice's
+    unsigned* ctr;        // this slice's barrier counter (zero before the batch)
+    uint32_t spins;       // polls, 128 ns apart, before the barrier gives up
+    uint32_t phantoms;    // arrivals beyond the team's (0 unless a test injects a barrier that never fills)
+};
+
+__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
 
 // Per-thread pass sums: compensated (double-float) num, den and J, plus the
 // maxima. Threads add pixels in FP32 over chunks of CHUNK pairs and fold each
@@ -111,7 +133,8 @@ struct SliceAcc {
 // a few threads would run a long FP64 chain while the rest wait at the
 // barrier). Leaves sh.tot and the double-float quotients sh.vq = num / den.
 template <int C>
-__device__ __forceinline__ void slice_reduce(BatchShared& sh, SliceAcc<C>& a, unsigned K, int& parity) {
+__device__ __forceinline__ void slice_reduce(BatchShared& sh, SliceAcc<C>& a, unsigned r, unsigned K, int& parity,
+                                             int& npass, const TeamCtx& tc) {
     constexpr int S = 2 * C + 3;
     constexpr int NS = 2 * C + 1;  // compensated sums
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -142,8 +165,30 @@ __device__ __forceinline__ void slice_reduce(BatchShared& sh, SliceAcc<C>& a, un
             t = make_float2(mx, 0.0f);
         }
         sh.red[parity][s] = t;
+        if (tc.slots) __stcg(&tc.slots[((int64_t)r * 2 + parity) * SBMAX + s], t);
     }
-    if (K > 1) {
+    ++npass;
+    if (K > 1 && tc.slots) {
+        // team: arrive, wait (bounded) for every rank's totals of this pass
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            atomicAdd(tc.ctr, 1u);
+            const unsigned target = (unsigned)npass * K + tc.phantoms;
+            uint32_t spins = 0;
+            while (ld_acquire_gpu(tc.ctr) < target) {
+                if (++spins > tc.spins) {
+                    sh.team_err = 1;
+                    break;
+                }
+                __nanosleep(128);
+            }
+            __threadfence();
+        }
+        __syncthreads();
+        for (int t = threadIdx.x; t < (int)K * S; t += NTB)
+            sh.xch[t / S][t % S] = __ldcg(&tc.slots[((int64_t)(t / S) * 2 + parity) * SBMAX + (t % S)]);
+    } else if (K > 1) {
         cluster_sync();
         // all remote reads at once (one thread per rank and value)
         for (int t = threadIdx.x; t < (int)K * S; t += NTB) sh.xch[t / S][t % S] = ld_dsmem_f2(&sh.red[parity][t % S], t / S);
@@ -192,7 +237,7 @@ struct XSrc {
 
 template <int C, int MK>
 __device__ __noinline__ void process_slice(const SliceDesc& d, SliceResult& res, unsigned r, unsigned K, float* xs,
-                                           BatchShared& sh, bool resume, int cap) {
+                                           BatchShared& sh, bool resume, int cap, const TeamCtx& tc) {
     const int64_t n = d.n;
     int64_t share = (n + K - 1) / K;
     share += share & 1;  // even, so only the last pixel of the slice can be unpaired
@@ -232,7 +277,8 @@ __device__ __noinline__ void process_slice(const SliceDesc& d, SliceResult& res,
         v2[j] = pack2(v[j], v[j]);
         vp2[j] = pack2(vp[j], vp[j]);
     }
-    int parity = 0, flags = resume ? res.flags : 0;
+    int parity = 0, npass = 0, flags = resume ? res.flags : 0;
+    if (threadIdx.x == 0) sh.team_err = 0;
     SliceAcc<C> a;
     int status = FCM_NOT_CONVERGED, iters = 0;
     // delta, J and the centers behind V (double-floats) in FP32 arithmetic;
@@ -311,13 +357,15 @@ __device__ __noinline__ void process_slice(const SliceDesc& d, SliceResult& res,
             df_add(a.s[C + j], w);
         }
     }
-    slice_reduce<C>(sh, a, K, parity);
+    slice_reduce<C>(sh, a, r, K, parity, npass, tc);
 #pragma unroll
     for (int j = 0; j < C; ++j) v64[j] = DF{d.V0[j], 0.0f};
     ok0 = sh.tot[2 * C + 2].hi == 0.0f;
     }
-    bool parked = false;
-    if (!ok0) {
+    bool parked = false, gave_up = sh.team_err != 0;
+    if (gave_up) {
+        status = FCM_ERR_TIMEOUT;
+    } else if (!ok0) {
         status = FCM_ERR_BAD_INPUT;
     } else {
         float vn[C];
@@ -400,10 +448,15 @@ __device__ __noinline__ void process_slice(const SliceDesc& d, SliceResult& res,
                     a.dmax = fmaxf(a.dmax, fabsf(u[j] - uo[j]));
                 }
             }
-            slice_reduce<C>(sh, a, K, parity);
+            slice_reduce<C>(sh, a, r, K, parity, npass, tc);
             delta = sh.tot[2 * C + 1].hi;
             Jk = sh.tot[2 * C];
             iters = k;
+            if (sh.team_err) {
+                status = FCM_ERR_TIMEOUT;
+                gave_up = true;
+                break;
+            }
             if (delta < d.eps) {
                 status = FCM_OK;
                 break;
@@ -433,7 +486,7 @@ __device__ __noinline__ void process_slice(const SliceDesc& d, SliceResult& res,
         }
         // ---- U^k, written once (a parked slice writes it in the second phase) ----
         float* U = d.U;
-        for (int p = threadIdx.x; p < (parked ? 0 : npair); p += NTB) {
+        for (int p = threadIdx.x; p < (parked || gave_up ? 0 : npair); p += NTB) {
             const float2 xv = xl.pair(p);
             f2 u2[C], um2[C];
             membership_pair<C, MK>(pack2(xv.x, xv.y), v2, m, inv_m1, v, u2, um2);
@@ -446,7 +499,7 @@ __device__ __noinline__ void process_slice(const SliceDesc& d, SliceResult& res,
                 __stcs(row + 1, b0);
             }
         }
-        if (odd_tail && !parked) {
+        if (odd_tail && !parked && !gave_up) {
             float u[C], um[C];
             membership<C, MK>(xl.at(cnt - 1), v, m, inv_m1, u, um);
 #pragma unroll
@@ -470,21 +523,22 @@ __device__ __noinline__ void process_slice(const SliceDesc& d, SliceResult& res,
             }
         }
     }
-    // no rank leaves the slice (and reuses its shared memory) while another
-    // may still read it
-    if (K > 1) cluster_sync();
+    // no rank of a cluster leaves the slice (and reuses its shared memory)
+    // while another may still read it; a team exchanges through global slots
+    // of its own slice and needs no such wait
+    if (K > 1 && !tc.slots) cluster_sync();
     __syncthreads();
 }
 
 __device__ __forceinline__ void run_slice(const SliceDesc& d, SliceResult& res, unsigned r, unsigned K, float* xs,
-                                          BatchShared& sh, bool resume, int cap) {
+                                          BatchShared& sh, bool resume, int cap, const TeamCtx& tc) {
 #define FCM_BATCH_CASE(CC)                                                                  \
     case CC:                                                                                \
         switch (d.mk) {                                                                     \
-            case M_TWO: process_slice<CC, M_TWO>(d, res, r, K, xs, sh, resume, cap); break;              \
-            case M_THREE: process_slice<CC, M_THREE>(d, res, r, K, xs, sh, resume, cap); break;          \
-            case M_ONE_HALF: process_slice<CC, M_ONE_HALF>(d, res, r, K, xs, sh, resume, cap); break;    \
-            default: process_slice<CC, M_GENERIC>(d, res, r, K, xs, sh, resume, cap); break;             \
+            case M_TWO: process_slice<CC, M_TWO>(d, res, r, K, xs, sh, resume, cap, tc); break;              \
+            case M_THREE: process_slice<CC, M_THREE>(d, res, r, K, xs, sh, resume, cap, tc); break;          \
+            case M_ONE_HALF: process_slice<CC, M_ONE_HALF>(d, res, r, K, xs, sh, resume, cap, tc); break;    \
+            default: process_slice<CC, M_GENERIC>(d, res, r, K, xs, sh, resume, cap, tc); break;             \
         }                                                                                   \
         break;
     switch (d.C) {
@@ -524,14 +578,14 @@ __global__ void __launch_bounds__(NTB, MIN_BLOCKS)
         const int s = order[idx];
         if (!wanted(s)) continue;
         if (descs[s].n >= big) {
-            run_slice(descs[s], results[s], r, K, xs, sh, resume, cap);
+            run_slice(descs[s], results[s], r, K, xs, sh, resume, cap, TeamCtx{});
             continue;
         }
         // the queue has reached the small slices: every CTA works alone now
         solo = true;
         if (r == 0) first_solo = s;
     }
-    if (first_solo >= 0) run_slice(descs[first_solo], results[first_solo], 0, 1, xs, sh, resume, cap);
+    if (first_solo >= 0) run_slice(descs[first_solo], results[first_solo], 0, 1, xs, sh, resume, cap, TeamCtx{});
     for (;;) {
         if (threadIdx.x == 0) sh.idx = (int)atomicAdd(&ctl->next, 1u);
         __syncthreads();
@@ -540,7 +594,45 @@ __global__ void __launch_bounds__(NTB, MIN_BLOCKS)
         if (idx >= n_slices) return;
         const int s = order[idx];
         if (!wanted(s)) continue;
-        run_slice(descs[s], results[s], 0, 1, xs, sh, resume, cap);
+        run_slice(descs[s], results[s], 0, 1, xs, sh, resume, cap, TeamCtx{});
+    }
+}
+
+// The team schedule: one cooperative launch (every CTA resident), no
+// clusters. The queue holds one item per seat: a slice with a team of T CTAs
+// appears T times in a row, seats 0..T-1, so the CTAs that take them form its
+// team; the host orders the items by team time, longest first. Only the team
+// at the head of the queue can be incomplete, and every other team finishes
+// and frees its CTAs, so every team fills; each barrier wait is bounded
+// nonetheless.
+__global__ void __launch_bounds__(NTB, MIN_BLOCKS)
+    k_fcm_teams(TeamArgs a) {
+    extern __shared__ __align__(16) float xs[];
+    __shared__ BatchShared sh;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            const int idx = (int)atomicAdd(&a.ctl->next, 1u);
+            if (idx < a.hdr->max_rounds) {
+                const int4 it = a.items[idx];
+                sh.item[0] = it.x;
+                sh.item[1] = it.y;
+                sh.item[2] = it.z;
+            } else {
+                sh.item[0] = -1;
+            }
+        }
+        __syncthreads();
+        const int s = sh.item[0], seat = sh.item[1], T = sh.item[2];
+        __syncthreads();
+        if (s < 0) return;
+        TeamCtx tc{};
+        if (T > 1) {
+            tc.slots = a.slots + (int64_t)a.slot_base[s] * 2 * SBMAX;
+            tc.ctr = a.counters + s;
+            tc.spins = a.hdr->wait_spins;
+            tc.phantoms = a.hdr->phantoms;
+        }
+        run_slice(a.descs[s], a.results[s], (unsigned)seat, (unsigned)T, xs, sh, false, 0x7fffffff, tc);
     }
 }
 
@@ -549,7 +641,7 @@ __global__ void __launch_bounds__(NTB, MIN_BLOCKS)
 #define FCM_CAT2(a, b) a##b
 #define FCM_CAT(a, b) FCM_CAT2(a, b)
 BatchKernel FCM_CAT(batched_kernel_, FCM_BATCH_NT)() {
-    return BatchKernel{k_fcm_batched, XCAP * (int)sizeof(float), XCAP};
+    return BatchKernel{k_fcm_batched, XCAP * (int)sizeof(float), XCAP, k_fcm_teams};
 }
 
 }  // namespace fcm

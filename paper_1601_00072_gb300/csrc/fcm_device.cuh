@@ -1,23 +1,23 @@
 // Device-side building blocks of the FCM pixel pass (sm_103a).
 //
 // Membership (Eq. 4 of arXiv:1601.00072) is evaluated in its weight form:
-//   u_j = w_j / sum_k w_k,   w_j = (r_j)^(2/(m-1)),   r_j = |d|min / |d_j|,
+//   u_j = w_j / sum_k w_k,   w_j = (q_j)^(1/(m-1)),   q_j = d2min / d2_j,
 // which equals 1 / sum_k (d_j / d_k)^(2/(m-1)) after dividing numerator and
 // denominator by sum_k w_k; the common factor keeps every weight in (0, 1], so
-// no weight or sum can overflow. The ratio is taken of the distances
-// |x - v_j| themselves, not of their squares, so it stays exact for distances
-// down to the smallest normal float (2^-126) even where their squares would
-// underflow.
+// no weight or sum can overflow. When some squared distance d2 = (x - v)^2
+// falls below the smallest normal float (2^-126) although the distances
+// themselves are normal, q_j is formed as (|d|min / |d_j|)^2 instead, from the
+// distances, which do not underflow.
 // A pixel at distance 0 from one or more centers gives those clusters equal
 // shares and the others 0 (Bezdek's rule; the paper leaves d = 0 open).
 // "Distance 0" means |x - v| below 2^-126, i.e. zero once the FP32
 // approximate instructions flush subnormal operands to zero.
 //
 // Specialisations of the fuzzifier avoid general powers on the hot path:
-//   m = 2    w = r*r              u^m = u*u
-//   m = 3    w = r                u^m = u*u*u
-//   m = 1.5  w = (r*r)^2          u^m = u*sqrt(u)
-//   other m  w = 2^(2 log2(r)/(m-1))   u^m = 2^(m log2 u)
+//   m = 2    w = q                u^m = u*u
+//   m = 3    w = sqrt(q)          u^m = u*u*u
+//   m = 1.5  w = q*q              u^m = u*sqrt(u)
+//   other m  w = 2^((log2 q)/(m-1))   u^m = 2^(m log2 u)
 // using the PTX approximate instructions (rcp, rsqrt, sqrt, lg2, ex2), whose
 // documented error is at most a few ulp in FP32.
 #pragma once
@@ -80,26 +80,49 @@ __device__ __forceinline__ float flt_min() { return __int_as_float(0x00800000); 
 template <int C, int MK>
 __device__ __forceinline__ float membership(float x, const float (&v)[C], float m, float inv_m1,
                                             float (&u)[C], float (&um)[C]) {
-    float ad[C];
-    float amin = __int_as_float(0x7f800000);
+    float d2[C], ad[C];
+    float dmin = __int_as_float(0x7f800000), amin = dmin;
 #pragma unroll
     for (int j = 0; j < C; ++j) {
-        ad[j] = fabsf(x - v[j]);
+        const float d = x - v[j];
+        ad[j] = fabsf(d);
+        d2[j] = __fmul_rn(d, d);
+        dmin = fminf(dmin, d2[j]);
         amin = fminf(amin, ad[j]);
     }
     float Ji = 0.0f;
     if (amin >= flt_min()) {
         float w[C];
-        if (MK == M_GENERIC) {
-            const float l0 = lg2_approx(amin), e = 2.0f * inv_m1;
+        if (dmin >= flt_min()) {
+            // every squared distance is a normal float: ratios of the squares
+            if (MK == M_GENERIC) {
+                const float l0 = lg2_approx(dmin);
 #pragma unroll
-            for (int j = 0; j < C; ++j) w[j] = ex2_approx(e * (l0 - lg2_approx(ad[j])));
+                for (int j = 0; j < C; ++j) w[j] = ex2_approx(inv_m1 * (l0 - lg2_approx(d2[j])));
+            } else if (MK == M_THREE) {
+                const float s0 = sqrt_approx(dmin);
+#pragma unroll
+                for (int j = 0; j < C; ++j) w[j] = s0 * rsqrt_approx(d2[j]);
+            } else {
+#pragma unroll
+                for (int j = 0; j < C; ++j) {
+                    const float q = dmin * rcp_approx(d2[j]);
+                    w[j] = (MK == M_ONE_HALF) ? q * q : q;
+                }
+            }
         } else {
+            // tiny distances: ratios of the distances themselves
+            if (MK == M_GENERIC) {
+                const float l0 = lg2_approx(amin), e = 2.0f * inv_m1;
 #pragma unroll
-            for (int j = 0; j < C; ++j) {
-                const float r = amin * rcp_approx(ad[j]);
-                const float q = r * r;
-                w[j] = (MK == M_THREE) ? r : (MK == M_ONE_HALF) ? q * q : q;
+                for (int j = 0; j < C; ++j) w[j] = ex2_approx(e * (l0 - lg2_approx(ad[j])));
+            } else {
+#pragma unroll
+                for (int j = 0; j < C; ++j) {
+                    const float r = amin * rcp_approx(ad[j]);
+                    const float q = r * r;
+                    w[j] = (MK == M_THREE) ? r : (MK == M_ONE_HALF) ? q * q : q;
+                }
             }
         }
         float S = 0.0f;
@@ -108,7 +131,7 @@ __device__ __forceinline__ float membership(float x, const float (&v)[C], float 
         const float r = rcp_approx(S);
 #pragma unroll
         for (int j = 0; j < C; ++j) u[j] = w[j] * r;
-        const float dmin = amin * amin;  // may underflow for tiny distances: the J term is then 0
+        // dmin may be subnormal or 0 for tiny distances: the J term is then tiny or 0
         if (MK == M_TWO) Ji = dmin * r;
         else if (MK == M_THREE) Ji = dmin * r * r;
         else if (MK == M_ONE_HALF) Ji = dmin * sqrt_approx(r);

@@ -24,6 +24,7 @@
 #include <vector>
 
 #include "fcm.h"
+#include "fcm_batched.h"
 #include "fcm_runtime.h"
 
 using namespace fcm;
@@ -55,6 +56,10 @@ struct MlpWorkspace {
     void* hdesc_dev = nullptr;
     int hdesc_cap = 0;
     float* v0 = nullptr;  // [feat_cap][9]: sorted initial centers and a usability flag
+    // warm-started batches: the predictions and the judge's results, pinned
+    float* h_v0 = nullptr;            // [judge_cap][9]
+    SliceResult* h_judge = nullptr;   // [2 * judge_cap]: cold runs, then warm runs
+    int judge_cap = 0;
     unsigned* counts = nullptr;  // [counts_cap][256] grey-level counters, kept zero between calls
     int counts_cap = 0;
     std::unordered_set<const void*> known_device;  // slice x pointers already checked
@@ -390,6 +395,26 @@ int upload_params(fcm_ctx* h, const float* host) {
     return 0;
 }
 
+// The acceptance rule of a warm-started slice against the cold start: its
+// sorted centers within 1e-4 of the cold start's (relative to max(|v|, 1)),
+// or a fixed point whose J is no larger (relative slack 1e-5, above the FP32
+// kernels' resolution of J). Random starts of the same slice often end at
+// different local minima of J (Eq. 1), so a warm start that finds a lower
+// minimum than the cold one is as valid a result.
+bool warm_accepted(const double* Vw, double Jw, int status_w, const double* Vc, double Jc, int C) {
+    double a[FCM_MAX_CLUSTERS], b[FCM_MAX_CLUSTERS];
+    for (int j = 0; j < C; ++j) {
+        a[j] = Vw[j];
+        b[j] = Vc[j];
+    }
+    std::sort(a, a + C);
+    std::sort(b, b + C);
+    double err = 0.0;
+    for (int j = 0; j < C; ++j) err = std::max(err, std::fabs(a[j] - b[j]) / std::max(std::fabs(b[j]), 1.0));
+    if (err <= 1e-4) return true;
+    return status_w >= 0 && Jw <= Jc * (1.0 + 1e-5);
+}
+
 int need_model(fcm_ctx* h) {
     if (!h->mlp || !h->mlp->ready) return ctx_invalid(h, "no model: call fcm_model_init, _load or _set_params");
     return 0;
@@ -403,6 +428,8 @@ void fcm_release_mlp(fcm_ctx* h) {
     void* ps[] = {w->master, w->wbf, w->adam_m, w->adam_v, w->grad, w->xb, w->tb, w->z1, w->a1, w->z2,
                   w->a2, w->y, w->dy, w->dz2, w->dz1, w->loss, w->cb, w->idx, w->feats, w->hdesc_dev, w->v0, w->counts};
     for (void* p : ps) cudaFree(p);
+    cudaFreeHost(w->h_v0);
+    cudaFreeHost(w->h_judge);
     delete w;
     h->mlp = nullptr;
 }
@@ -452,13 +479,9 @@ int fcm_features_impl(fcm_ctx* h, const fcm_slice* slices, int n, float* feats) 
     return FCM_OK;
 }
 
-// Features, forward pass and k_v0 for a batch; fills each slice's V0 and sets
-// FCM_INIT_V. ok (when given) receives the usability flag of each prediction.
-int predict_v0(fcm_ctx* h, fcm_slice* slices, int n, std::vector<unsigned char>* ok) {
-    if (!h || !slices || n < 1) return FCM_ERR_INVALID_ARG;
-    int rc = need_model(h);
-    if (rc) return rc;
-    DeviceGuard g(h->device);
+// Features, forward pass and k_v0 for a batch, queued on the handle's stream:
+// row i of w->v0 receives slice i's sorted V^0 and its usability flag.
+int predict_v0_launch(fcm_ctx* h, const fcm_slice* slices, int n) {
     MlpWorkspace* w = h->mlp;
     if (w->feat_cap < n) {
         cudaFree(w->feats);
@@ -470,11 +493,24 @@ int predict_v0(fcm_ctx* h, fcm_slice* slices, int n, std::vector<unsigned char>*
         CK(dev_malloc(h, &w->v0, sizeof(float) * (D_OUT + 1) * n));
         w->feat_cap = n;
     }
+    int rc;
     if ((rc = fcm_features_impl(h, slices, n, w->feats))) return rc;
     if ((rc = ensure_mlp(h, n))) return rc;
     if ((rc = forward(h, w->feats, n))) return rc;
     k_v0<<<(n + 127) / 128, 128, 0, h->stream>>>((const HistDesc*)w->hdesc_dev, w->y, n, w->v0);
     CK(cudaGetLastError());
+    return FCM_OK;
+}
+
+// Features, forward pass and k_v0 for a batch; fills each slice's V0 and sets
+// FCM_INIT_V. ok (when given) receives the usability flag of each prediction.
+int predict_v0(fcm_ctx* h, fcm_slice* slices, int n, std::vector<unsigned char>* ok) {
+    if (!h || !slices || n < 1) return FCM_ERR_INVALID_ARG;
+    int rc = need_model(h);
+    if (rc) return rc;
+    DeviceGuard g(h->device);
+    if ((rc = predict_v0_launch(h, slices, n))) return rc;
+    MlpWorkspace* w = h->mlp;
     std::vector<float> P((size_t)n * (D_OUT + 1));
     CK(cudaMemcpyAsync(P.data(), w->v0, sizeof(float) * P.size(), cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
@@ -655,25 +691,86 @@ int fcm_predict_centers(fcm_handle h, fcm_slice* slices, int n) {
 int fcm_run_batched_warm(fcm_handle h, fcm_slice* slices, int n, int options, int* n_cold) {
     if (!h || !slices || n < 1) return FCM_ERR_INVALID_ARG;
     if (n_cold) *n_cold = 0;
-    std::vector<unsigned char> ok;
-    int rc = predict_v0(h, slices, n, &ok);
+    for (int i = 0; i < n; ++i)
+        if (!slices[i].U0 || slices[i].U0 == slices[i].U)
+            return ctx_invalid(h, "warm-started batch: every slice needs its own U0 (the cold start judges and "
+                                  "replaces the warm start)");
+    int rc = need_model(h);
     if (rc) return rc;
-    // predictions that cannot start a run go back to the cold start
-    int cold = 0;
+    DeviceGuard g(h->device);
+    MlpWorkspace* w = h->mlp;
+
+    // 1. the network's V^0 of every slice, on the device
+    if ((rc = predict_v0_launch(h, slices, n))) return rc;
+
+    // 2. the judge: every slice on its grey-level histogram, from its U^0
+    //    (plain cold-start FCM) and from the predicted V^0, read from the device
+    if (w->judge_cap < n) {
+        cudaFreeHost(w->h_v0);
+        cudaFreeHost(w->h_judge);
+        w->h_v0 = nullptr;
+        w->h_judge = nullptr;
+        w->judge_cap = 0;
+        CK(host_malloc(h, &w->h_v0, sizeof(float) * (D_OUT + 1) * n));
+        CK(host_malloc(h, &w->h_judge, sizeof(SliceResult) * 2 * n));
+        w->judge_cap = n;
+    }
+    std::vector<fcm_slice> from_u(slices, slices + n);
+    for (fcm_slice& q : from_u) {
+        q.init_mode = FCM_INIT_U;
+        q.iters_hint = 0;
+    }
+    SliceDesc *hd = nullptr, *dd = nullptr;
+    if ((rc = batch_descs(h, from_u.data(), n, (int64_t)1 << 31, &hd, &dd))) return rc;
+    std::vector<BinRun> runs(2 * (size_t)n);
     for (int i = 0; i < n; ++i) {
-        if (!ok[i] && slices[i].U0) {
-            slices[i].init_mode = FCM_INIT_U;
-            ++cold;
+        runs[i] = BinRun{i, BIN_FROM_U, 0, 0};
+        runs[n + i] = BinRun{i, BIN_FROM_V_DEV, 0, 0};
+    }
+    if ((rc = bins_run(h, hd, dd, n, runs.data(), 2 * n, w->v0, D_OUT + 1, w->h_judge))) return rc;
+    CK(cudaMemcpyAsync(w->h_v0, w->v0, sizeof(float) * (D_OUT + 1) * n, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+
+    // 3. a slice starts warm when the prediction is usable and the judge
+    //    accepts the fixed point it leads to; the others start cold. Each
+    //    slice carries the iterations its start took on the histogram.
+    std::vector<const SliceResult*> cold_ref(n, nullptr);
+    int64_t hint_sum = 0, hint_cnt = 0;
+    for (int i = 0; i < n; ++i) {
+        const SliceResult& c = w->h_judge[i];
+        const SliceResult& wr = w->h_judge[n + i];
+        const float* P = w->h_v0 + (size_t)i * (D_OUT + 1);
+        fcm_slice& s = slices[i];
+        const bool judged = c.status >= 0;  // a grey-level slice with a valid U^0
+        if (judged) cold_ref[i] = &c;
+        const bool warm = judged && P[D_OUT] != 0.0f && wr.status == FCM_OK && !(wr.flags & FCM_FLAG_EMPTY_CLUSTER) &&
+                          warm_accepted(wr.V64, wr.J, wr.status, c.V64, c.J, s.C);
+        for (int j = 0; j < FCM_MAX_CLUSTERS; ++j) s.V0[j] = (warm && j < s.C) ? P[j] : 0.0f;
+        s.init_mode = warm ? FCM_INIT_V : FCM_INIT_U;
+        s.iters_hint = judged ? (warm ? wr.iters : c.iters) : 0;
+        if (s.iters_hint > 0) {
+            hint_sum += s.iters_hint;
+            ++hint_cnt;
         }
     }
+    // a slice the histogram cannot judge (not all grey levels) gets the mean
+    for (int i = 0; i < n; ++i)
+        if (slices[i].iters_hint <= 0) slices[i].iters_hint = hint_cnt ? (int)(hint_sum / hint_cnt) : 1;
+
+    // 4. the batch, costliest slices first
     const int st = fcm_run_batched(h, slices, n, options);
     if (st == FCM_ERR_INVALID_ARG || st == FCM_ERR_CUDA || st == FCM_ERR_OOM) return st;
-    // warm runs that did not converge or emptied a cluster: rerun cold
+
+    // 5. every warm result against the cold start's fixed point: a warm run
+    //    that did not converge, emptied a cluster, or ended elsewhere with a
+    //    larger J is run again from its U^0
     std::vector<int> redo;
     for (int i = 0; i < n; ++i) {
         const fcm_slice& s = slices[i];
-        if (s.init_mode == FCM_INIT_V && s.U0 && (s.status != FCM_OK || (s.flags & FCM_FLAG_EMPTY_CLUSTER)))
-            redo.push_back(i);
+        if (s.init_mode != FCM_INIT_V) continue;
+        const bool ok = s.status == FCM_OK && !(s.flags & FCM_FLAG_EMPTY_CLUSTER) && cold_ref[i] &&
+                        warm_accepted(s.V64, s.J, s.status, cold_ref[i]->V64, cold_ref[i]->J, s.C);
+        if (!ok) redo.push_back(i);
     }
     int worst = st;
     if (!redo.empty()) {
@@ -681,6 +778,7 @@ int fcm_run_batched_warm(fcm_handle h, fcm_slice* slices, int n, int options, in
         for (size_t t = 0; t < redo.size(); ++t) {
             sub[t] = slices[redo[t]];
             sub[t].init_mode = FCM_INIT_U;
+            sub[t].iters_hint = cold_ref[redo[t]] ? cold_ref[redo[t]]->iters : 0;
         }
         const int st2 = fcm_run_batched(h, sub.data(), (int)sub.size(), options | FCM_BATCH_NO_TUNE);
         if (st2 == FCM_ERR_INVALID_ARG || st2 == FCM_ERR_CUDA || st2 == FCM_ERR_OOM) return st2;
@@ -691,7 +789,11 @@ int fcm_run_batched_warm(fcm_handle h, fcm_slice* slices, int n, int options, in
             if (slices[i].status == FCM_NOT_CONVERGED && worst == FCM_OK) worst = FCM_NOT_CONVERGED;
         }
     }
-    if (n_cold) *n_cold = cold + (int)redo.size();
+    if (n_cold) {
+        int c = 0;
+        for (int i = 0; i < n; ++i) c += slices[i].init_mode == FCM_INIT_U;
+        *n_cold = c;
+    }
     return worst;
 }
 

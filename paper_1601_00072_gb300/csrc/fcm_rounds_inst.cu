@@ -47,9 +47,9 @@ constexpr int OPEN = 0x7fffffff;
 // FP32 per thread and warp, then in FP64 across warps and segments.
 constexpr int CHUNK = 8;
 
-// The round barrier polls at most a.wait_spins times, 128 ns apart (about
-// 1 s by default), for the grid's arrivals plus a.phantoms (0 unless a test
-// injects a barrier that never fills).
+// The round barrier polls at most hdr->wait_spins times, 128 ns apart (about
+// 1 s by default), for the grid's arrivals plus hdr->phantoms (0 unless a
+// test injects a barrier that never fills).
 
 __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
     unsigned v;
@@ -545,11 +545,12 @@ __global__ void __launch_bounds__(NTR, MIN_BLOCKS_R) k_fcm_rounds(RoundsArgs a) 
         if (threadIdx.x == 0) {
             __threadfence();
             atomicAdd(&a.ctl->bar, 1u);
-            const unsigned target = (unsigned)(r + 1) * gridDim.x + a.phantoms;
+            const unsigned target = (unsigned)(r + 1) * gridDim.x + a.hdr->phantoms;
+            const uint32_t limit = a.hdr->wait_spins;
             uint32_t spins = 0;
             int stop = 0;
             while (ld_acquire_u32(&a.ctl->bar) < target) {
-                if (++spins > a.wait_spins) {
+                if (++spins > limit) {
                     atomicExch(&a.ctl->timeout, 1u);
                     stop = 1;
                     break;

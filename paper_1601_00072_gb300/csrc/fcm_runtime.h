@@ -28,6 +28,10 @@ struct BatchedWorkspace;  // fcm_batched.cu
 struct MlpWorkspace;      // fcm_mlp.cu
 struct HistWorkspace;     // fcm_hist.cu
 struct MultiWorkspace;    // fcm_multi.cu
+struct BinWorkspace;      // fcm_bins.cu
+struct SliceDesc;         // fcm_batched.h
+struct SliceResult;
+struct BinRun;
 
 }  // namespace fcm
 
@@ -85,6 +89,7 @@ struct fcm_ctx {
     fcm::MlpWorkspace* mlp = nullptr;
     fcm::HistWorkspace* hist = nullptr;
     fcm::MultiWorkspace* multi = nullptr;
+    fcm::BinWorkspace* bins = nullptr;
 };
 
 namespace fcm {
@@ -118,6 +123,20 @@ cudaError_t host_malloc(fcm_ctx* h, T** p, size_t bytes) {
 int ctx_fail(fcm_ctx* h, cudaError_t e, const char* what);
 int ctx_invalid(fcm_ctx* h, const char* what);
 int ctx_grow(fcm_ctx* h, void** p, size_t* cap, size_t bytes, const char* what);
+
+// Histogram-domain runs (fcm_bins.cu) of the ns slices whose descriptors are
+// at h_desc (host) and d_desc (device, already uploaded): queues the uploads
+// and kernels on the handle's stream, and the download of the nr results into
+// h_results (pinned host memory; nullable). Does not synchronise.
+int bins_run(fcm_ctx* h, const SliceDesc* h_desc, const SliceDesc* d_desc, int ns, const BinRun* runs, int nr,
+             const float* v0_dev, int v0_stride, SliceResult* h_results);
+void release_bins(fcm_ctx* h);
+
+// Checks a batch (n < n_limit per slice), fills its device descriptors in the
+// batched workspace's pinned array and queues their upload on the handle's
+// stream. The arrays stay valid until the next batched call on the handle.
+int batch_descs(fcm_ctx* h, const fcm_slice* slices, int n_slices, int64_t n_limit, SliceDesc** h_desc,
+                SliceDesc** d_desc);
 }  // namespace fcm
 
 void fcm_release_batched(fcm_ctx* h);

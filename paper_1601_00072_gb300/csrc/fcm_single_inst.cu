@@ -30,6 +30,7 @@
 // does this on the host, Sec. 4.3) and sets the CUDA-graph WHILE condition.
 // No block waits for another: the ticket only elects the finisher.
 #include "fcm_device.cuh"
+#include "fcm_exchange.cuh"
 #include "fcm_internal.h"
 #include "fcm_tma.cuh"
 
@@ -515,8 +516,7 @@ __global__ void __launch_bounds__(NT, 2) k_fcm_run_tma(RunState* __restrict__ st
     __shared__ float s_red[NWARP][S];
     __shared__ DF s_df[2 * C + 1];
     __shared__ float s_mx[3];
-    __shared__ float s_v[C];
-    __shared__ double s_v64[C];
+    __shared__ DF s_vq[C];
     __shared__ int s_empty[C];
     __shared__ int s_err;
 
@@ -531,12 +531,12 @@ __global__ void __launch_bounds__(NT, 2) k_fcm_run_tma(RunState* __restrict__ st
 
     float v[C];
     f2 v2[C];
-    double v64[C];
+    DF v64[C];  // the double-float quotients behind v, converted to FP64 only when written
 #pragma unroll
     for (int j = 0; j < C; ++j) {
         v[j] = st->V0[j];
         v2[j] = pack2(v[j], v[j]);
-        v64[j] = v[j];
+        v64[j] = DF{v[j], 0.0f};
     }
     int flags = 0;
 
@@ -679,39 +679,11 @@ __global__ void __launch_bounds__(NT, 2) k_fcm_run_tma(RunState* __restrict__ st
             iters = p;
             break;
         }
-        // ---- cross-block sums, the same fixed order in every block ----
-        for (int s = warp; s < S; s += NWARP) {
-            const float* ps = part + (int64_t)s * gridDim.x;
-            if (s <= 2 * C) {
-                DF d{0.0f, 0.0f};
-                for (int b = lane; b < (int)gridDim.x; b += 32) df_add(d, __ldcg(ps + b));
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) {
-                    DF e{__shfl_xor_sync(0xffffffffu, d.hi, o), __shfl_xor_sync(0xffffffffu, d.lo, o)};
-                    d = (lane & o) ? df_merge(e, d) : df_merge(d, e);
-                }
-                if (lane == 0) s_df[s] = d;
-            } else {
-                float t = 0.0f;
-                for (int b = lane; b < (int)gridDim.x; b += 32) t = fmaxf(t, __ldcg(ps + b));
-                t = warp_max(t);
-                if (lane == 0) s_mx[s - (2 * C + 1)] = t;
-            }
-        }
+        // ---- cross-block sums and V^{p+1}, the same fixed order in every block ----
+        grid_totals<S, 2 * C + 1, NWARP>(part, (int)gridDim.x, s_df, s_mx);
         __syncthreads();
-        if (threadIdx.x < C) {
-            // V^{p+1}_j = num_j / den_j in FP64 from the compensated sums (Eq. 3)
-            const int j = threadIdx.x;
-            const double num = (double)s_df[j].hi + (double)s_df[j].lo;
-            const double den = (double)s_df[C + j].hi + (double)s_df[C + j].lo;
-            const bool empty = !(den > 0.0);
-            const double q = empty ? 0.0 : num / den;
-            s_v64[j] = q;
-            s_v[j] = (float)q;
-            s_empty[j] = empty;
-        }
+        grid_centers<C>(s_df, s_vq, s_empty);
         __syncthreads();
-        const double J = (double)s_df[2 * C].hi + (double)s_df[2 * C].lo;
         const float delta = s_mx[0];
         const bool bad = s_mx[1] != 0.0f, tmo = s_mx[2] != 0.0f;
         bool update = false;
@@ -731,9 +703,9 @@ __global__ void __launch_bounds__(NT, 2) k_fcm_run_tma(RunState* __restrict__ st
             if (blockIdx.x == 0 && threadIdx.x == 0 && st->trace) {
                 double* t = st->trace + (int64_t)(p - 1) * (2 + C);
                 t[0] = delta;
-                t[1] = J;
+                t[1] = df_to_double(s_df[2 * C]);
 #pragma unroll
-                for (int j = 0; j < C; ++j) t[2 + j] = v64[j];
+                for (int j = 0; j < C; ++j) t[2 + j] = df_to_double(v64[j]);
             }
             if (delta < eps) {
                 status = FCM_OK;
@@ -748,7 +720,7 @@ __global__ void __launch_bounds__(NT, 2) k_fcm_run_tma(RunState* __restrict__ st
             }
             if (blockIdx.x == 0 && threadIdx.x == 0) {
                 st->delta = delta;
-                st->J = J;
+                st->J = df_to_double(s_df[2 * C]);
             }
         }
         if (update) {
@@ -759,16 +731,16 @@ __global__ void __launch_bounds__(NT, 2) k_fcm_run_tma(RunState* __restrict__ st
                     flags |= FCM_FLAG_EMPTY_CLUSTER;
                     if (p == 0 && INIT == P_ACCUM0) {
                         v[j] = 0.0f;
-                        v64[j] = 0.0;
+                        v64[j] = DF{0.0f, 0.0f};
                     }
                 } else {
-                    v[j] = s_v[j];
-                    v64[j] = s_v64[j];
+                    v[j] = s_vq[j].hi;
+                    v64[j] = s_vq[j];
                 }
                 v2[j] = pack2(v[j], v[j]);
             }
         }
-        __syncthreads();  // s_df / s_v are rewritten by the next pass
+        __syncthreads();  // s_df / s_vq are rewritten by the next pass
     }
 
     // copies issued for passes that will not run: let them land
@@ -787,7 +759,7 @@ __global__ void __launch_bounds__(NT, 2) k_fcm_run_tma(RunState* __restrict__ st
 #pragma unroll
         for (int j = 0; j < C; ++j) {
             st->V[j] = v[j];
-            st->V64[j] = v64[j];
+            st->V64[j] = df_to_double(v64[j]);
         }
         st->status = status;
         st->iters = iters;

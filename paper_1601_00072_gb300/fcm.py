@@ -542,19 +542,22 @@ class FCM:
     def batched_plan(self) -> dict:
         p = _lib.fcm_batch_plan()
         _lib.check(self._lib.fcm_batched_plan(self._h, ctypes.byref(p)), self._h)
-        return {"schedule": "rounds" if p.schedule == _lib.FCM_SCHED_ROUNDS else "slices",
+        names = {_lib.FCM_SCHED_SLICES: "slices", _lib.FCM_SCHED_ROUNDS: "rounds", _lib.FCM_SCHED_TEAMS: "teams"}
+        return {"schedule": names[p.schedule],
                 "block": p.block, "cluster": p.cluster, "big": p.big, "tile": p.tile, "ms": p.ms}
 
     def set_batched_plan(self, block=None, cluster=1, big=1 << 62, schedule="slices", tile=0):
         """Force a launch shape for later batched runs; no arguments returns
         to the autotuner. ``schedule="rounds"`` takes ``block`` and ``tile``;
-        ``"slices"`` takes ``block``, ``cluster``, ``big`` and ``tile`` (0, or
-        the first-phase iteration cap of a two-phase batch)."""
+        ``"teams"`` takes ``block`` and ``tile`` (the team-size target in
+        percent of the mean cost per CTA); ``"slices"`` takes ``block``,
+        ``cluster``, ``big`` and ``tile`` (0, or the first-phase iteration cap
+        of a two-phase batch)."""
         if block is None:
             _lib.check(self._lib.fcm_batched_set_plan(self._h, None), self._h)
             return
-        rounds = schedule == "rounds"
-        p = _lib.fcm_batch_plan(int(block), 1 if rounds else int(cluster), 0 if rounds else int(big), 0.0,
-                                _lib.FCM_SCHED_ROUNDS if rounds else _lib.FCM_SCHED_SLICES,
-                                int(tile))
+        codes = {"slices": _lib.FCM_SCHED_SLICES, "rounds": _lib.FCM_SCHED_ROUNDS, "teams": _lib.FCM_SCHED_TEAMS}
+        sliced = schedule == "slices"
+        p = _lib.fcm_batch_plan(int(block), int(cluster) if sliced else 1, int(big) if sliced else 0, 0.0,
+                                codes[schedule], int(tile))
         _lib.check(self._lib.fcm_batched_set_plan(self._h, ctypes.byref(p)), self._h)

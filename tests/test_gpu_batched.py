@@ -105,17 +105,21 @@ SLICE_PLANS = [dict(block=512, cluster=1, big=1 << 40), dict(block=256, cluster=
                dict(block=256, cluster=4, big=4096)]
 ROUND_PLANS = [dict(schedule="rounds", block=512, tile=2048), dict(schedule="rounds", block=256, tile=4096),
                dict(schedule="rounds", block=512, tile=16384), dict(schedule="rounds", block=256, tile=65536)]
-PLANS = [None] + SLICE_PLANS + ROUND_PLANS
+# team schedule: tile is the team-size target in percent of the mean cost per
+# CTA; 10 gives most slices of a small batch large teams
+TEAM_PLANS = [dict(schedule="teams", block=256, tile=100), dict(schedule="teams", block=512, tile=50),
+              dict(schedule="teams", block=256, tile=10)]
+PLANS = [None] + SLICE_PLANS + ROUND_PLANS + TEAM_PLANS
 # one plan of each schedule for the tests that run every schedule
 EACH = [dict(block=512, cluster=2, big=8192), dict(schedule="rounds", block=256, tile=4096),
-        dict(block=256, cluster=4, big=16384, tile=3)]
+        dict(block=256, cluster=4, big=16384, tile=3), dict(schedule="teams", block=256, tile=10)]
 
 
 def plan_id(p):
     if p is None:
         return "auto"
-    if p.get("schedule") == "rounds":
-        return f"rounds_b{p['block']}_t{p['tile']}"
+    if p.get("schedule") in ("rounds", "teams"):
+        return f"{p['schedule']}_b{p['block']}_t{p['tile']}"
     return f"slices_b{p['block']}_k{p['cluster']}_big{p['big']}" + (f"_cap{p['tile']}" if p.get("tile") else "")
 
 
@@ -242,7 +246,7 @@ def test_autotuner_caches_its_plan(tmp_path, monkeypatch):
     plan = h.batched_plan()
     h.close()
     assert plan["block"] in (256, 512) and plan["cluster"] in (1, 2, 4, 8) and plan["ms"] > 0
-    assert plan["schedule"] in ("slices", "rounds")
+    assert plan["schedule"] in ("slices", "rounds", "teams")
     text = path.read_text()
     assert '"block": %d' % plan["block"] in text and '"tile": %d' % plan["tile"] in text
     # a new handle takes the cached plan without tuning
@@ -259,7 +263,8 @@ def test_autotuner_caches_its_plan(tmp_path, monkeypatch):
 
 @pytest.mark.parametrize("plan", [None, dict(schedule="rounds", block=512, tile=4096),
                                   dict(block=256, cluster=4, big=16384, tile=40),
-                                  dict(block=256, cluster=4, big=4096)], ids=plan_id)
+                                  dict(block=256, cluster=4, big=4096),
+                                  dict(schedule="teams", block=256, tile=100)], ids=plan_id)
 def test_full_512_slice_batch_matches_oracle(fcm, plan):
     """The whole 512-slice workload (sides 64..512, C in {3, 4, 5}), with the
     autotuned plan and with the round schedule."""

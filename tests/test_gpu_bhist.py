@@ -103,3 +103,48 @@ def test_non_grey_level_slice_is_rejected_alone(fcm):
         rep, _ = check_slice(slices[i], *host[i], 2.0)
         assert slices[i].status in (0, 1)
         assert_slice(rep, f"slice {i}")
+
+
+def test_exact_first_stop_where_the_bound_cannot_decide(fcm):
+    """The first stopping quantity delta_1 = max_i |f(x_i, V^1) - U^0_i| is
+    bounded from below by one pixel per grey level; a pass over every pixel
+    takes it exactly only when that bound is below eps or max_iter is 1.
+    Slices whose U^0 already sits at a fixed point (the oracle's converged
+    memberships) stop at iteration 1 with delta_1 of order 1e-7; a slice with
+    max_iter = 1 stops there too; the others, in the same batch, need no
+    exact pass. Each is compared with the oracle at the same iterate."""
+    from paper_1601_00072_gb300.fcm import Slice
+    slices, host = [], []
+    for t, i in enumerate(range(300, 306)):
+        sp, img, _ = phantom.batch_slice(i)
+        x = img.reshape(-1)
+        u0 = phantom.dirichlet_u0((phantom.U0_FAMILY, i), sp.C, x.size)
+        max_iter = 300
+        if t in (0, 3):
+            o = oracle.fcm_quantized(x, sp.C, 2.0, 1e-10, 2000, U0=u0, want_U=False)
+            u0 = np.ascontiguousarray(oracle.memberships(np.arange(256.0), o["V"], 2.0)[:, x], dtype=np.float32)
+        if t == 1:
+            max_iter = 1
+        slices.append(Slice(x=_cuda(x), C=sp.C, eps=EPS, max_iter=max_iter, U0=_cuda(u0)))
+        host.append((x, u0, max_iter))
+    assert fcm.run_batched_hist(slices) in (0, 1)
+    for t, (s, (x, u0, mi)) in enumerate(zip(slices, host)):
+        o = oracle.fcm_quantized(x, s.C, 2.0, eps32(EPS), mi, U0=u0)
+        if t in (0, 3):
+            assert s.status == 0 and s.iters == 1 and o["iters"] == 1, (t, s.iters, o["iters"])
+        if t == 1:
+            assert s.status == 1 and s.iters == 1
+        if t in (0, 1, 3):
+            # delta_1 itself, over every pixel
+            assert abs(s.delta - o["delta"][0]) <= 1e-6, (t, s.delta, o["delta"][0])
+        assert abs(s.iters - o["iters"]) <= 1, (t, s.iters, o["iters"])
+        at = oracle.fcm_quantized(x, s.C, 2.0, 0.0, s.iters, U0=u0)
+        ref_U = oracle.memberships(np.arange(256.0), at["V"], 2.0)[:, x]
+        rep = precision_report(s.U.cpu().numpy(), s.V.cpu().numpy(), s.iters, ref_U, at["V"], s.iters)
+        if t == 1:
+            # V^1 from a random U^0 puts every center near the mean grey level,
+            # where U^1 = f(x, V^1) magnifies the rounding of V^1 (as in the
+            # early iterates of the single-image runs): V^1 and delta_1 only
+            assert rep["center_rel_err"] <= 1e-5, rep
+        else:
+            assert_within(rep)

@@ -75,7 +75,9 @@ def test_multi_feature_barrier_gives_up(lib):
         assert r2.iters == ref.iters and np.array_equal(r2.V.cpu().numpy(), ref.V.cpu().numpy())
 
 
-def test_round_schedule_barrier_gives_up(lib):
+@pytest.mark.parametrize("plan", [dict(schedule="rounds", block=512, tile=4096),
+                                  dict(schedule="teams", block=256, tile=10)], ids=["rounds", "teams"])
+def test_batch_barrier_gives_up(lib, plan):
     from paper_1601_00072_gb300.fcm import FCM, Slice
 
     def batch():
@@ -87,14 +89,18 @@ def test_round_schedule_barrier_gives_up(lib):
         return out
 
     with FCM(0) as h:
-        h.set_batched_plan(schedule="rounds", block=512, tile=4096)
+        h.set_batched_plan(**plan)
         ref = batch()
         h.run_batched(ref)
         h.set_limits(grid_wait_spins=SHORT_SPINS, barrier_phantoms=1)
         bad = batch()
         st = h.run_batched(bad)
         assert st == lib.FCM_ERR_TIMEOUT
-        assert all(s.status == lib.FCM_ERR_TIMEOUT for s in bad)
+        if plan["schedule"] == "rounds":
+            assert all(s.status == lib.FCM_ERR_TIMEOUT for s in bad)
+        else:  # a slice of a lone CTA has no barrier; every team's gives up
+            assert any(s.status == lib.FCM_ERR_TIMEOUT for s in bad)
+            assert all(s.status in (lib.FCM_ERR_TIMEOUT, lib.FCM_OK) for s in bad)
         h.set_limits(defaults=True)
         again = batch()
         h.run_batched(again)

@@ -133,8 +133,9 @@ def test_adam_steps_match_oracle(fcm):
     above both its error (the 1e-3 bound of the gradient test) and eps. There
     the update must match to a small fraction of lr; where the gradient is
     exactly zero (one-hot inputs of cluster counts absent from the batch) the
-    weight must not move at all; and no weight may move by more than lr per
-    step."""
+    weight must not move at all. A bias-corrected step moves a weight by at
+    most lr at step 1 and, by the Cauchy-Schwarz inequality on
+    m_hat^2 / v_hat, at most lr * sqrt(1.0027) at step 2."""
     slices, host = batch_slices(range(24))
     g = np.random.default_rng(5)
     Cs = np.array([C for _, _, C in host], dtype=np.int32)
@@ -169,7 +170,8 @@ def test_adam_steps_match_oracle(fcm):
             bound = tol * lr + 1e-6 * np.abs(q[k])
             assert np.all(d[certain] <= bound[certain]), (steps, k, float((d - bound)[certain].max()))
             assert np.array_equal(got[k][zero], p0[k][zero]), (steps, k)
-            assert np.all(np.abs(got[k] - p0[k]) <= steps * lr * (1 + 1e-4) + 1e-6 * np.abs(p0[k])), (steps, k)
+            step_bound = lr * (1.0 + 1e-4) + (steps - 1) * lr * np.sqrt(1.0028)
+            assert np.all(np.abs(got[k] - p0[k]) <= step_bound + 1e-6 * np.abs(p0[k])), (steps, k)
             compared += int(certain.sum())
         print(f"\n{steps} Adam step(s): {compared} of {mlp.N_PARAMS} weights compared element by element")
         assert compared >= 0.5 * mlp.N_PARAMS
@@ -242,19 +244,98 @@ def test_training_on_the_gpu_saves_iterations(fcm):
     assert ok.mean() >= 0.85
 
 
-@pytest.mark.skipif(not os.path.exists(os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
-                                                    "paper_1601_00072_gb300", "data", "warmstart.fcmw")),
-                    reason="no trained model file")
+MODEL_FILE = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                          "paper_1601_00072_gb300", "data", "warmstart.fcmw")
+
+
+@pytest.mark.skipif(not os.path.exists(MODEL_FILE), reason="no trained model file")
 def test_shipped_model_saves_iterations_on_the_batch(fcm):
+    """The whole 512-slice batch: the judge keeps a warm start only where its
+    fixed point passes the acceptance rule against the cold start, so every
+    returned slice passes it against an independent cold batch (a
+    trajectory-sensitive slice may end elsewhere in FP32 than on the
+    histogram: at most one is allowed)."""
     from paper_1601_00072_gb300 import warmstart
     fcm.model_load(warmstart.MODEL_PATH)
     cold, _ = batch_slices(range(512))
     warm, _ = batch_slices(range(512))
     cold_it, warm_it, ok, n_cold = _gain(fcm, cold, warm)
+    ran_cold = sum(s.init == "U" for s in warm)
     print(f"\ncold mean iters {cold_it.mean():.1f}, warm {warm_it.mean():.1f}, "
-          f"accepted {ok.mean():.3f}, ran cold {n_cold}")
+          f"accepted {ok.mean():.4f}, ran cold {n_cold}, failing {np.flatnonzero(~ok).tolist()}")
+    assert n_cold == ran_cold
     assert warm_it.mean() < 0.8 * cold_it.mean()
-    assert ok.mean() >= 0.93
+    assert (~ok).sum() <= 1
+
+
+def _oracle_model():
+    """The shipped network's parameters as the oracle's FP64 dict, weight
+    matrices rounded to BF16 as the library uses them."""
+    raw = open(MODEL_FILE, "rb").read()
+    head = np.frombuffer(raw[:20], dtype=np.int32)
+    assert head[0] == 0x57434D46 and head[2] == mlp.D_IN and head[3] == mlp.D_H and head[4] == mlp.D_OUT
+    return oracle_params(np.frombuffer(raw[20:], dtype=np.float32).copy())
+
+
+def _oracle_accepts(Vw, Jw, st_w, Vc, Jc):
+    vw, vc = np.sort(np.asarray(Vw, np.float64)), np.sort(np.asarray(Vc, np.float64))
+    return bool(np.max(np.abs(vw - vc) / np.maximum(np.abs(vc), 1.0)) <= 1e-4 or (st_w >= 0 and Jw <= Jc * (1 + 1e-5)))
+
+
+@pytest.mark.skipif(not os.path.exists(MODEL_FILE), reason="no trained model file")
+def test_judge_decisions_match_an_oracle_judge(fcm):
+    """The oracle takes the same steps on the CPU: the network's V^0 (FP64
+    forward with the shipped BF16 weights), the 256-bin run from V^0 and from
+    U^0, and the acceptance rule. The slices the library runs warm are the
+    ones the oracle accepts (up to borderline slices, where the FP32 and FP64
+    predictions differ by a few 1e-5 of a grey level), and every returned
+    result passes the rule against the oracle's cold fixed point."""
+    from paper_1601_00072_gb300 import warmstart
+    fcm.model_load(warmstart.MODEL_PATH)
+    idx = list(range(0, 512, 4))
+    warm, host = batch_slices(idx)
+    fcm.run_batched_warm(warm)
+    P = _oracle_model()
+    X = np.stack([mlp.features(x, C) for x, _, C in host])
+    V0 = mlp.predict_centers(P, X, [C for _, _, C in host])
+    agree = passes = 0
+    for s, (x, u0, C), v0 in zip(warm, host, V0):
+        oc = oracle.fcm_quantized(x, C, 2.0, eps32(1e-5), 300, U0=u0, want_U=False)
+        ow = oracle.fcm_quantized(x, C, 2.0, eps32(1e-5), 300, V0=v0.astype(np.float32).astype(np.float64),
+                                  want_U=False)
+        accept = ow["status"] == oracle.CONVERGED and _oracle_accepts(ow["V"], ow["J"][-1], 0, oc["V"], oc["J"][-1])
+        agree += accept == (s.init == "V")
+        passes += _oracle_accepts(s.V64, s.J, s.status, oc["V"], oc["J"][-1])
+    print(f"\njudge agrees with the oracle on {agree} of {len(idx)} slices; {passes} results pass the rule")
+    assert agree >= 0.95 * len(idx)
+    assert passes >= len(idx) - 1
+
+
+def test_judge_replaces_warm_starts_that_end_worse(fcm):
+    """A network that predicts the same centers (28, 57, 85, 113, 142 grey
+    levels) for every slice: usable starts, many of which lead to another
+    fixed point than the cold start's. The judge sends those slices back to
+    their U^0, and every returned slice passes the acceptance rule against
+    the oracle's cold fixed point."""
+    p = np.zeros(mlp.N_PARAMS, dtype=np.float32)
+    p[-8:] = (np.arange(8) + 1) / 9.0
+    fcm.set_model_params(p)
+    idx = list(range(64))
+    warm, host = batch_slices(idx)
+    cold, _ = batch_slices(idx)
+    st, n_cold = fcm.run_batched_warm(warm, tune=False)
+    fcm.run_batched(cold, tune=False)
+    assert n_cold == sum(s.init == "U" for s in warm)
+    passes = 0
+    for s, c, (x, u0, C) in zip(warm, cold, host):
+        oc = oracle.fcm_quantized(x, C, 2.0, eps32(1e-5), 300, U0=u0, want_U=False)
+        passes += _oracle_accepts(s.V64, s.J, s.status, oc["V"], oc["J"][-1])
+        if s.init == "U":  # ran cold: the plain cold start's own result
+            assert s.iters == c.iters
+            assert np.allclose(s.V.cpu().numpy(), c.V.cpu().numpy(), rtol=1e-6, atol=1e-5)
+    print(f"\nran cold {n_cold} of {len(idx)}; {passes} pass the rule")
+    assert 0 < n_cold < len(idx)
+    assert passes >= len(idx) - 1
 
 
 def test_unusable_predictions_fall_back_to_cold_start(fcm):
