@@ -183,6 +183,32 @@ int fcm_run(fcm_handle h, const float* x, int64_t n, int C, float m,
             float* V, int options, fcm_report* rep);
 
 /*
+ * fcm_init_dirichlet — the random initial membership of Algorithm 1 step 2
+ * ("initialize U randomly", Sec. 2.1), drawn on the device: each pixel's
+ * column of U^0 is a uniform Dirichlet(1, ..., 1) draw, C standard
+ * exponentials E_j = -ln r_j normalised to sum 1. The uniforms r_j come from
+ * the counter-based generator Philox4x32-10 (Salmon et al., SC'11): pixel i
+ * uses counter (i mod 2^32, i div 2^32, j div 4, 0) under key
+ * (seed mod 2^32, seed div 2^32), word j mod 4; a word w gives
+ * r = (2 floor(w / 512) + 1) / 2^24. A pixel's draw depends only on its index
+ * and the seed. Exponentials and the normalisation are FP32.
+ *
+ *   n, C     pixels (>= 1) and clusters (1..8).
+ *   U        C*n floats, device memory, cluster-major; receives U^0.
+ *
+ * Queued on the handle's stream; returns FCM_OK or FCM_ERR_INVALID_ARG.
+ */
+int fcm_init_dirichlet(fcm_handle h, int64_t n, int C, uint64_t seed, float* U);
+
+/*
+ * fcm_run_seeded — fcm_run from the seeded random start: fcm_init_dirichlet
+ * into U, then fcm_run with FCM_INIT_U and U^0 read from U (updated in place).
+ * Arguments as fcm_run; U must be device memory.
+ */
+int fcm_run_seeded(fcm_handle h, const float* x, int64_t n, int C, float m, float eps, int max_iter,
+                   uint64_t seed, float* U, float* V, int options, fcm_report* rep);
+
+/*
  * fcm_run_stream — fcm_run over a sequence of images of one shape (n pixels,
  * C clusters, the same m, eps and max_iter), each read from and written back
  * to host memory, with the host-device copies overlapped with the runs:
@@ -353,6 +379,11 @@ typedef struct {
 #define FCM_BATCH_RETUNE 16  /* run the autotuner even if a plan is cached        */
 #define FCM_BATCH_NO_TUNE 32 /* use the cached or default plan, never tune        */
 #define FCM_BATCH_NO_GRAPH 64 /* launch directly instead of replaying a CUDA graph */
+#define FCM_BATCH_PRESOLVE 128 /* unless every slice has an iters_hint: first run each slice
+                                  on its grey-level histogram from its own start and order
+                                  the queue (and size teams) by the iterations that took,
+                                  within the call (the structs' iters_hint are not
+                                  written); the pixel runs and their results are the same */
 
 /*
  * fcm_run_batched — Algorithm 1 on each of n_slices slices, in one persistent

@@ -66,6 +66,7 @@ FCM_SCHED_TEAMS = 2
 FCM_BATCH_RETUNE = 16
 FCM_BATCH_NO_TUNE = 32
 FCM_BATCH_NO_GRAPH = 64
+FCM_BATCH_PRESOLVE = 128
 FCM_MODEL_PARAMS = 51464
 MODEL_D_IN = 264
 MODEL_D_OUT = 8
@@ -85,6 +86,9 @@ SIGNATURES = [
     ("fcm_get_limits", _i, [_vp, ctypes.POINTER(fcm_limits)]),
     ("fcm_run", _i, [_vp, _vp, _i64, _i, _f, _f, _i, _i, _vp, _vp, _vp, _i,
                      ctypes.POINTER(fcm_report)]),
+    ("fcm_init_dirichlet", _i, [_vp, _i64, _i, ctypes.c_uint64, _vp]),
+    ("fcm_run_seeded", _i, [_vp, _vp, _i64, _i, _f, _f, _i, ctypes.c_uint64, _vp, _vp, _i,
+                            ctypes.POINTER(fcm_report)]),
     ("fcm_run_stream", _i, [_vp, _i, ctypes.POINTER(_vp), _i64, _i, _f, _f, _i, ctypes.POINTER(_vp),
                             ctypes.POINTER(_vp), _vp, _i, ctypes.POINTER(fcm_report)]),
     ("fcm_run_hist", _i, [_vp, _vp, _i64, _i, _f, _f, _i, _i, _vp, _vp, _vp, ctypes.POINTER(fcm_report)]),

@@ -507,7 +507,7 @@ int ilog2(int64_t v) {
     return l;
 }
 
-std::string bucket_key(fcm_ctx* h, const fcm_slice* s, int n) {
+std::string bucket_key(fcm_ctx* h, const fcm_slice* s, int n, bool presolved) {
     int64_t total = 0, largest = 0;
     unsigned cset = 0;
     bool hinted = true;
@@ -517,6 +517,7 @@ std::string bucket_key(fcm_ctx* h, const fcm_slice* s, int n) {
         cset |= 1u << s[i].C;
         hinted &= s[i].iters_hint > 0;
     }
+    hinted |= presolved;
     char buf[512];
     std::snprintf(buf, sizeof(buf), "%s|C%x|s%d|p%d|l%d%s", h->device_name.c_str(), cset, ilog2(n), ilog2(total),
                   ilog2(largest), hinted ? "|hinted" : "");
@@ -657,7 +658,7 @@ int check_slices(fcm_ctx* h, const fcm_slice* slices, int n_slices, int64_t n_li
 
 // The device descriptors of a batch in the pinned host array, and its work
 // order.
-int fill_descs(fcm_ctx* h, const fcm_slice* slices, int n_slices) {
+int fill_descs(fcm_ctx* h, const fcm_slice* slices, int n_slices, const int* hints = nullptr) {
     int rc = ensure_batched(h, n_slices);
     if (rc) return rc;
     BatchedWorkspace* w = h->batched;
@@ -697,14 +698,16 @@ int fill_descs(fcm_ctx* h, const fcm_slice* slices, int n_slices) {
         for (int j = 0; j < s.C; ++j) d.V0[j] = s.init_mode == FCM_INIT_V ? s.V0[j] : 0.0f;
     }
     // the cost of each slice for the work order: its pixels, times its
-    // expected passes when every slice carries an iteration hint
+    // expected passes when every slice carries an iteration hint (its own,
+    // or the pre-solve's in hints)
+    auto hint = [&](int i) { return hints ? hints[i] : slices[i].iters_hint; };
     bool hinted = true;
-    for (int i = 0; i < n_slices && hinted; ++i) hinted = slices[i].iters_hint > 0;
+    for (int i = 0; i < n_slices && hinted; ++i) hinted = hint(i) > 0;
     w->cost.resize(n_slices);
     w->size.resize(n_slices);
     for (int i = 0; i < n_slices; ++i) {
         w->size[i] = slices[i].n;
-        w->cost[i] = hinted ? slices[i].n * (int64_t)(slices[i].iters_hint + 3) : slices[i].n;
+        w->cost[i] = hinted ? slices[i].n * (int64_t)(hint(i) + 3) : slices[i].n;
     }
     order_for(w, n_slices, (int64_t)1 << 62);
     return FCM_OK;
@@ -748,6 +751,39 @@ int batch_descs(fcm_ctx* h, const fcm_slice* slices, int n_slices, int64_t n_lim
 
 }  // namespace fcm
 
+namespace {
+
+// FCM_BATCH_PRESOLVE: every slice's iteration count from its own start, run
+// to convergence on its grey-level histogram (the runs give the per-pixel
+// iterates up to rounding, so the counts agree within about one), into
+// hints (the caller's structs are not touched). A slice that is not all grey
+// levels gets the mean of the others.
+int presolve_hints(fcm_ctx* h, const fcm_slice* slices, int n, std::vector<int>* hints) {
+    for (int i = 0; i < n; ++i)
+        if (slices[i].n >= ((int64_t)1 << 31)) return FCM_OK;  // beyond the bin counters: no hints
+    SliceDesc *hd = nullptr, *dd = nullptr;
+    int rc = batch_descs(h, slices, n, (int64_t)1 << 31, &hd, &dd);
+    if (rc) return rc;
+    std::vector<BinRun> runs(n);
+    for (int i = 0; i < n; ++i) runs[i] = BinRun{i, slices[i].init_mode == FCM_INIT_U ? BIN_FROM_U : BIN_FROM_V, 0, 0};
+    BatchedWorkspace* w = h->batched;
+    if ((rc = bins_run(h, hd, dd, n, runs.data(), n, nullptr, 0, w->h_res))) return rc;
+    CK(cudaStreamSynchronize(h->stream));
+    int64_t sum = 0, cnt = 0;
+    for (int i = 0; i < n; ++i)
+        if (w->h_res[i].status >= 0 && w->h_res[i].iters > 0) {
+            sum += w->h_res[i].iters;
+            ++cnt;
+        }
+    hints->resize(n);
+    for (int i = 0; i < n; ++i)
+        (*hints)[i] = (w->h_res[i].status >= 0 && w->h_res[i].iters > 0) ? w->h_res[i].iters
+                                                                        : (cnt ? (int)(sum / cnt) : 1);
+    return FCM_OK;
+}
+
+}  // namespace
+
 extern "C" {
 
 int fcm_run_batched(fcm_handle h, fcm_slice* slices, int n_slices, int options) {
@@ -756,7 +792,13 @@ int fcm_run_batched(fcm_handle h, fcm_slice* slices, int n_slices, int options) 
     int rc = check_slices(h, slices, n_slices, (int64_t)1 << 40, &in_place);
     if (rc) return rc;
     DeviceGuard g(h->device);
-    rc = fill_descs(h, slices, n_slices);
+    std::vector<int> hints;  // the pre-solve's iteration counts, or empty
+    if (options & FCM_BATCH_PRESOLVE) {
+        bool hinted = true;
+        for (int i = 0; i < n_slices && hinted; ++i) hinted = slices[i].iters_hint > 0;
+        if (!hinted && (rc = presolve_hints(h, slices, n_slices, &hints))) return rc;
+    }
+    rc = fill_descs(h, slices, n_slices, hints.empty() ? nullptr : hints.data());
     if (rc) return rc;
     BatchedWorkspace* w = h->batched;
 
@@ -765,7 +807,7 @@ int fcm_run_batched(fcm_handle h, fcm_slice* slices, int n_slices, int options) 
         plan = w->forced_plan;
     } else {
         if (!w->cache_loaded) load_cache(w);
-        const std::string key = bucket_key(h, slices, n_slices);
+        const std::string key = bucket_key(h, slices, n_slices, !hints.empty());
         auto it = w->plans.find(key);
         const bool may_tune = !(options & FCM_BATCH_NO_TUNE) && !in_place;
         if (it != w->plans.end() && !(options & FCM_BATCH_RETUNE)) {

@@ -11,7 +11,7 @@
 // pixels of any slice, so a large slice is shared by many SMs):
 //   A  histogram, input checks, one pixel index per grey level, and the
 //      per-chunk sums of V^1 (Eq. 3) for slices started from U^0;
-//   S0 per run (one CTA): V^1, then the first stopping quantity
+//   S0 per run (one warp): V^1, then the first stopping quantity
 //      delta_1 = max_i |f(x_i, V^1) - U^0_i| is bounded from below by the
 //      recorded pixel of every grey level; when that bound already reaches
 //      eps, the first iteration cannot stop and the run proceeds on the bins;
@@ -170,51 +170,14 @@ __global__ void __launch_bounds__(BNT) k_bins_pass_a(BinArgs a) {
 }
 
 // ---------------------------------------------------------------------------
-// Solve: one CTA per run
+// Solve: one warp per run
 // ---------------------------------------------------------------------------
 
-struct SolveShared {
-    DF wsum[BNW][2 * FCM_MAX_CLUSTERS];
-    DF tot[2 * FCM_MAX_CLUSTERS];
-    float wmax[BNW];
-    float v1[FCM_MAX_CLUSTERS];
-    double v164[FCM_MAX_CLUSTERS];
-    int empty;
-    BinScratch sc;
-};
-
-template <int C>
-__device__ __forceinline__ void block_df_sums(SolveShared& sh, DF (&s)[2 * C]) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-    for (int q = 0; q < 2 * C; ++q) {
-        const DF d = warp_sum_df(s[q]);
-        if (lane == 0) sh.wsum[warp][q] = d;
-    }
-    __syncthreads();
-    if (threadIdx.x < 2 * C) {
-        const int q = threadIdx.x;
-        DF t = sh.wsum[0][q];
-        for (int w = 1; w < BNW; ++w) t = df_merge(t, sh.wsum[w][q]);
-        sh.tot[q] = t;
-    }
-    __syncthreads();
-}
-
-__device__ __forceinline__ float block_max(SolveShared& sh, float mx) {
-    mx = warp_max(mx);
-    if ((threadIdx.x & 31) == 0) sh.wmax[threadIdx.x >> 5] = mx;
-    __syncthreads();
-    float r = sh.wmax[0];
-    for (int w = 1; w < BNW; ++w) r = fmaxf(r, sh.wmax[w]);
-    __syncthreads();
-    return r;
-}
+constexpr int SNT = 32;  // threads of a solve CTA: one warp, lane l holds grey levels l + 32 t
 
 template <int C, int MK>
-__device__ __noinline__ void solve_run(const BinArgs& a, int r, const BinRun& run, const SliceDesc& d,
-                                       SolveShared& sh) {
-    const int s = run.slice, b = threadIdx.x;
+__device__ __noinline__ void solve_run(const BinArgs& a, int r, const BinRun& run, const SliceDesc& d) {
+    const int s = run.slice, lane = threadIdx.x;
     const bool from_u = run.init == BIN_FROM_U;
     const float m = d.m, inv_m1 = d.inv_m1;
     SliceResult& res = a.results[r];
@@ -231,11 +194,13 @@ __device__ __noinline__ void solve_run(const BinArgs& a, int r, const BinRun& ru
     }
     if (bad) {
         // not a grey-level slice (or a bad U^0 / V^0): the status, and V = V^0
-        if (b < C) {
-            if (run.write_u) d.V[b] = v0[b];
-            res.V64[b] = v0[b];
-        }
-        if (b == 0) {
+#pragma unroll
+        for (int j = 0; j < C; ++j)
+            if (lane == j) {
+                if (run.write_u) d.V[j] = v0[j];
+                res.V64[j] = v0[j];
+            }
+        if (lane == 0) {
             res.iters = 0;
             res.status = FCM_ERR_BAD_INPUT;
             res.flags = 0;
@@ -244,54 +209,58 @@ __device__ __noinline__ void solve_run(const BinArgs& a, int r, const BinRun& ru
         }
         return;
     }
-    const unsigned long long cnt = a.hist[(int64_t)s * 256 + b];
-    if (b == 0) sh.empty = 0;
+    float cnt[WB];
+#pragma unroll
+    for (int t = 0; t < WB; ++t) cnt[t] = (float)a.hist[(int64_t)s * 256 + lane + 32 * t];
 
     // ---- V^1 (Eq. 3): from the chunk sums of pass A, or from the bins with U^0 = f(b, V^0) ----
-    float up[C];
-#pragma unroll
-    for (int j = 0; j < C; ++j) up[j] = 0.0f;
+    float up[WB][C];
+    DF tot[2 * C];
     if (from_u) {
-        if (b < 2 * C) {
-            const int c0 = a.chunk_base[s], c1 = a.chunk_base[s + 1];
-            DF t{0.0f, 0.0f};
-            for (int c = c0; c < c1; ++c) {
-                const float2 p = a.part[(int64_t)c * 2 * FCM_MAX_CLUSTERS + b];
-                t = df_merge(t, DF{p.x, p.y});
+        // lane q < 2C merges sum q over the slice's chunks, in chunk order
+        DF mine{0.0f, 0.0f};
+        if (lane < 2 * C) {
+            for (int c = a.chunk_base[s]; c < a.chunk_base[s + 1]; ++c) {
+                const float2 p = a.part[(int64_t)c * 2 * FCM_MAX_CLUSTERS + lane];
+                mine = df_merge(mine, DF{p.x, p.y});
             }
-            sh.tot[b] = t;
         }
-        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < 2 * C; ++q)
+            tot[q] = DF{__shfl_sync(0xffffffffu, mine.hi, q), __shfl_sync(0xffffffffu, mine.lo, q)};
     } else {
-        float um0[C];
-        membership<C, MK>((float)b, v0, m, inv_m1, up, um0);
-        const float hh = (float)cnt, hl = (float)((double)cnt - (double)hh);
-        DF acc[2 * C];
+        float acc[2 * C];
 #pragma unroll
-        for (int j = 0; j < C; ++j) {
-            acc[j] = weighted(um0[j] * (float)b, hh, hl);
-            acc[C + j] = weighted(um0[j], hh, hl);
+        for (int q = 0; q < 2 * C; ++q) acc[q] = 0.0f;
+#pragma unroll
+        for (int t = 0; t < WB; ++t) {
+            const float b = (float)(lane + 32 * t);
+            float um[C];
+            membership<C, MK>(b, v0, m, inv_m1, up[t], um);
+#pragma unroll
+            for (int j = 0; j < C; ++j) {
+                acc[j] = fmaf(cnt[t], um[j] * b, acc[j]);
+                acc[C + j] = fmaf(cnt[t], um[j], acc[C + j]);
+            }
         }
-        block_df_sums<C>(sh, acc);
+#pragma unroll
+        for (int q = 0; q < 2 * C; ++q) tot[q] = DF{acc[q], 0.0f};
+        warp_sum_df_n<2 * C>(tot);
     }
-    if (b < C) {
-        const DF den = sh.tot[C + b];
-        if (den.hi > 0.0f) {
-            const DF q = df_div(sh.tot[b], den);
-            sh.v1[b] = q.hi;
-            sh.v164[b] = (double)q.hi + (double)q.lo;
-        } else {
-            sh.v1[b] = v0[b];  // an empty cluster keeps V^0, or 0 from a U^0
-            sh.v164[b] = v0[b];
-            atomicOr(&sh.empty, 1);
-        }
-    }
-    __syncthreads();
     float v[C];
+    DF v64[C];
+    int flags = 0;
 #pragma unroll
-    for (int j = 0; j < C; ++j) v[j] = sh.v1[j];
-    double v64 = b < C ? sh.v164[b] : 0.0;
-    int flags = sh.empty ? FCM_FLAG_EMPTY_CLUSTER : 0;
+    for (int j = 0; j < C; ++j) {
+        if (tot[C + j].hi > 0.0f) {
+            v64[j] = df_div(tot[j], tot[C + j]);
+            v[j] = v64[j].hi;
+        } else {
+            v[j] = v0[j];  // an empty cluster keeps V^0, or 0 from a U^0
+            v64[j] = DF{v0[j], 0.0f};
+            flags = FCM_FLAG_EMPTY_CLUSTER;
+        }
+    }
     float* T = a.table + (int64_t)r * 256 * FCM_MAX_CLUSTERS;
 
     // ---- the first stopping quantity, from U^0 ----
@@ -300,19 +269,23 @@ __device__ __noinline__ void solve_run(const BinArgs& a, int r, const BinRun& ru
         if (a.phase == 0) {
             // U^1 per grey level, kept for pass B; the recorded pixel of each
             // grey level gives a lower bound of delta_1
-            float u1[C], um1[C];
-            membership<C, MK>((float)b, v, m, inv_m1, u1, um1);
-#pragma unroll
-            for (int j = 0; j < C; ++j) T[b * FCM_MAX_CLUSTERS + j] = u1[j];
             float lb = 0.0f;
-            const int rp = a.rep[(int64_t)s * 256 + b];
-            if (rp >= 0) {
 #pragma unroll
-                for (int j = 0; j < C; ++j) lb = fmaxf(lb, fabsf(u1[j] - __ldg(d.U0 + (int64_t)j * d.n + rp)));
+            for (int t = 0; t < WB; ++t) {
+                const int b = lane + 32 * t;
+                float u1[C], um1[C];
+                membership<C, MK>((float)b, v, m, inv_m1, u1, um1);
+#pragma unroll
+                for (int j = 0; j < C; ++j) T[b * FCM_MAX_CLUSTERS + j] = u1[j];
+                const int rp = a.rep[(int64_t)s * 256 + b];
+                if (rp >= 0) {
+#pragma unroll
+                    for (int j = 0; j < C; ++j) lb = fmaxf(lb, fabsf(u1[j] - __ldg(d.U0 + (int64_t)j * d.n + rp)));
+                }
             }
-            lb = block_max(sh, lb);
+            lb = warp_max(lb);
             if (!(lb >= d.eps) || d.max_iter == 1) {
-                if (b == 0) a.need_b[r] = 1;  // pass B takes delta_1 over every pixel; S1 resumes
+                if (lane == 0) a.need_b[r] = 1;  // pass B takes delta_1 over every pixel; S1 resumes
                 return;
             }
             d1 = lb;  // proves delta_1 >= eps: the run goes on to iteration 2
@@ -322,27 +295,30 @@ __device__ __noinline__ void solve_run(const BinArgs& a, int r, const BinRun& ru
     }
 
     // ---- iterations on the bins ----
-    float u[C];
     int k, status;
     float delta;
-    solve_bins<C, MK>(sh.sc, cnt, from_u, d1, v, up, u, v64, m, inv_m1, d.eps, d.max_iter, flags, k, status, delta);
+    DF J;
+    solve_bins_warp<C, MK>(cnt, from_u, d1, v, v64, up, m, inv_m1, d.eps, d.max_iter, flags, k, status, delta, J);
 #pragma unroll
-    for (int j = 0; j < C; ++j) T[b * FCM_MAX_CLUSTERS + j] = u[j];
-    if (b < C) {
-        if (run.write_u) d.V[b] = v[b];
-        res.V64[b] = v64;
-    }
-    if (b == 0) {
+    for (int t = 0; t < WB; ++t)
+#pragma unroll
+        for (int j = 0; j < C; ++j) T[(lane + 32 * t) * FCM_MAX_CLUSTERS + j] = up[t][j];
+#pragma unroll
+    for (int j = 0; j < C; ++j)
+        if (lane == j) {
+            if (run.write_u) d.V[j] = v[j];
+            res.V64[j] = (double)v64[j].hi + (double)v64[j].lo;
+        }
+    if (lane == 0) {
         res.iters = k;
         res.status = status;
         res.flags = flags;
         res.delta = (double)delta;
-        res.J = (double)sh.sc.tot[2 * C].hi + (double)sh.sc.tot[2 * C].lo;
+        res.J = (double)J.hi + (double)J.lo;
     }
 }
 
-__global__ void __launch_bounds__(BNT) k_bins_solve(BinArgs a) {
-    __shared__ SolveShared sh;
+__global__ void __launch_bounds__(SNT) k_bins_solve(BinArgs a) {
     const int r = blockIdx.x;
     if (r >= a.n_runs) return;
     if (a.phase == 1 && !a.need_b[r]) return;
@@ -351,10 +327,10 @@ __global__ void __launch_bounds__(BNT) k_bins_solve(BinArgs a) {
 #define FCM_BINS_S(CC)                                                                   \
     case CC:                                                                             \
         switch (d.mk) {                                                                  \
-            case M_TWO: solve_run<CC, M_TWO>(a, r, run, d, sh); break;                   \
-            case M_THREE: solve_run<CC, M_THREE>(a, r, run, d, sh); break;               \
-            case M_ONE_HALF: solve_run<CC, M_ONE_HALF>(a, r, run, d, sh); break;         \
-            default: solve_run<CC, M_GENERIC>(a, r, run, d, sh); break;                  \
+            case M_TWO: solve_run<CC, M_TWO>(a, r, run, d); break;                       \
+            case M_THREE: solve_run<CC, M_THREE>(a, r, run, d); break;                   \
+            case M_ONE_HALF: solve_run<CC, M_ONE_HALF>(a, r, run, d); break;             \
+            default: solve_run<CC, M_GENERIC>(a, r, run, d); break;                      \
         }                                                                                \
         break;
     switch (d.C) {
@@ -605,10 +581,10 @@ cudaError_t launch_bins(const BinArgs& a0, bool write_any, cudaStream_t s) {
     BinArgs a = a0;
     a.phase = 0;
     if (a.n_chunks > 0) k_bins_pass_a<<<a.n_chunks, BNT, 0, s>>>(a);
-    k_bins_solve<<<a.n_runs, BNT, 0, s>>>(a);
+    k_bins_solve<<<a.n_runs, SNT, 0, s>>>(a);
     if (a.n_chunks > 0) k_bins_pass_b<<<a.n_chunks, BNT, 0, s>>>(a);
     a.phase = 1;
-    k_bins_solve<<<a.n_runs, BNT, 0, s>>>(a);
+    k_bins_solve<<<a.n_runs, SNT, 0, s>>>(a);
     if (write_any && a.n_chunks > 0) k_bins_pass_c<<<a.n_chunks, BNT, 0, s>>>(a);
     return cudaGetLastError();
 }

@@ -291,6 +291,23 @@ __device__ __forceinline__ DF warp_sum_df(DF d) {
     return d;
 }
 
+// N warp-wide double-float sums at once: every level of the xor tree issues
+// the shuffles of all N sums before their merges, so the N chains of five
+// dependent levels overlap instead of running one after another. Each sum is
+// the same as warp_sum_df's (same operands, same order).
+template <int N>
+__device__ __forceinline__ void warp_sum_df_n(DF (&d)[N]) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        DF e[N];
+#pragma unroll
+        for (int q = 0; q < N; ++q) e[q] = DF{__shfl_xor_sync(0xffffffffu, d[q].hi, o), __shfl_xor_sync(0xffffffffu, d[q].lo, o)};
+#pragma unroll
+        for (int q = 0; q < N; ++q) d[q] = (lane & o) ? df_merge(e[q], d[q]) : df_merge(d[q], e[q]);
+    }
+}
+
 __device__ __forceinline__ float warp_sum(float v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);

@@ -1,6 +1,6 @@
 // Algorithm 1 (arXiv:1601.00072, Sec. 2.1) on the 256-bin grey-level
 // histogram: the loop of the histogram-domain run (brFCM, cited in Sec. 3),
-// shared by the single-image kernel and the batch kernel (one CTA per slice).
+// shared by the single-image kernel and the batch kernels (one warp per run).
 //
 // Under Eq. 4 a pixel's memberships depend only on its grey level, so the
 // center sums of Eq. 3 and J of Eq. 1 are sums over bins weighted by their
@@ -12,119 +12,78 @@
 
 namespace fcm {
 
-constexpr int HNT = 256;  // threads of a bin-solver CTA: thread b holds grey level b
+constexpr int HNT = 256;  // threads of the pixel-pass CTAs
 
 __device__ __forceinline__ bool grey_level(float v) {
     return v >= 0.0f && v <= 255.0f && v == rintf(v);  // false for NaN
 }
 
-// w * (hh + hl) as a double-float pair: the exact product w * hh (TwoProd by
-// FMA) plus the small w * hl.
-__device__ __forceinline__ DF weighted(float w, float hh, float hl) {
-    const float p = w * hh;
-    const float e = fmaf(w, hh, -p);
-    DF d{p, 0.0f};
-    df_add(d, fmaf(w, hl, e));
-    return d;
-}
+// The loop runs in one warp: lane l holds grey levels l + 32 t, t < WB. A
+// lane adds its eight bins' terms in FP32, then a double-float xor tree over
+// the warp gives every lane the same totals, so every lane forms V^{k+1}
+// (double-float quotients) itself: no block barrier, and a CTA of 32 threads
+// per run lets the many runs of a batch share each SM.
+constexpr int WB = 256 / 32;
 
-// Shared scratch of the bin solver, sized for FCM_MAX_CLUSTERS.
-struct BinScratch {
-    DF wtot[HNT / 32][2 * FCM_MAX_CLUSTERS + 1];
-    float wmax[HNT / 32];
-    DF tot[2 * FCM_MAX_CLUSTERS + 1];  // after the solve: tot[2C] = J_k
-    float s_v[FCM_MAX_CLUSTERS], s_delta;
-    double s_v64[FCM_MAX_CLUSTERS];
-    int s_empty;
-};
-
-// Iterations k = 1, 2, ... of Algorithm 1 on the bins, in one CTA of HNT
-// threads; thread b holds grey level b and its pixel count cnt.
-//   v     in: V^1 (the same in every thread); out: V^k of the returned U^k.
-//   up    the bin's U^0 when the run started from centers (from_u false); a
-//         run from memberships takes its first stopping quantity d1 from the
-//         pass over the pixels instead.
-//   u     out: the bin's U^k.
-//   v64   threads j < C: in, the quotient behind V^1_j; out, behind V^k_j.
-// Sums over the bins run in compensated FP32 (per-bin exact products,
-// double-float warp trees, the eight warp totals merged in a fixed order by
-// warp 0); an empty cluster keeps its center and sets the flag.
+// Iterations k = 1, 2, ... of Algorithm 1 on the bins of one run.
+//   cnt   the pixel counts of the lane's bins (as floats).
+//   v     in: V^1; out: V^k of the returned U^k. v64: the double-float
+//         quotients behind v (in and out).
+//   up    in: the bins' U^0 when the run started from centers (from_u
+//         false); out: U^k. A run from memberships takes its first stopping
+//         quantity d1 from the pixels instead.
+//   J     out: J_k (Eq. 1) as a double-float.
 template <int C, int MK>
-__device__ __forceinline__ void solve_bins(BinScratch& sc, unsigned long long cnt, bool from_u, float d1,
-                                           float (&v)[C], float (&up)[C], float (&u)[C], double& v64, float m,
-                                           float inv_m1, float eps, int max_iter, int& flags, int& k_out,
-                                           int& status_out, float& delta_out) {
+__device__ __forceinline__ void solve_bins_warp(const float (&cnt)[WB], bool from_u, float d1, float (&v)[C],
+                                                DF (&v64)[C], float (&up)[WB][C], float m, float inv_m1, float eps,
+                                                int max_iter, int& flags, int& k_out, int& status_out,
+                                                float& delta_out, DF& J) {
     constexpr int S = 2 * C + 1;
-    const int b = threadIdx.x, lane = b & 31, warp = b >> 5;
-    const bool present = cnt > 0ull;
-    // the count as an unevaluated float pair (exact below 2^48)
-    const float hh = (float)cnt, hl = (float)((double)cnt - (double)hh);
-    float um[C];
-    int status = FCM_NOT_CONVERGED, k = 1;
+    const int lane = threadIdx.x & 31;
+    int status = FCM_NOT_CONVERGED, k;
     float delta = 0.0f;
     for (k = 1;; ++k) {
-        const float Ji = membership<C, MK>((float)b, v, m, inv_m1, u, um);
-        DF s[S];
+        float acc[S];
+#pragma unroll
+        for (int q = 0; q < S; ++q) acc[q] = 0.0f;
         float mx = 0.0f;
+        const bool first_from_u = from_u && k == 1;
 #pragma unroll
-        for (int j = 0; j < C; ++j) {
-            s[j] = weighted(um[j] * (float)b, hh, hl);
-            s[C + j] = weighted(um[j], hh, hl);
-            if (present && !(from_u && k == 1)) mx = fmaxf(mx, fabsf(u[j] - up[j]));
+        for (int t = 0; t < WB; ++t) {
+            const float b = (float)(lane + 32 * t);
+            float u[C], um[C];
+            const float Ji = membership<C, MK>(b, v, m, inv_m1, u, um);
+#pragma unroll
+            for (int j = 0; j < C; ++j) {
+                acc[j] = fmaf(cnt[t], um[j] * b, acc[j]);
+                acc[C + j] = fmaf(cnt[t], um[j], acc[C + j]);
+                if (cnt[t] > 0.0f && !first_from_u) mx = fmaxf(mx, fabsf(u[j] - up[t][j]));
+                up[t][j] = u[j];
+            }
+            acc[2 * C] = fmaf(cnt[t], Ji, acc[2 * C]);
         }
-        s[2 * C] = weighted(Ji, hh, hl);
+        DF tot[S];
 #pragma unroll
-        for (int q = 0; q < S; ++q) s[q] = warp_sum_df(s[q]);
+        for (int q = 0; q < S; ++q) tot[q] = DF{acc[q], 0.0f};
+        warp_sum_df_n<S>(tot);
         mx = warp_max(mx);
-        if (lane == 0) {
-#pragma unroll
-            for (int q = 0; q < S; ++q) sc.wtot[warp][q] = s[q];
-            sc.wmax[warp] = mx;
-        }
-        __syncthreads();
-        if (warp == 0) {
-            // lane q merges sum q over the warps, in warp order
-            if (lane < S) {
-                DF t = sc.wtot[0][lane];
-                for (int w = 1; w < HNT / 32; ++w) t = df_merge(t, sc.wtot[w][lane]);
-                sc.tot[lane] = t;
-            }
-            float dm = lane < HNT / 32 ? sc.wmax[lane] : 0.0f;
-            dm = warp_max(dm);
-            __syncwarp();
-            if (lane == 0) sc.s_delta = (from_u && k == 1) ? d1 : dm;
-            // V^{k+1} (Eq. 3), computed by lane j; an empty cluster keeps v_j
-            bool empty = false;
-            if (lane < C) {
-                const DF den = sc.tot[C + lane];
-                if (den.hi > 0.0f) {
-                    const DF q = df_div(sc.tot[lane], den);
-                    sc.s_v[lane] = q.hi;
-                    sc.s_v64[lane] = (double)q.hi + (double)q.lo;
-                } else {
-                    sc.s_v[lane] = v[lane];
-                    sc.s_v64[lane] = v64;
-                    empty = true;
-                }
-            }
-            const unsigned em = __ballot_sync(0xffffffffu, empty);
-            if (lane == 0) sc.s_empty = em != 0u;
-        }
-        __syncthreads();
-        delta = sc.s_delta;
+        delta = first_from_u ? d1 : mx;
+        J = tot[2 * C];
         if (delta < eps) {
             status = FCM_OK;
             break;
         }
         if (k >= max_iter) break;
+        // V^{k+1} (Eq. 3); an empty cluster keeps v_j
 #pragma unroll
         for (int j = 0; j < C; ++j) {
-            up[j] = u[j];
-            v[j] = sc.s_v[j];
+            if (tot[C + j].hi > 0.0f) {
+                v64[j] = df_div(tot[j], tot[C + j]);
+                v[j] = v64[j].hi;
+            } else {
+                flags |= FCM_FLAG_EMPTY_CLUSTER;
+            }
         }
-        if (b < C) v64 = sc.s_v64[b];
-        if (sc.s_empty) flags |= FCM_FLAG_EMPTY_CLUSTER;
-        __syncthreads();  // s_v and the totals are reused by the next iteration
     }
     k_out = k;
     status_out = status;

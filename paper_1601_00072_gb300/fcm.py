@@ -228,6 +228,38 @@ class FCM:
         return FCMResult(U=U, V=V, iters=rep.iters, status=st, delta=rep.delta, J=rep.J,
                          V64=np.array(rep.V64[:C]), flags=rep.flags, launches=rep.launches, trace=tr)
 
+    def init_dirichlet(self, n: int, C: int, seed: int, U=None):
+        """The seeded random U^0 of Algorithm 1 step 2, drawn on the device
+        (``fcm_init_dirichlet``) into ``U`` [C, n] (allocated when None)."""
+        import torch
+        if U is None:
+            U = torch.empty((C, n), dtype=torch.float32, device=torch.device("cuda", self.device))
+        if _numel(U) != C * n:
+            raise ValueError("U must hold C*n floats")
+        self._bind_stream()
+        _lib.check(self._lib.fcm_init_dirichlet(self._h, int(n), int(C), int(seed), _ptr(U)), self._h)
+        return U
+
+    def run_seeded(self, x, C: int, m: float = 2.0, eps: float = 1e-5, max_iter: int = 300, *, seed: int,
+                   U=None, V=None, raise_on_error: bool = True) -> FCMResult:
+        """Algorithm 1 from the seeded random start drawn on the device
+        (``fcm_run_seeded``); ``U`` receives U^k (allocated when None)."""
+        import torch
+        n = _numel(x)
+        dev = torch.device("cuda", self.device)
+        if U is None:
+            U = torch.empty((C, n), dtype=torch.float32, device=dev)
+        if V is None:
+            V = torch.empty(C, dtype=torch.float32, device=dev)
+        rep = _lib.fcm_report()
+        self._bind_stream()
+        st = self._lib.fcm_run_seeded(self._h, _ptr(x), n, int(C), float(m), float(eps), int(max_iter), int(seed),
+                                      _ptr(U), _ptr(V), 0, ctypes.byref(rep))
+        if raise_on_error:
+            _lib.check(st, self._h)
+        return FCMResult(U=U, V=V, iters=rep.iters, status=st, delta=rep.delta, J=rep.J,
+                         V64=np.array(rep.V64[:C]), flags=rep.flags, launches=rep.launches, trace=None)
+
     def run_stream(self, xs, C: int, m: float = 2.0, eps: float = 1e-5, max_iter: int = 300, *,
                    U0s=None, Us=None, V=None, recompute: bool = False,
                    raise_on_error: bool = True) -> list[FCMResult]:
@@ -426,12 +458,12 @@ class FCM:
             s.init = "V" if modes[i] == _lib.FCM_INIT_V else "U"
             s.V0_warm = V0[i, :s.C].copy() if warm else None
 
-    def _batch_opts(self, tune, retune, graph):
+    def _batch_opts(self, tune, retune, graph, presolve=False):
         return ((0 if tune else _lib.FCM_BATCH_NO_TUNE) | (_lib.FCM_BATCH_RETUNE if retune else 0)
-                | (0 if graph else _lib.FCM_BATCH_NO_GRAPH))
+                | (0 if graph else _lib.FCM_BATCH_NO_GRAPH) | (_lib.FCM_BATCH_PRESOLVE if presolve else 0))
 
     def run_batched(self, slices, tune: bool = True, retune: bool = False, graph: bool = True,
-                    raise_on_error: bool = False, read_back: bool = True) -> int:
+                    raise_on_error: bool = False, read_back: bool = True, presolve: bool = False) -> int:
         """Algorithm 1 on every slice in one persistent launch (see
         ``fcm_run_batched``). Fills each Slice's U, V and result fields and
         returns the aggregate status. With a ``Batch`` and ``read_back=False``
@@ -439,7 +471,8 @@ class FCM:
         ``batch.read_back()``; U and V are written either way."""
         b = _as_batch(slices)
         self._bind_stream()
-        st = self._lib.fcm_run_batched(self._h, self._arr_ptr(b.arr), len(b), self._batch_opts(tune, retune, graph))
+        st = self._lib.fcm_run_batched(self._h, self._arr_ptr(b.arr), len(b),
+                                       self._batch_opts(tune, retune, graph, presolve))
         if st in (_lib.FCM_ERR_INVALID_ARG, _lib.FCM_ERR_CUDA, _lib.FCM_ERR_OOM) or raise_on_error:
             _lib.check(st, self._h)
         if read_back or not isinstance(slices, Batch):

@@ -19,6 +19,9 @@ images here stand in for it with the same structure:
 * ``dirichlet_u0``  the random initial membership of Algorithm 1 step 2: a
   per-pixel uniform Dirichlet(1, ..., 1) drawn as normalised -ln(U(0, 1])
   in FP64 and stored as FP32, cluster-major ``U0[j, i]``.
+* ``philox_dirichlet_u0``  the same distribution from the counter-based
+  generator Philox4x32-10, the definition the library's on-device start
+  (``fcm_init_dirichlet``) implements on its own side.
 
 Every draw is keyed by a tuple of integers through ``numpy.random.SeedSequence``
 so that the same key gives the same array on any machine.
@@ -270,3 +273,55 @@ def single_image(name: str):
     x = img.reshape(-1)
     C = 4
     return x, lab.reshape(-1), dirichlet_u0(useed, C, x.size), C
+
+
+# ---------------------------------------------------------------------------
+# Counter-based random initial membership (the library's on-device start)
+# ---------------------------------------------------------------------------
+
+PHILOX_M0, PHILOX_M1 = 0xD2511F53, 0xCD9E8D57   # round multipliers
+PHILOX_W0, PHILOX_W1 = 0x9E3779B9, 0xBB67AE85   # key increments (Weyl sequence)
+
+
+def philox4x32_10(ctr, key):
+    """Philox4x32-10 (Salmon, Moraes, Dror and Shaw, "Parallel random numbers:
+    as easy as 1, 2, 3", SC'11): ten rounds on a 128-bit counter ``ctr`` (four
+    uint32 arrays) under a 64-bit key ``(k0, k1)``. A round multiplies words 0
+    and 2 by the two multipliers (64-bit products), and gives
+    (hi1 ^ c1 ^ k0, lo1, hi0 ^ c3 ^ k1, lo0); the key is bumped by the two
+    increments between rounds. Returns four uint32 arrays."""
+    mask = np.uint64(0xFFFFFFFF)
+    c = [np.asarray(v, dtype=np.uint64) & mask for v in ctr]
+    k0, k1 = np.uint64(key[0]) & mask, np.uint64(key[1]) & mask
+    for r in range(10):
+        if r:
+            k0 = (k0 + np.uint64(PHILOX_W0)) & mask
+            k1 = (k1 + np.uint64(PHILOX_W1)) & mask
+        p0 = c[0] * np.uint64(PHILOX_M0)
+        p1 = c[2] * np.uint64(PHILOX_M1)
+        c = [(p1 >> np.uint64(32)) ^ c[1] ^ k0, p1 & mask, (p0 >> np.uint64(32)) ^ c[3] ^ k1, p0 & mask]
+    return [v.astype(np.uint32) for v in c]
+
+
+def philox_dirichlet_u0(seed: int, C: int, n: int) -> np.ndarray:
+    """Uniform Dirichlet(1, ..., 1) membership per pixel, FP32 ``[C, n]``, from
+    Philox4x32-10 — the definition the library's on-device start implements.
+
+    Pixel i draws counter (i mod 2^32, i div 2^32, b, 0) for blocks b = 0, 1
+    under key (seed mod 2^32, seed div 2^32); cluster j takes word j mod 4 of
+    block j div 4. A word w gives r = (2 floor(w / 512) + 1) / 2^24 in (0, 1),
+    E_j = -ln r_j (standard exponential), u_j = E_j / sum_k E_k (FP64, then
+    rounded to FP32)."""
+    seed = int(seed)
+    key = (seed & 0xFFFFFFFF, (seed >> 32) & 0xFFFFFFFF)
+    out = np.empty((C, n), dtype=np.float32)
+    chunk = 1 << 22
+    for s in range(0, n, chunk):
+        i = np.arange(s, min(n, s + chunk), dtype=np.uint64)
+        lo, hi = i & np.uint64(0xFFFFFFFF), i >> np.uint64(32)
+        words = []
+        for b in range((C + 3) // 4):
+            words += philox4x32_10([lo, hi, np.full(i.size, b, dtype=np.uint64), np.zeros(i.size, np.uint64)], key)
+        E = np.stack([-np.log((2.0 * (w >> np.uint32(9)).astype(np.float64) + 1.0) / 16777216.0) for w in words[:C]])
+        out[:, s:s + i.size] = (E / E.sum(axis=0, keepdims=True)).astype(np.float32)
+    return out

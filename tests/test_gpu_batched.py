@@ -12,7 +12,7 @@ import pytest
 
 import oracle
 import phantom
-from parity import (assert_converged_within, assert_within, center_err, eps32, permuted_report,
+from parity import (WIDE_CAP, assert_converged_within, assert_within, center_err, eps32, permuted_report,
                     precision_report, sensitivity, trajectory_sensitive)
 
 pytestmark = pytest.mark.gpu
@@ -276,13 +276,39 @@ def test_full_512_slice_batch_matches_oracle(fcm, plan):
     finally:
         fcm.set_batched_plan()
     assert st in (0, 1)
-    worst = {"center_rel_err": 0.0, "max_abs_dU": 0.0, "label_agreement": 1.0, "sensitive": 0}
+    worst = {"center_rel_err": 0.0, "max_abs_dU": 0.0, "label_agreement": 1.0}
+    sensitive = []
     for i, (s, (x, u0, V0)) in enumerate(zip(slices, host)):
         rep, _ = check_slice(s, x, u0, V0, 2.0)
         assert_slice(rep, f"slice {i} (n={s.x.numel()}, C={s.C})")
         worst["center_rel_err"] = max(worst["center_rel_err"], rep["center_rel_err"])
         worst["max_abs_dU"] = max(worst["max_abs_dU"], rep["max_abs_dU"])
         worst["label_agreement"] = min(worst["label_agreement"], rep["label_agreement"])
-        worst["sensitive"] += rep["conditioning"] == "sensitive"
+        if rep["conditioning"] == "sensitive":
+            sensitive.append((i, {k: rep[k] for k in ("center_rel_err", "max_abs_dU")}, rep["tolerance_applied"]))
     print("worst over 512 slices:", worst, fcm.batched_plan())
-    assert worst["sensitive"] <= 10  # trajectory-sensitive slices, judged on converged results
+    print(f"judged on their converged result (trajectory-sensitive, at most {WIDE_CAP} each): {sensitive}")
+    # the oracle marks 13 of the 512 slices sensitive; 2 need the exception
+    # under every plan measured
+    assert len(sensitive) <= 3
+
+
+@pytest.mark.parametrize("plan", [None, dict(schedule="teams", block=256, tile=100),
+                                  dict(block=256, cluster=4, big=16384)], ids=plan_id)
+def test_presolved_batch_matches_oracle(fcm, plan):
+    """FCM_BATCH_PRESOLVE orders (and, for teams, splits) the work by each
+    slice's iteration count from a run on its histogram; the per-pixel runs
+    and their results are those of any other plan, and the caller's
+    iters_hint fields stay as they were."""
+    from paper_1601_00072_gb300.fcm import Batch
+    slices, host = make_batch(range(64, 96))
+    batch = Batch(slices)
+    if plan is not None:
+        fcm.set_batched_plan(**plan)
+    try:
+        st = fcm.run_batched(batch, presolve=True)
+    finally:
+        fcm.set_batched_plan()
+    assert st in (0, 1)
+    assert_batch(slices, host)
+    assert not batch.arr["iters_hint"].any()

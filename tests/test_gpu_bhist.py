@@ -58,7 +58,7 @@ def test_full_512_slice_batch(fcm):
         assert s.status in (0, 1), (i, s.status)
         assert_slice(rep, f"slice {i} (n={s.x.numel()}, C={s.C})")
         sensitive += rep["conditioning"] == "sensitive"
-    assert sensitive <= 10
+    assert sensitive <= 3  # of the 13 slices the oracle marks trajectory-sensitive
 
 
 def test_ragged_and_tiny_slices(fcm):
