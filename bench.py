@@ -55,6 +55,8 @@ UNIT = "pixel-iter/s"
 PROFILE = os.path.join(ROOT, "profiles", "fcm_pass_volume256.md")
 KERNEL_SOURCES = ["paper_1601_00072_gb300/csrc/fcm_single_inst.cu",
                   "paper_1601_00072_gb300/csrc/fcm_device.cuh",
+                  "paper_1601_00072_gb300/csrc/fcm_exchange.cuh",
+                  "paper_1601_00072_gb300/csrc/fcm_df.cuh",
                   "paper_1601_00072_gb300/csrc/fcm_tma.cuh",
                   "paper_1601_00072_gb300/csrc/fcm_internal.h"]
 
@@ -577,7 +579,7 @@ def bench_batched(h, dev, steps, warmup, plan=None, keep_results=False, n_slices
         "plan": plan_used,
         "plan_warm": plan_warm,
         "histogram_domain": {
-            "kernel": "k_bins_*: pixel passes in 16,384-pixel chunks over the whole GPU (histogram and V^1 "
+            "kernel": "k_bins_*: pixel passes in 8,192-pixel chunks over the whole GPU (histogram and V^1 "
                       "sums; the first stop over every pixel only where a bound cannot decide it; U by lookup), "
                       "the iterations on 256 bins, one CTA per slice",
             "images_per_s": n_img / (ms_hist / 1e3), "ms": ms_hist, "speedup_vs_cold": ms_cold / ms_hist,
@@ -794,6 +796,8 @@ def bench_ours(args):
                      "roofline": issue_roofline("profiles/fcm_recompute_volume256.md",
                                                 ["paper_1601_00072_gb300/csrc/fcm_recompute_inst.cu",
                                                  "paper_1601_00072_gb300/csrc/fcm_device.cuh",
+                                                 "paper_1601_00072_gb300/csrc/fcm_exchange.cuh",
+                                                 "paper_1601_00072_gb300/csrc/fcm_df.cuh",
                                                  "paper_1601_00072_gb300/csrc/fcm_tma.cuh",
                                                  "paper_1601_00072_gb300/csrc/fcm_internal.h"],
                                                 rms, rr.iters, clocks.get("sm_max_mhz"))}

@@ -438,7 +438,7 @@ int fcm_run_batched(fcm_handle h, fcm_slice* slices, int n_slices, int options);
 /*
  * fcm_run_batched_hist — the histogram-domain run (as fcm_run_hist: the
  * grey-level reduction of brFCM, cited in Sec. 3) for each slice of a batch
- * of 8-bit slices. The pixel passes are cut into chunks of 16,384 pixels,
+ * of 8-bit slices. The pixel passes are cut into chunks of 8,192 pixels,
  * one CTA each, over the whole GPU; the iterations run on each slice's 256
  * bins, one CTA per slice. A first pass builds every slice's histogram (and
  * from U^0 the sums of V^1); the first stopping quantity max_i |f(x_i, V^1)

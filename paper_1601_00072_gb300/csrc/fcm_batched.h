@@ -82,7 +82,7 @@ BatchKernel batched_kernel_512();
 // runs may share a slice's histogram (the warm-start judge solves each slice
 // from its U^0 and from the predicted centers); at most one run per slice
 // starts from U^0 and at most one writes the slice's U and V.
-constexpr int BIN_CHUNK = 16384;
+constexpr int BIN_CHUNK = 8192;
 
 enum BinInit : int {
     BIN_FROM_U = 0,      // U^0 of the slice descriptor

@@ -176,7 +176,8 @@ __global__ void __launch_bounds__(BNT) k_bins_pass_a(BinArgs a) {
 constexpr int SNT = 32;  // threads of a solve CTA: one warp, lane l holds grey levels l + 32 t
 
 template <int C, int MK>
-__device__ __noinline__ void solve_run(const BinArgs& a, int r, const BinRun& run, const SliceDesc& d) {
+__device__ __noinline__ void solve_run(const BinArgs& a, int r, const BinRun& run, const SliceDesc& d, float* s_cnt,
+                                       float* s_up) {
     const int s = run.slice, lane = threadIdx.x;
     const bool from_u = run.init == BIN_FROM_U;
     const float m = d.m, inv_m1 = d.inv_m1;
@@ -209,12 +210,11 @@ __device__ __noinline__ void solve_run(const BinArgs& a, int r, const BinRun& ru
         }
         return;
     }
-    float cnt[WB];
 #pragma unroll
-    for (int t = 0; t < WB; ++t) cnt[t] = (float)a.hist[(int64_t)s * 256 + lane + 32 * t];
+    for (int t = 0; t < WB; ++t) s_cnt[t * 32 + lane] = (float)a.hist[(int64_t)s * 256 + lane + 32 * t];
+    __syncwarp();
 
     // ---- V^1 (Eq. 3): from the chunk sums of pass A, or from the bins with U^0 = f(b, V^0) ----
-    float up[WB][C];
     DF tot[2 * C];
     if (from_u) {
         // lane q < 2C merges sum q over the slice's chunks, in chunk order
@@ -232,15 +232,16 @@ __device__ __noinline__ void solve_run(const BinArgs& a, int r, const BinRun& ru
         float acc[2 * C];
 #pragma unroll
         for (int q = 0; q < 2 * C; ++q) acc[q] = 0.0f;
-#pragma unroll
+#pragma unroll 1
         for (int t = 0; t < WB; ++t) {
-            const float b = (float)(lane + 32 * t);
-            float um[C];
-            membership<C, MK>(b, v0, m, inv_m1, up[t], um);
+            const float b = (float)(lane + 32 * t), c = s_cnt[t * 32 + lane];
+            float u[C], um[C];
+            membership<C, MK>(b, v0, m, inv_m1, u, um);
 #pragma unroll
             for (int j = 0; j < C; ++j) {
-                acc[j] = fmaf(cnt[t], um[j] * b, acc[j]);
-                acc[C + j] = fmaf(cnt[t], um[j], acc[C + j]);
+                s_up[up_at(t, j, lane)] = u[j];
+                acc[j] = fmaf(c, um[j] * b, acc[j]);
+                acc[C + j] = fmaf(c, um[j], acc[C + j]);
             }
         }
 #pragma unroll
@@ -270,7 +271,7 @@ __device__ __noinline__ void solve_run(const BinArgs& a, int r, const BinRun& ru
             // U^1 per grey level, kept for pass B; the recorded pixel of each
             // grey level gives a lower bound of delta_1
             float lb = 0.0f;
-#pragma unroll
+#pragma unroll 1
             for (int t = 0; t < WB; ++t) {
                 const int b = lane + 32 * t;
                 float u1[C], um1[C];
@@ -298,11 +299,11 @@ __device__ __noinline__ void solve_run(const BinArgs& a, int r, const BinRun& ru
     int k, status;
     float delta;
     DF J;
-    solve_bins_warp<C, MK>(cnt, from_u, d1, v, v64, up, m, inv_m1, d.eps, d.max_iter, flags, k, status, delta, J);
-#pragma unroll
+    solve_bins_warp<C, MK>(s_cnt, from_u, d1, v, v64, s_up, m, inv_m1, d.eps, d.max_iter, flags, k, status, delta, J);
+#pragma unroll 1
     for (int t = 0; t < WB; ++t)
 #pragma unroll
-        for (int j = 0; j < C; ++j) T[(lane + 32 * t) * FCM_MAX_CLUSTERS + j] = up[t][j];
+        for (int j = 0; j < C; ++j) T[(lane + 32 * t) * FCM_MAX_CLUSTERS + j] = s_up[up_at(t, j, lane)];
 #pragma unroll
     for (int j = 0; j < C; ++j)
         if (lane == j) {
@@ -319,6 +320,8 @@ __device__ __noinline__ void solve_run(const BinArgs& a, int r, const BinRun& ru
 }
 
 __global__ void __launch_bounds__(SNT) k_bins_solve(BinArgs a) {
+    __shared__ float s_cnt[WB * 32];                     // the run's pixel counts
+    __shared__ float s_up[WB * FCM_MAX_CLUSTERS * 32];   // the run's U^k per grey level (up_at)
     const int r = blockIdx.x;
     if (r >= a.n_runs) return;
     if (a.phase == 1 && !a.need_b[r]) return;
@@ -327,10 +330,10 @@ __global__ void __launch_bounds__(SNT) k_bins_solve(BinArgs a) {
 #define FCM_BINS_S(CC)                                                                   \
     case CC:                                                                             \
         switch (d.mk) {                                                                  \
-            case M_TWO: solve_run<CC, M_TWO>(a, r, run, d); break;                       \
-            case M_THREE: solve_run<CC, M_THREE>(a, r, run, d); break;                   \
-            case M_ONE_HALF: solve_run<CC, M_ONE_HALF>(a, r, run, d); break;             \
-            default: solve_run<CC, M_GENERIC>(a, r, run, d); break;                      \
+            case M_TWO: solve_run<CC, M_TWO>(a, r, run, d, s_cnt, s_up); break;          \
+            case M_THREE: solve_run<CC, M_THREE>(a, r, run, d, s_cnt, s_up); break;      \
+            case M_ONE_HALF: solve_run<CC, M_ONE_HALF>(a, r, run, d, s_cnt, s_up); break; \
+            default: solve_run<CC, M_GENERIC>(a, r, run, d, s_cnt, s_up); break;         \
         }                                                                                \
         break;
     switch (d.C) {

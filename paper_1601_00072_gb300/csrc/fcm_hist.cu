@@ -290,28 +290,31 @@ __global__ void __launch_bounds__(32) k_hist_solve(HistState* st, float* __restr
         const float hi = (float)q;
         v64[j] = DF{hi, (float)(q - (double)hi)};
     }
-    float cnt[WB];
-    float up[WB][C];
-#pragma unroll
+    __shared__ float s_cnt[WB * 32];
+    __shared__ float s_up[WB * FCM_MAX_CLUSTERS * 32];
+#pragma unroll 1
     for (int t = 0; t < WB; ++t) {
-        cnt[t] = (float)st->hist[lane + 32 * t];
+        s_cnt[t * 32 + lane] = (float)st->hist[lane + 32 * t];
         if (!FROM_U) {
-            float v0[C], um0[C];
+            float v0[C], u0[C], um0[C];
 #pragma unroll
             for (int j = 0; j < C; ++j) v0[j] = st->V0[j];
-            membership<C, MK>((float)(lane + 32 * t), v0, m, inv_m1, up[t], um0);
+            membership<C, MK>((float)(lane + 32 * t), v0, m, inv_m1, u0, um0);
+#pragma unroll
+            for (int j = 0; j < C; ++j) s_up[up_at(t, j, lane)] = u0[j];
         }
     }
+    __syncwarp();
     int flags = st->flags;
     int k, status;
     float delta;
     DF J;
-    solve_bins_warp<C, MK>(cnt, FROM_U, FROM_U ? __uint_as_float(st->d1bits) : 0.0f, v, v64, up, m, inv_m1, eps,
+    solve_bins_warp<C, MK>(s_cnt, FROM_U, FROM_U ? __uint_as_float(st->d1bits) : 0.0f, v, v64, s_up, m, inv_m1, eps,
                            max_iter, flags, k, status, delta, J);
-#pragma unroll
+#pragma unroll 1
     for (int t = 0; t < WB; ++t)
 #pragma unroll
-        for (int j = 0; j < C; ++j) table[(lane + 32 * t) * C + j] = up[t][j];
+        for (int j = 0; j < C; ++j) table[(lane + 32 * t) * C + j] = s_up[up_at(t, j, lane)];
     if (lane == 0) {
         st->iters = k;
         st->status = status;
