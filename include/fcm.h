@@ -30,7 +30,10 @@
  *   - Arithmetic: memberships and per-thread sums in FP32; the sums across
  *     threads and blocks (center numerators/denominators and J) in
  *     compensated FP32 (double-float, about 44 bits) or FP64, in a fixed
- *     order, so a run is deterministic.
+ *     order, so a run is deterministic. The histogram-domain entry points
+ *     form V^1 the same way from the pixels; their loop over the 256 bins
+ *     sums non-negative terms in FP32 within each warp (a fixed tree, at
+ *     most five roundings) and combines the warp totals in double-float.
  *   - Ownership: the caller owns x, U, V and every output array; the library
  *     never frees them. A handle owns its device workspace, CUDA graphs and
  *     autotuning cache, and frees them in fcm_destroy.

@@ -11,7 +11,7 @@
 // pixels of any slice, so a large slice is shared by many SMs):
 //   A  histogram, input checks, one pixel index per grey level, and the
 //      per-chunk sums of V^1 (Eq. 3) for slices started from U^0;
-//   S0 per run (one warp): V^1, then the first stopping quantity
+//   S0 per run (one CTA, a thread per grey level): V^1, then the first stopping quantity
 //      delta_1 = max_i |f(x_i, V^1) - U^0_i| is bounded from below by the
 //      recorded pixel of every grey level; when that bound already reaches
 //      eps, the first iteration cannot stop and the run proceeds on the bins;
@@ -21,9 +21,12 @@
 //   S1 the runs of B, with the exact delta_1;
 //   C  U^k by table lookup for the runs that write their slice.
 // The results are those of the exact algorithm: the bound only skips pass B
-// when it proves the stop decision it would feed. Sums run in FP32 over a few
-// pixels, then in compensated FP32 (double-float) per thread, warp, CTA and
-// chunk, merged in chunk order: the iterates do not depend on the schedule.
+// when it proves the stop decision it would feed. The pixel sums of V^1 run in
+// FP32 over a few pixels, then in compensated FP32 (double-float) per thread,
+// warp, CTA and chunk, merged in chunk order: the iterates do not depend on
+// the schedule. The bin loop sums 256 non-negative terms in FP32 within each
+// warp (a fixed tree, at most five roundings), then across the eight warps in
+// double-float.
 #include <cstring>
 #include <vector>
 
@@ -170,15 +173,15 @@ __global__ void __launch_bounds__(BNT) k_bins_pass_a(BinArgs a) {
 }
 
 // ---------------------------------------------------------------------------
-// Solve: one warp per run
+// Solve: one CTA per run, thread b holding grey level b
 // ---------------------------------------------------------------------------
 
-constexpr int SNT = 32;  // threads of a solve CTA: one warp, lane l holds grey levels l + 32 t
+constexpr int SNT = HNT;
 
 template <int C, int MK>
-__device__ __noinline__ void solve_run(const BinArgs& a, int r, const BinRun& run, const SliceDesc& d, float* s_cnt,
-                                       float* s_up) {
-    const int s = run.slice, lane = threadIdx.x;
+__device__ __noinline__ void solve_run(const BinArgs& a, int r, const BinRun& run, const SliceDesc& d,
+                                       BinScratch& sc, DF* s_tot) {
+    const int s = run.slice, b = threadIdx.x;
     const bool from_u = run.init == BIN_FROM_U;
     const float m = d.m, inv_m1 = d.inv_m1;
     SliceResult& res = a.results[r];
@@ -195,13 +198,11 @@ __device__ __noinline__ void solve_run(const BinArgs& a, int r, const BinRun& ru
     }
     if (bad) {
         // not a grey-level slice (or a bad U^0 / V^0): the status, and V = V^0
-#pragma unroll
-        for (int j = 0; j < C; ++j)
-            if (lane == j) {
-                if (run.write_u) d.V[j] = v0[j];
-                res.V64[j] = v0[j];
-            }
-        if (lane == 0) {
+        if (b < C) {
+            if (run.write_u) d.V[b] = v0[b];
+            res.V64[b] = v0[b];
+        }
+        if (b == 0) {
             res.iters = 0;
             res.status = FCM_ERR_BAD_INPUT;
             res.flags = 0;
@@ -210,56 +211,56 @@ __device__ __noinline__ void solve_run(const BinArgs& a, int r, const BinRun& ru
         }
         return;
     }
-#pragma unroll
-    for (int t = 0; t < WB; ++t) s_cnt[t * 32 + lane] = (float)a.hist[(int64_t)s * 256 + lane + 32 * t];
-    __syncwarp();
+    const float cnt = (float)a.hist[(int64_t)s * 256 + b];
+    int par = 0, flags = 0;
+    float v[C], up[C];
+    DF v64[C];
 
     // ---- V^1 (Eq. 3): from the chunk sums of pass A, or from the bins with U^0 = f(b, V^0) ----
-    DF tot[2 * C];
     if (from_u) {
-        // lane q < 2C merges sum q over the slice's chunks, in chunk order
-        DF mine{0.0f, 0.0f};
-        if (lane < 2 * C) {
+        // thread q < 2C merges sum q over the slice's chunks, in chunk order
+        if (b < 2 * C) {
+            DF mine{0.0f, 0.0f};
             for (int c = a.chunk_base[s]; c < a.chunk_base[s + 1]; ++c) {
-                const float2 p = a.part[(int64_t)c * 2 * FCM_MAX_CLUSTERS + lane];
+                const float2 p = a.part[(int64_t)c * 2 * FCM_MAX_CLUSTERS + b];
                 mine = df_merge(mine, DF{p.x, p.y});
             }
+            s_tot[b] = mine;
         }
+        __syncthreads();
 #pragma unroll
-        for (int q = 0; q < 2 * C; ++q)
-            tot[q] = DF{__shfl_sync(0xffffffffu, mine.hi, q), __shfl_sync(0xffffffffu, mine.lo, q)};
-    } else {
-        float acc[2 * C];
-#pragma unroll
-        for (int q = 0; q < 2 * C; ++q) acc[q] = 0.0f;
-#pragma unroll 1
-        for (int t = 0; t < WB; ++t) {
-            const float b = (float)(lane + 32 * t), c = s_cnt[t * 32 + lane];
-            float u[C], um[C];
-            membership<C, MK>(b, v0, m, inv_m1, u, um);
-#pragma unroll
-            for (int j = 0; j < C; ++j) {
-                s_up[up_at(t, j, lane)] = u[j];
-                acc[j] = fmaf(c, um[j] * b, acc[j]);
-                acc[C + j] = fmaf(c, um[j], acc[C + j]);
+        for (int j = 0; j < C; ++j) {
+            up[j] = 0.0f;
+            if (s_tot[C + j].hi > 0.0f) {
+                v64[j] = df_div(s_tot[j], s_tot[C + j]);
+                v[j] = v64[j].hi;
+            } else {
+                v[j] = v0[j];  // an empty cluster keeps 0 from a U^0
+                v64[j] = DF{v0[j], 0.0f};
+                flags = FCM_FLAG_EMPTY_CLUSTER;
             }
         }
+    } else {
+        float um[C], t[2 * C + 1], dummy;
+        DF tot[2 * C];
+        membership<C, MK>((float)b, v0, m, inv_m1, up, um);
 #pragma unroll
-        for (int q = 0; q < 2 * C; ++q) tot[q] = DF{acc[q], 0.0f};
-        warp_sum_df_n<2 * C>(tot);
-    }
-    float v[C];
-    DF v64[C];
-    int flags = 0;
+        for (int j = 0; j < C; ++j) {
+            t[j] = cnt * (um[j] * (float)b);
+            t[C + j] = cnt * um[j];
+        }
+        t[2 * C] = 0.0f;
+        block_sums<2 * C>(sc, par, t, tot, dummy);
 #pragma unroll
-    for (int j = 0; j < C; ++j) {
-        if (tot[C + j].hi > 0.0f) {
-            v64[j] = df_div(tot[j], tot[C + j]);
-            v[j] = v64[j].hi;
-        } else {
-            v[j] = v0[j];  // an empty cluster keeps V^0, or 0 from a U^0
-            v64[j] = DF{v0[j], 0.0f};
-            flags = FCM_FLAG_EMPTY_CLUSTER;
+        for (int j = 0; j < C; ++j) {
+            if (tot[C + j].hi > 0.0f) {
+                v64[j] = df_div(tot[j], tot[C + j]);
+                v[j] = v64[j].hi;
+            } else {
+                v[j] = v0[j];  // an empty cluster keeps V^0
+                v64[j] = DF{v0[j], 0.0f};
+                flags = FCM_FLAG_EMPTY_CLUSTER;
+            }
         }
     }
     float* T = a.table + (int64_t)r * 256 * FCM_MAX_CLUSTERS;
@@ -270,23 +271,21 @@ __device__ __noinline__ void solve_run(const BinArgs& a, int r, const BinRun& ru
         if (a.phase == 0) {
             // U^1 per grey level, kept for pass B; the recorded pixel of each
             // grey level gives a lower bound of delta_1
-            float lb = 0.0f;
-#pragma unroll 1
-            for (int t = 0; t < WB; ++t) {
-                const int b = lane + 32 * t;
-                float u1[C], um1[C];
-                membership<C, MK>((float)b, v, m, inv_m1, u1, um1);
+            float u1[C], um1[C], t[2], lb;
+            DF tot[1];
+            membership<C, MK>((float)b, v, m, inv_m1, u1, um1);
 #pragma unroll
-                for (int j = 0; j < C; ++j) T[b * FCM_MAX_CLUSTERS + j] = u1[j];
-                const int rp = a.rep[(int64_t)s * 256 + b];
-                if (rp >= 0) {
+            for (int j = 0; j < C; ++j) T[b * FCM_MAX_CLUSTERS + j] = u1[j];
+            t[0] = 0.0f;
+            t[1] = 0.0f;
+            const int rp = a.rep[(int64_t)s * 256 + b];
+            if (rp >= 0) {
 #pragma unroll
-                    for (int j = 0; j < C; ++j) lb = fmaxf(lb, fabsf(u1[j] - __ldg(d.U0 + (int64_t)j * d.n + rp)));
-                }
+                for (int j = 0; j < C; ++j) t[1] = fmaxf(t[1], fabsf(u1[j] - __ldg(d.U0 + (int64_t)j * d.n + rp)));
             }
-            lb = warp_max(lb);
+            block_sums<1>(sc, par, t, tot, lb);
             if (!(lb >= d.eps) || d.max_iter == 1) {
-                if (lane == 0) a.need_b[r] = 1;  // pass B takes delta_1 over every pixel; S1 resumes
+                if (b == 0) a.need_b[r] = 1;  // pass B takes delta_1 over every pixel; S1 resumes
                 return;
             }
             d1 = lb;  // proves delta_1 >= eps: the run goes on to iteration 2
@@ -299,18 +298,16 @@ __device__ __noinline__ void solve_run(const BinArgs& a, int r, const BinRun& ru
     int k, status;
     float delta;
     DF J;
-    solve_bins_warp<C, MK>(s_cnt, from_u, d1, v, v64, s_up, m, inv_m1, d.eps, d.max_iter, flags, k, status, delta, J);
-#pragma unroll 1
-    for (int t = 0; t < WB; ++t)
+    solve_bins<C, MK>(sc, par, cnt, from_u, d1, v, v64, up, m, inv_m1, d.eps, d.max_iter, flags, k, status, delta, J);
 #pragma unroll
-        for (int j = 0; j < C; ++j) T[(lane + 32 * t) * FCM_MAX_CLUSTERS + j] = s_up[up_at(t, j, lane)];
+    for (int j = 0; j < C; ++j) T[b * FCM_MAX_CLUSTERS + j] = up[j];
 #pragma unroll
     for (int j = 0; j < C; ++j)
-        if (lane == j) {
+        if (b == j) {
             if (run.write_u) d.V[j] = v[j];
             res.V64[j] = (double)v64[j].hi + (double)v64[j].lo;
         }
-    if (lane == 0) {
+    if (b == 0) {
         res.iters = k;
         res.status = status;
         res.flags = flags;
@@ -319,9 +316,9 @@ __device__ __noinline__ void solve_run(const BinArgs& a, int r, const BinRun& ru
     }
 }
 
-__global__ void __launch_bounds__(SNT) k_bins_solve(BinArgs a) {
-    __shared__ float s_cnt[WB * 32];                     // the run's pixel counts
-    __shared__ float s_up[WB * FCM_MAX_CLUSTERS * 32];   // the run's U^k per grey level (up_at)
+__global__ void __launch_bounds__(SNT, 2) k_bins_solve(BinArgs a) {
+    __shared__ BinScratch sc;
+    __shared__ DF s_tot[2 * FCM_MAX_CLUSTERS];
     const int r = blockIdx.x;
     if (r >= a.n_runs) return;
     if (a.phase == 1 && !a.need_b[r]) return;
@@ -330,10 +327,10 @@ __global__ void __launch_bounds__(SNT) k_bins_solve(BinArgs a) {
 #define FCM_BINS_S(CC)                                                                   \
     case CC:                                                                             \
         switch (d.mk) {                                                                  \
-            case M_TWO: solve_run<CC, M_TWO>(a, r, run, d, s_cnt, s_up); break;          \
-            case M_THREE: solve_run<CC, M_THREE>(a, r, run, d, s_cnt, s_up); break;      \
-            case M_ONE_HALF: solve_run<CC, M_ONE_HALF>(a, r, run, d, s_cnt, s_up); break; \
-            default: solve_run<CC, M_GENERIC>(a, r, run, d, s_cnt, s_up); break;         \
+            case M_TWO: solve_run<CC, M_TWO>(a, r, run, d, sc, s_tot); break;          \
+            case M_THREE: solve_run<CC, M_THREE>(a, r, run, d, sc, s_tot); break;      \
+            case M_ONE_HALF: solve_run<CC, M_ONE_HALF>(a, r, run, d, sc, s_tot); break; \
+            default: solve_run<CC, M_GENERIC>(a, r, run, d, sc, s_tot); break;         \
         }                                                                                \
         break;
     switch (d.C) {

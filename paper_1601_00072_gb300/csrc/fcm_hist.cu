@@ -11,7 +11,7 @@
 //
 // Per run: one pass over the pixels builds the histogram (and, from U^0, the
 // sums of V^1); with U^0 given, a second pass takes the first stopping
-// quantity against the pixels' U^0; one warp then iterates on the bins; a last
+// quantity against the pixels' U^0; one CTA then iterates on the bins; a last
 // pass writes U^k by table lookup. HBM traffic is 4 + 4C bytes per pixel for
 // each of the (up to) three passes instead of 4 + 8C per iteration.
 #include <cuda_runtime.h>
@@ -274,59 +274,50 @@ __global__ void __launch_bounds__(HNT) k_hist_delta1(const float* __restrict__ x
     }
 }
 
-// Algorithm 1 on the bins, one warp (solve_bins_warp: lane l holds grey
-// levels l + 32 t); V64 is formed once at the end.
+// Algorithm 1 on the bins, one CTA (solve_bins: thread b holds grey level b).
 template <int C, int MK, bool FROM_U>
-__global__ void __launch_bounds__(32) k_hist_solve(HistState* st, float* __restrict__ table, float m, float inv_m1,
-                                                  float eps, int max_iter) {
+__global__ void __launch_bounds__(HNT) k_hist_solve(HistState* st, float* __restrict__ table, float m, float inv_m1,
+                                                   float eps, int max_iter) {
+    __shared__ BinScratch sc;
     if (st->bad) return;
-    const int lane = threadIdx.x;
-    float v[C];
+    const int b = threadIdx.x;
+    float v[C], up[C];
     DF v64[C];
 #pragma unroll
     for (int j = 0; j < C; ++j) {
         v[j] = st->V[j];
         const double q = st->V64[j];
-        const float hi = (float)q;
-        v64[j] = DF{hi, (float)(q - (double)hi)};
+        v64[j] = DF{(float)q, (float)(q - (double)(float)q)};
+        up[j] = 0.0f;
     }
-    __shared__ float s_cnt[WB * 32];
-    __shared__ float s_up[WB * FCM_MAX_CLUSTERS * 32];
-#pragma unroll 1
-    for (int t = 0; t < WB; ++t) {
-        s_cnt[t * 32 + lane] = (float)st->hist[lane + 32 * t];
-        if (!FROM_U) {
-            float v0[C], u0[C], um0[C];
+    if (!FROM_U) {
+        float v0[C], um0[C];
 #pragma unroll
-            for (int j = 0; j < C; ++j) v0[j] = st->V0[j];
-            membership<C, MK>((float)(lane + 32 * t), v0, m, inv_m1, u0, um0);
-#pragma unroll
-            for (int j = 0; j < C; ++j) s_up[up_at(t, j, lane)] = u0[j];
-        }
+        for (int j = 0; j < C; ++j) v0[j] = st->V0[j];
+        membership<C, MK>((float)b, v0, m, inv_m1, up, um0);
     }
-    __syncwarp();
-    int flags = st->flags;
+    const float cnt = (float)st->hist[b];
+    int flags = st->flags, par = 0;
     int k, status;
     float delta;
     DF J;
-    solve_bins_warp<C, MK>(s_cnt, FROM_U, FROM_U ? __uint_as_float(st->d1bits) : 0.0f, v, v64, s_up, m, inv_m1, eps,
-                           max_iter, flags, k, status, delta, J);
-#pragma unroll 1
-    for (int t = 0; t < WB; ++t)
+    solve_bins<C, MK>(sc, par, cnt, FROM_U, FROM_U ? __uint_as_float(st->d1bits) : 0.0f, v, v64, up, m, inv_m1,
+                      eps, max_iter, flags, k, status, delta, J);
 #pragma unroll
-        for (int j = 0; j < C; ++j) table[(lane + 32 * t) * C + j] = s_up[up_at(t, j, lane)];
-    if (lane == 0) {
+    for (int j = 0; j < C; ++j) table[b * C + j] = up[j];
+    if (b == 0) {
         st->iters = k;
         st->status = status;
         st->flags = flags;
         st->delta = (double)delta;
         st->J = (double)J.hi + (double)J.lo;
-#pragma unroll
-        for (int j = 0; j < C; ++j) st->V[j] = v[j];
     }
 #pragma unroll
     for (int j = 0; j < C; ++j)
-        if (lane == j) st->V64[j] = (double)v64[j].hi + (double)v64[j].lo;
+        if (b == j) {
+            st->V[j] = v[j];
+            st->V64[j] = (double)v64[j].hi + (double)v64[j].lo;
+        }
 }
 
 // U^k by table lookup: U_ij = table[x_i][j].
@@ -464,7 +455,7 @@ extern "C" int fcm_run_hist(fcm_handle h, const float* x, int64_t n, int C, floa
     k.pass0[fu]<<<nblocks, HNT, 0, h->stream>>>(x, from_u ? U0 : nullptr, n, m, w->d_st, w->part);
     k.init[fu]<<<1, HNT, 0, h->stream>>>(w->d_st, w->part, nblocks, m, inv_m1);
     if (from_u) k.delta1<<<nblocks, HNT, 0, h->stream>>>(x, U0, n, m, inv_m1, w->d_st);
-    k.solve[fu]<<<1, 32, 0, h->stream>>>(w->d_st, w->table, m, inv_m1, eps, max_iter);
+    k.solve[fu]<<<1, HNT, 0, h->stream>>>(w->d_st, w->table, m, inv_m1, eps, max_iter);
     k.emit<<<nblocks, HNT, 0, h->stream>>>(x, n, w->table, w->d_st, U);
     CK(cudaGetLastError());
     CK(cudaMemcpyAsync(hs, w->d_st, sizeof(HistState), cudaMemcpyDeviceToHost, h->stream));

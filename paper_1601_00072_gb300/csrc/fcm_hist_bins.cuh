@@ -1,6 +1,6 @@
 // Algorithm 1 (arXiv:1601.00072, Sec. 2.1) on the 256-bin grey-level
 // histogram: the loop of the histogram-domain run (brFCM, cited in Sec. 3),
-// shared by the single-image kernel and the batch kernels (one warp per run).
+// shared by the single-image kernel and the batch kernels (one CTA per run).
 //
 // Under Eq. 4 a pixel's memberships depend only on its grey level, so the
 // center sums of Eq. 3 and J of Eq. 1 are sums over bins weighted by their
@@ -12,89 +12,105 @@
 
 namespace fcm {
 
-constexpr int HNT = 256;  // threads of the pixel-pass CTAs
+constexpr int HNT = 256;  // threads of the pixel-pass and bin-loop CTAs
 
 __device__ __forceinline__ bool grey_level(float v) {
     return v >= 0.0f && v <= 255.0f && v == rintf(v);  // false for NaN
 }
 
-// The loop runs in one warp: lane l holds grey levels l + 32 t, t < WB. A
-// lane adds its eight bins' terms in FP32, then a double-float xor tree over
-// the warp gives every lane the same totals, so every lane forms V^{k+1}
-// (double-float quotients) itself: no block barrier, and a CTA of 32 threads
-// per run lets the many runs of a batch share each SM. The loop body is kept
-// small (bins two at a time, the tree's five levels rolled, U^{k-1} in shared
-// memory): one warp per SM runs it from the instruction cache.
-constexpr int WB = 256 / 32;
+// The loop runs in one CTA of HNT threads, thread b holding grey level b.
+// A sum over the bins is taken in two steps: a five-level FP32 xor tree in
+// each warp (non-negative terms: at most five roundings, no cancellation),
+// then the eight warp totals in double-float, by a three-level xor tree over
+// groups of eight lanes that every warp evaluates alike. So every thread
+// holds the same totals and forms the same V^{k+1} (double-float quotients),
+// and one barrier per reduction suffices: the warp totals are double-buffered
+// by the parity `par`, which every reduction flips.
+constexpr int HNW = HNT / 32;
+static_assert(HNW == 8, "the cross-warp tree takes eight warp totals");
 
-// Shared U of one warp's bins: s_up[(t * FCM_MAX_CLUSTERS + j) * 32 + lane]
-// is cluster j of grey level lane + 32 t (conflict-free across the lanes).
-__device__ __forceinline__ int up_at(int t, int j, int lane) { return (t * FCM_MAX_CLUSTERS + j) * 32 + lane; }
+struct BinScratch {
+    float w[2][HNW][2 * FCM_MAX_CLUSTERS + 2];  // [parity][warp]: N sums, then one maximum
+};
 
-// N double-float sums over the warp, the five xor levels in a rolled loop
-// (every level issues all N pairs of shuffles before the N merges).
+// N block sums and one block maximum: t[0..N-1] are this thread's terms and
+// t[N] its maximum; on return every thread holds the totals tot[] and the
+// maximum mx, the same in all threads. All HNT threads must call it.
 template <int N>
-__device__ __forceinline__ void warp_sum_df_rolled(DF (&d)[N]) {
-    const int lane = threadIdx.x & 31;
-#pragma unroll 1
+__device__ __forceinline__ void block_sums(BinScratch& sc, int& par, float (&t)[N + 1], DF (&tot)[N], float& mx) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-        DF e[N];
+        float e[N + 1];
 #pragma unroll
-        for (int q = 0; q < N; ++q) e[q] = DF{__shfl_xor_sync(0xffffffffu, d[q].hi, o), __shfl_xor_sync(0xffffffffu, d[q].lo, o)};
+        for (int q = 0; q <= N; ++q) e[q] = __shfl_xor_sync(0xffffffffu, t[q], o);
 #pragma unroll
-        for (int q = 0; q < N; ++q) d[q] = (lane & o) ? df_merge(e[q], d[q]) : df_merge(d[q], e[q]);
+        for (int q = 0; q < N; ++q) t[q] += e[q];  // a + b == b + a: every lane gets the same total
+        t[N] = fmaxf(t[N], e[N]);
     }
+    if (lane == 0) {
+#pragma unroll
+        for (int q = 0; q <= N; ++q) sc.w[par][warp][q] = t[q];
+    }
+    __syncthreads();
+    // lane l takes the total of warp l & 7 for sum 4 r + (l >> 3)
+    const int g = lane >> 3, w = lane & 7;
+#pragma unroll
+    for (int r = 0; r < (N + 3) / 4; ++r) {
+        const int q = 4 * r + g;
+        DF d{q < N ? sc.w[par][w][q] : 0.0f, 0.0f};
+#pragma unroll
+        for (int o = 4; o > 0; o >>= 1) {
+            const DF e{__shfl_xor_sync(0xffffffffu, d.hi, o), __shfl_xor_sync(0xffffffffu, d.lo, o)};
+            d = (lane & o) ? df_merge(e, d) : df_merge(d, e);  // lower warp first, in every lane
+        }
+#pragma unroll
+        for (int gg = 0; gg < 4; ++gg)
+            if (4 * r + gg < N)
+                tot[4 * r + gg] = DF{__shfl_sync(0xffffffffu, d.hi, 8 * gg), __shfl_sync(0xffffffffu, d.lo, 8 * gg)};
+    }
+    mx = sc.w[par][0][N];
+#pragma unroll
+    for (int u = 1; u < HNW; ++u) mx = fmaxf(mx, sc.w[par][u][N]);
+    par ^= 1;
 }
 
-// Iterations k = 1, 2, ... of Algorithm 1 on the bins of one run.
-//   s_cnt the pixel counts of the bins (as floats), s_cnt[t * 32 + lane] for
-//         grey level lane + 32 t.
-//   v     in: V^1; out: V^k of the returned U^k. v64: the double-float
-//         quotients behind v (in and out).
-//   s_up  the warp's U (up_at): in, the bins' U^0 when the run started from
-//         centers (from_u false); out, U^k. A run from memberships takes its
-//         first stopping quantity d1 from the pixels instead.
-//   J     out: J_k (Eq. 1) as a double-float.
+// Iterations k = 1, 2, ... of Algorithm 1 on the bins of one run, in one CTA.
+//   cnt   the pixel count of this thread's grey level (as a float).
+//   from_u  the run started from U^0: its first stopping quantity is d1,
+//         taken over the pixels (a run from centers has U^0 per grey level).
+//   v, v64  in: V^1 (the same in every thread) and the double-float quotients
+//         behind it; out: V^k of the returned U^k.
+//   up    in: U^0 of this grey level (runs from centers); out: its U^k.
+//   J     out: J_k (Eq. 1).
+// An empty cluster keeps its center and sets the flag.
 template <int C, int MK>
-__device__ __forceinline__ void solve_bins_warp(const float* s_cnt, bool from_u, float d1, float (&v)[C],
-                                                DF (&v64)[C], float* s_up, float m, float inv_m1, float eps,
-                                                int max_iter, int& flags, int& k_out, int& status_out,
-                                                float& delta_out, DF& J) {
+__device__ __forceinline__ void solve_bins(BinScratch& sc, int& par, float cnt, bool from_u, float d1,
+                                           float (&v)[C], DF (&v64)[C], float (&up)[C], float m, float inv_m1,
+                                           float eps, int max_iter, int& flags, int& k_out, int& status_out,
+                                           float& delta_out, DF& J) {
     constexpr int S = 2 * C + 1;
-    const int lane = threadIdx.x & 31;
+    const float b = (float)threadIdx.x;
     int status = FCM_NOT_CONVERGED, k;
     float delta = 0.0f;
-    for (k = 1;; ++k) {
-        float acc[S];
-#pragma unroll
-        for (int q = 0; q < S; ++q) acc[q] = 0.0f;
-        float mx = 0.0f;
-        const bool first_from_u = from_u && k == 1;
 #pragma unroll 1
-        for (int t = 0; t < WB; t += 2) {
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const float b = (float)(lane + 32 * (t + h));
-                const float c = s_cnt[(t + h) * 32 + lane];
-                float u[C], um[C];
-                const float Ji = membership<C, MK>(b, v, m, inv_m1, u, um);
-#pragma unroll
-                for (int j = 0; j < C; ++j) {
-                    acc[j] = fmaf(c, um[j] * b, acc[j]);
-                    acc[C + j] = fmaf(c, um[j], acc[C + j]);
-                    float& upj = s_up[up_at(t + h, j, lane)];
-                    if (c > 0.0f && !first_from_u) mx = fmaxf(mx, fabsf(u[j] - upj));
-                    upj = u[j];
-                }
-                acc[2 * C] = fmaf(c, Ji, acc[2 * C]);
-            }
-        }
+    for (k = 1;; ++k) {
+        float u[C], um[C];
+        const float Ji = membership<C, MK>(b, v, m, inv_m1, u, um);
+        float t[S + 1], dm;
         DF tot[S];
+        float mx = 0.0f;
 #pragma unroll
-        for (int q = 0; q < S; ++q) tot[q] = DF{acc[q], 0.0f};
-        warp_sum_df_rolled<S>(tot);
-        mx = warp_max(mx);
-        delta = first_from_u ? d1 : mx;
+        for (int j = 0; j < C; ++j) {
+            t[j] = cnt * (um[j] * b);
+            t[C + j] = cnt * um[j];
+            if (cnt > 0.0f) mx = fmaxf(mx, fabsf(u[j] - up[j]));
+            up[j] = u[j];
+        }
+        t[2 * C] = cnt * Ji;
+        t[S] = mx;
+        block_sums<S>(sc, par, t, tot, dm);
+        delta = (from_u && k == 1) ? d1 : dm;
         J = tot[2 * C];
         if (delta < eps) {
             status = FCM_OK;
