@@ -30,7 +30,15 @@
  *   - Arithmetic: memberships and per-thread sums in FP32; the sums across
  *     threads and blocks (center numerators/denominators and J) in
  *     compensated FP32 (double-float, about 44 bits) or FP64, in a fixed
- *     order, so a run is deterministic. The histogram-domain entry points
+ *     order. A run is deterministic, with one exception: on images large
+ *     enough that every warp of the whole-run kernel holds more than a ring
+ *     of tiles (about 4 million pixels), 40% of each pass's tiles go to
+ *     whichever warps ask first, so SMs that stream faster take more of them
+ *     (about 11% faster on a 256^3 volume). Which block sums which tile then
+ *     depends on timing, and so does the FP32 rounding of the block sums:
+ *     results agree to rounding, and the iteration count can differ by one
+ *     when delta_k lands at eps. FCM_OPT_DETERMINISTIC keeps fixed shares
+ *     for bit-reproducible runs. The histogram-domain entry points
  *     form V^1 the same way from the pixels; their loop over the 256 bins
  *     sums non-negative terms in FP32 within each warp (a fixed tree, at
  *     most five roundings) and combines the warp totals in double-float.
@@ -85,6 +93,9 @@ extern "C" {
                                  from V^{k-1}, so an iteration reads only x; U^k is
                                  written once at the end (one cooperative launch;
                                  needs n % 4 == 0 and 16-byte-aligned rows) */
+#define FCM_OPT_DETERMINISTIC 32 /* whole-run kernel: every tile in fixed warp
+                                     shares, so the result does not depend on
+                                     timing (see the arithmetic note above) */
 
 typedef struct fcm_ctx* fcm_handle;
 
@@ -230,7 +241,7 @@ int fcm_run_seeded(fcm_handle h, const float* x, int64_t n, int C, float m, floa
  *             i's U^0 from U[i].
  *   U         n_images pointers to C*n floats. Out: each image's U^k.
  *   V         n_images*C floats, host memory. Out: row i = image i's V^k.
- *   options   0 or FCM_OPT_RECOMPUTE.
+ *   options   0, or FCM_OPT_RECOMPUTE and/or FCM_OPT_DETERMINISTIC.
  *   reps      nullable; n_images reports.
  *
  * Needs n % 4 == 0 and a device with cooperative launch; returns

@@ -28,6 +28,7 @@ FCM_OPT_NO_GRAPH = 2
 FCM_OPT_NO_TMA = 4
 FCM_OPT_NO_PERSISTENT = 8
 FCM_OPT_RECOMPUTE = 16
+FCM_OPT_DETERMINISTIC = 32
 
 
 class fcm_report(ctypes.Structure):

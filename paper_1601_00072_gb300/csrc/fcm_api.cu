@@ -70,6 +70,16 @@ WaitLimits default_limits() {
     return w;
 }
 
+// Percent of a pass's tiles the whole-run kernel deals in fixed warp shares;
+// FCM_RUN_STATIC_PCT overrides the default (100: fixed shares only).
+int default_static_pct() {
+    if (const char* e = std::getenv("FCM_RUN_STATIC_PCT")) {
+        const long v = std::atol(e);
+        if (v >= 1 && v <= 100) return (int)v;
+    }
+    return DEFAULT_STATIC_PCT;
+}
+
 bool is_device_pointer(const void* p) {
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
@@ -317,6 +327,7 @@ int fcm_create(fcm_handle* out, int device, void* cuda_stream) {
     h->max_smem_optin = (int)prop.sharedMemPerBlockOptin;
     h->device_name = prop.name;
     h->limits = default_limits();
+    h->static_pct = default_static_pct();
     *out = h;
     return FCM_OK;
 }
@@ -471,6 +482,7 @@ int fcm_run(fcm_handle h, const float* x, int64_t n, int C, float m, float eps, 
     hs->C = C;
     hs->status = STATUS_RUNNING;
     hs->lim = h->limits;
+    hs->static_pct = (options & FCM_OPT_DETERMINISTIC) ? 100 : h->static_pct;
     if (init_mode == FCM_INIT_V && !V_dev) std::memcpy(hs->V0, V, sizeof(float) * C);
     CK(cudaMemcpyAsync(h->d_st, hs, sizeof(RunState), cudaMemcpyHostToDevice, h->stream));
     if (init_mode == FCM_INIT_V && V_dev)
@@ -561,7 +573,8 @@ int fcm_run_stream(fcm_handle h, int n_images, const float* const* x, int64_t n,
     if (max_iter < 1) return ctx_invalid(h, "max_iter must be >= 1");
     if (n > (int64_t)1 << 40) return ctx_invalid(h, "n too large");
     if (n % 4 != 0) return ctx_invalid(h, "fcm_run_stream needs n % 4 == 0");
-    if (options & ~FCM_OPT_RECOMPUTE) return ctx_invalid(h, "fcm_run_stream takes no option but FCM_OPT_RECOMPUTE");
+    if (options & ~(FCM_OPT_RECOMPUTE | FCM_OPT_DETERMINISTIC))
+        return ctx_invalid(h, "fcm_run_stream takes no option but FCM_OPT_RECOMPUTE and FCM_OPT_DETERMINISTIC");
 
     DeviceGuard g(h->device);
     int rc = ensure_single_workspace(h);
@@ -622,6 +635,7 @@ int fcm_run_stream(fcm_handle h, int n_images, const float* const* x, int64_t n,
         hs->C = C;
         hs->status = STATUS_RUNNING;
         hs->lim = h->limits;
+        hs->static_pct = (options & FCM_OPT_DETERMINISTIC) ? 100 : h->static_pct;
         const float* u0 = (U0 && U0[i]) ? U0[i] : U[i];
         // upload, once the download of image i - NS has drained this set
         if (i >= NS) e = cudaStreamWaitEvent(h->pipe_in, out_done[b], 0);
@@ -709,6 +723,7 @@ int fcm_time_pass(fcm_handle h, const float* x, int64_t n, int C, float m, float
     hs->k = 1;
     hs->status = STATUS_RUNNING;
     hs->lim = h->limits;
+    hs->static_pct = (options & FCM_OPT_DETERMINISTIC) ? 100 : h->static_pct;
     const bool V_dev = is_device_pointer(V);
     if (!V_dev)
         for (int j = 0; j < C; ++j) {

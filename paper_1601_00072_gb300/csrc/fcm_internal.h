@@ -11,6 +11,16 @@ namespace fcm {
 constexpr int NT = 256;                                  // threads per block of the pass
 constexpr int NWARP = NT / 32;
 constexpr int WARP_TILE = 128;                           // pixels per warp tile of the TMA kernels
+constexpr int DCHUNK = 4;  // tiles per grab from the shared part of a pass (whole-run kernels)
+// Issue-side state of one warp's TMA ring in the whole-run kernels (lane 0
+// only, kept in shared memory): copies issued, next tile of the chunk being
+// issued, pass, index in the fixed share, ring slot, tiles left in the chunk,
+// and the counter value grabbed for the next chunk.
+struct IssueState {
+    int64_t issued, cb;
+    int ip, ik, is, cl;
+    unsigned grab;
+};
 constexpr int SLOTS_MAX = 2 * FCM_MAX_CLUSTERS + 4;      // num[C], den[C], J, delta, 2 flags
 constexpr int STATUS_RUNNING = 2;
 
@@ -67,7 +77,14 @@ struct alignas(128) RunState {
     unsigned int ticket;  // last-block-done counter of the current pass
     int launches;         // passes started in this run (loop guard)
     WaitLimits lim;
+    // whole-run kernel: percent of each pass's tiles dealt to the warps in
+    // fixed shares (100: all of them); the rest is taken in chunks from
+    // dyn[pass & 1] (zeroed by the upload of this state, re-zeroed on the
+    // device two passes before each reuse)
+    int static_pct;
+    unsigned int dyn[2];
 };
+constexpr int DEFAULT_STATIC_PCT = 60;
 
 typedef void (*PassFn)(RunState*, double*, cudaGraphConditionalHandle, int);
 

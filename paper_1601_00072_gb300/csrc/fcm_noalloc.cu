@@ -159,6 +159,7 @@ extern "C" int fcm_run_noalloc(const float* x, int64_t n, int C, float m, float 
     hs.C = C;
     hs.status = STATUS_RUNNING;
     hs.lim = WaitLimits{DEFAULT_GRID_SPINS, DEFAULT_TMA_POLLS, 0u, 0u};
+    hs.static_pct = DEFAULT_STATIC_PCT;
     const bool V_dev = on_device(V);
     if (init_mode == FCM_INIT_V && !V_dev) std::memcpy(hs.V0, V, sizeof(float) * C);
 

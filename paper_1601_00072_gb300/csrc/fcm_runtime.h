@@ -51,6 +51,9 @@ struct fcm_ctx {
     // run's state; alloc_fail_in > 0 makes the allocation that many calls
     // from now fail once (fault injection for tests, 0 = off)
     fcm::WaitLimits limits{fcm::DEFAULT_GRID_SPINS, fcm::DEFAULT_TMA_POLLS, 0u, 0u};
+    // whole-run kernel: percent of a pass's tiles dealt in fixed warp shares
+    // (FCM_RUN_STATIC_PCT in the environment overrides it, 1..100)
+    int static_pct = fcm::DEFAULT_STATIC_PCT;
     int alloc_fail_in = 0;
 
     // single-image path

@@ -29,6 +29,8 @@
 // block order, forms V^{k+1}, decides convergence on the device (the paper
 // does this on the host, Sec. 4.3) and sets the CUDA-graph WHILE condition.
 // No block waits for another: the ticket only elects the finisher.
+#include <climits>
+
 #include "fcm_device.cuh"
 #include "fcm_exchange.cuh"
 #include "fcm_internal.h"
@@ -495,12 +497,19 @@ __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
 // (2^23, about 1 s, by default), and waits for st->lim.phantoms arrivals
 // beyond the grid's own (0 unless a test injects a barrier that never fills).
 
-// Every warp keeps the same tiles in every pass, so the U tile a warp reads in
-// pass p + 1 is the one it wrote in pass p. Its ring therefore streams one
-// sequence of loads across passes (look-ahead min(STAGES, tiles per warp), so
-// a tile is never re-read before the warp has written it; a proxy fence orders
+// Tiles are dealt in two parts. Every warp keeps the same fixed share of tiles
+// in every pass (tile gw + k * nwarps, k < ks), so the U tile it reads from
+// that share in pass p + 1 is one it wrote itself in pass p. Its ring
+// therefore streams one sequence of loads across passes (a proxy fence orders
 // the warp's stores before its own TMA re-read) and keeps DRAM busy while the
-// grid exchanges the 2C + 4 sums of a pass. After each pass every block
+// grid exchanges the 2C + 4 sums of a pass. The rest of each pass is taken in
+// chunks of DCHUNK consecutive tiles from a per-pass counter, so warps on SMs
+// that stream faster take more of it and the warps finish a pass together
+// (with fixed shares alone, the slowest SMs took about 1.5x as long as the
+// fastest). A warp reaches the shared part of pass p only after its fixed
+// share of pass p, which it starts after the grid barrier of pass p - 1, so
+// every tile it takes was written before that barrier. The counter grab is
+// issued one chunk ahead, so its latency hides behind the chunk's copies. After each pass every block
 // publishes its FP32 totals, waits at a bounded grid barrier (co-residency is
 // guaranteed by the cooperative launch), and computes the cross-block sums in
 // the same fixed order as every other block, so all blocks derive the same
@@ -519,6 +528,10 @@ __global__ void __launch_bounds__(NT, 2) k_fcm_run_tma(RunState* __restrict__ st
     __shared__ DF s_vq[C];
     __shared__ int s_empty[C];
     __shared__ int s_err;
+    // what each ring stage holds: tile and pass (pass INT_MAX: nothing)
+    __shared__ int64_t s_tile[NWARP][Sh::STAGES];
+    __shared__ int s_pass[NWARP][Sh::STAGES];
+    __shared__ IssueState s_iss[NWARP];
 
     const float* __restrict__ x = st->x;
     const float* U0 = st->Uprev;
@@ -546,9 +559,14 @@ __global__ void __launch_bounds__(NT, 2) k_fcm_run_tma(RunState* __restrict__ st
     const int64_t nwarps = (int64_t)gridDim.x * NWARP;
     const int64_t gw = (int64_t)blockIdx.x * NWARP + warp;
     const int64_t ntiles = (n + WTILE - 1) / WTILE;
-    const int nk = (int)(ntiles > gw ? (ntiles - 1 - gw) / nwarps + 1 : 0);
+    // fixed share: ks tiles per warp, when every warp has more than a ring of
+    // them; otherwise every tile is dealt in fixed shares (nk per warp)
+    const int64_t ks = ntiles * (int64_t)st->static_pct / 100 / nwarps;
+    const bool shared_part = st->static_pct < 100 && ks > Sh::STAGES;
+    const int nk = shared_part ? (int)ks : (int)(ntiles > gw ? (ntiles - 1 - gw) / nwarps + 1 : 0);
+    const int64_t n_fixed = shared_part ? ks * nwarps : ntiles;
+    const int64_t n_chunks = (ntiles - n_fixed + DCHUNK - 1) / DCHUNK;
     const int look = nk < Sh::STAGES ? nk : Sh::STAGES;
-    const int64_t tile_stride = nwarps * (int64_t)WTILE;
     const int npass = 1 + max_iter;  // passes the run can take
     const uint32_t wait_limit = st->lim.tma_polls, grid_spins = st->lim.grid_spins;
     const unsigned phantoms = st->lim.phantoms;
@@ -557,22 +575,30 @@ __global__ void __launch_bounds__(NT, 2) k_fcm_run_tma(RunState* __restrict__ st
 
     if (lane == 0) {
 #pragma unroll
-        for (int s = 0; s < Sh::STAGES; ++s) mbar_init(&full[s], 1);
+        for (int s = 0; s < Sh::STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            s_pass[warp][s] = INT_MAX;
+        }
         mbar_fence_init();
     }
     if (threadIdx.x == 0) s_err = 0;
     __syncthreads();
 
-    // Issue side (lane 0): pass ip, tile ik of the next load, ring slot is.
-    int ip = 0, ik = 0, is = 0;
-    int64_t issued = 0;
-    auto issue_next = [&]() {
-        if (ip >= npass || nk == 0) return;
-        const int64_t i0 = gw * (int64_t)WTILE + ik * tile_stride;
+    // Issue side (lane 0), kept in shared memory so that it takes no
+    // registers during the tile work: pass ip, index ik in the fixed share,
+    // the chunk being issued (next tile cb, cl tiles left), the grab for the
+    // next chunk, ring slot is, and the copies issued so far.
+    IssueState& q = s_iss[warp];
+    if (lane == 0) q = IssueState{0, 0, 0, 0, 0, 0, 0u};
+    auto issue_tile = [&](int64_t tile, int ip) {
+        const int64_t i0 = tile * WTILE;
         const uint32_t bytes = (uint32_t)min((int64_t)WTILE, n - i0) * 4u;  // multiple of 16
         const bool with_u = !(ip == 0 && INIT == P_INITV);
         const float* Usrc = (ip == 0 || (ip == 1 && INIT == P_ACCUM0)) ? U0 : U;
+        const int is = q.is;
         float* dst = ring + is * Sh::STAGE_FLOATS;
+        s_tile[warp][is] = tile;
+        s_pass[warp][is] = ip;
         mbar_expect_tx(&full[is], bytes * (with_u ? 1 + C : 1));
         bulk_g2s(dst, x + i0, bytes, &full[is], pol_x);
         if (with_u) {
@@ -580,15 +606,38 @@ __global__ void __launch_bounds__(NT, 2) k_fcm_run_tma(RunState* __restrict__ st
             for (int j = 0; j < C; ++j)
                 bulk_g2s(dst + (1 + j) * WTILE, Usrc + (int64_t)j * n + i0, bytes, &full[is], pol_u);
         }
-        ++issued;
-        if (++ik == nk) {
-            ik = 0;
-            ++ip;
+        ++q.issued;
+        q.is = is + 1 == Sh::STAGES ? 0 : is + 1;
+    };
+    auto issue_next = [&]() {
+        while (q.ip < npass && nk > 0) {
+            const int ip = q.ip;
+            if (q.ik < nk) {
+                const int64_t tile = gw + (int64_t)q.ik * nwarps;
+                if (++q.ik == nk && shared_part) q.grab = atomicAdd(&st->dyn[ip & 1], 1u);  // first chunk, ahead
+                issue_tile(tile, ip);
+                return;
+            }
+            if (q.cl == 0) {
+                if (shared_part && (int64_t)q.grab < n_chunks) {
+                    q.cb = n_fixed + (int64_t)q.grab * DCHUNK;
+                    q.cl = (int)min((int64_t)DCHUNK, ntiles - q.cb);
+                    q.grab = atomicAdd(&st->dyn[ip & 1], 1u);  // the chunk after this one, ahead
+                } else {
+                    ++q.ip;  // pass ip is dealt out: on to the next pass's fixed share
+                    q.ik = 0;
+                    continue;
+                }
+            }
+            --q.cl;
+            issue_tile(q.cb++, ip);
+            return;
         }
-        if (++is == Sh::STAGES) is = 0;
+        s_pass[warp][q.is] = INT_MAX;  // nothing more to load
     };
     if (lane == 0)
         for (int t = 0; t < look; ++t) issue_next();
+    __syncwarp();
 
     int cs = 0;  // consume side: ring slot and phase parity
     uint32_t parity = 0;
@@ -603,25 +652,28 @@ __global__ void __launch_bounds__(NT, 2) k_fcm_run_tma(RunState* __restrict__ st
 #pragma unroll
             for (int j = 0; j < C; ++j) a.bad |= !finite_f(v[j]);
         }
-        // ---- the pass over this warp's tiles ----
-        int64_t i0 = gw * (int64_t)WTILE;
-        for (int k = 0; k < nk; ++k, i0 += tile_stride) {
+        // ---- the pass over this warp's tiles: the ring's items of pass p ----
+        while (s_pass[warp][cs] == p) {
             const bool ok = mbar_wait_bounded(&full[cs], parity, wait_limit);
             if (__any_sync(0xffffffffu, !ok)) {
                 err = true;
                 break;
             }
+            const int64_t i0 = s_tile[warp][cs] * WTILE;
             const int cnt = (int)min((int64_t)WTILE, n - i0);
             const float* sb = ring + cs * Sh::STAGE_FLOATS;
             if (p == 0)
                 tile_work<C, MK, INIT>(sb, cnt, i0, lane, U, n, v, v2, m, inv_m1, pol_u, a);
             else
                 tile_work<C, MK, P_ITER>(sb, cnt, i0, lane, U, n, v, v2, m, inv_m1, pol_u, a);
-            // this lane's stores of U must precede the warp's own TMA re-read
+            // this lane's stores of U must precede any TMA re-read of the tile:
+            // the warp's own (fixed share, next pass) or another warp's after
+            // the grid barrier (shared part)
             asm volatile("fence.proxy.async.global;" ::: "memory");
             __syncwarp();
             ++consumed;
             if (lane == 0) issue_next();
+            __syncwarp();  // the stage records written by lane 0
             if (++cs == Sh::STAGES) {
                 cs = 0;
                 parity ^= 1u;
@@ -686,6 +738,12 @@ __global__ void __launch_bounds__(NT, 2) k_fcm_run_tma(RunState* __restrict__ st
         __syncthreads();
         const float delta = s_mx[0];
         const bool bad = s_mx[1] != 0.0f, tmo = s_mx[2] != 0.0f;
+        // the loads this warp issues from here on may read U tiles that other
+        // warps wrote before the barrier
+        if (lane == 0) asm volatile("fence.proxy.async.global;" ::: "memory");
+        // every chunk of pass p was taken before this barrier; its counter
+        // serves pass p + 2, whose first grab follows the next barrier
+        if (blockIdx.x == 0 && threadIdx.x == 0) st->dyn[p & 1] = 0u;
         bool update = false;
         if (tmo) {
             status = FCM_ERR_TIMEOUT;
@@ -747,7 +805,7 @@ __global__ void __launch_bounds__(NT, 2) k_fcm_run_tma(RunState* __restrict__ st
     if (lane == 0) {
         int ds = cs;
         uint32_t dp = parity;
-        for (int64_t q = consumed; q < issued; ++q) {
+        for (int64_t t = consumed; t < q.issued; ++t) {
             mbar_wait_bounded(&full[ds], dp, wait_limit);
             if (++ds == Sh::STAGES) {
                 ds = 0;

@@ -167,7 +167,7 @@ class FCM:
     def run(self, x, C: int, m: float = 2.0, eps: float = 1e-5, max_iter: int = 300, *,
             U0=None, V0=None, U=None, V=None, trace: bool = False, graph: bool = True,
             tma: bool = True, persistent: bool = True, recompute: bool = False,
-            raise_on_error: bool = True) -> FCMResult:
+            deterministic: bool = False, raise_on_error: bool = True) -> FCMResult:
         """Algorithm 1 on one image.
 
         ``x``: n float32 pixels (CUDA tensor, pinned/CPU tensor or numpy).
@@ -175,7 +175,10 @@ class FCM:
         ``U`` holding U^0 (updated in place). Start from centers: ``V0`` [C].
         ``U`` (allocated when None) receives U^k and ``V`` (allocated when
         None, or V0 itself) receives V^k. ``recompute=True`` keeps no U
-        between iterations (``FCM_OPT_RECOMPUTE``).
+        between iterations (``FCM_OPT_RECOMPUTE``). ``deterministic=True``
+        deals every tile of the whole-run kernel in fixed warp shares, so
+        large images give bit-identical results run after run
+        (``FCM_OPT_DETERMINISTIC``).
         """
         import torch
         n = _numel(x)
@@ -207,7 +210,8 @@ class FCM:
             raise ValueError("U and U0 must hold C*n floats and V C floats")
         opts = ((_lib.FCM_OPT_TRACE if trace else 0) | (0 if graph else _lib.FCM_OPT_NO_GRAPH)
                 | (0 if tma else _lib.FCM_OPT_NO_TMA) | (0 if persistent else _lib.FCM_OPT_NO_PERSISTENT)
-                | (_lib.FCM_OPT_RECOMPUTE if recompute else 0))
+                | (_lib.FCM_OPT_RECOMPUTE if recompute else 0)
+                | (_lib.FCM_OPT_DETERMINISTIC if deterministic else 0))
         rep = _lib.fcm_report()
         self._bind_stream()
         st = self._lib.fcm_run(self._h, _ptr(x), n, int(C), float(m), float(eps), int(max_iter),
@@ -262,7 +266,7 @@ class FCM:
 
     def run_stream(self, xs, C: int, m: float = 2.0, eps: float = 1e-5, max_iter: int = 300, *,
                    U0s=None, Us=None, V=None, recompute: bool = False,
-                   raise_on_error: bool = True) -> list[FCMResult]:
+                   deterministic: bool = False, raise_on_error: bool = True) -> list[FCMResult]:
         """Algorithm 1 on a sequence of same-sized images in host memory
         (``fcm_run_stream``): the upload of the next image and the download
         of the previous one overlap the current run.
@@ -305,7 +309,9 @@ class FCM:
         reps = (_lib.fcm_report * k)()
         self._bind_stream()
         st = self._lib.fcm_run_stream(self._h, k, xp, n, int(C), float(m), float(eps), int(max_iter),
-                                      u0p, up, _ptr(V), _lib.FCM_OPT_RECOMPUTE if recompute else 0, reps)
+                                      u0p, up, _ptr(V),
+                                      (_lib.FCM_OPT_RECOMPUTE if recompute else 0)
+                                      | (_lib.FCM_OPT_DETERMINISTIC if deterministic else 0), reps)
         if raise_on_error:
             _lib.check(st, self._h)
         return [FCMResult(U=Us[i], V=V[i], iters=reps[i].iters, status=reps[i].status, delta=reps[i].delta,

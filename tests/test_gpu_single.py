@@ -79,16 +79,21 @@ def test_phantom1024_matches_oracle(fcm):
     assert_within(rep)
 
 
-@pytest.mark.parametrize("m,recompute", [(2.0, False), (1.5, False), (3.0, False), (2.0, True)])
-def test_volume256_matches_oracle(fcm, m, recompute):
-    """Full 16.7M-voxel run; U compared on a 200k-voxel sample."""
+@pytest.mark.parametrize("m,recompute,deterministic",
+                         [(2.0, False, False), (1.5, False, False), (3.0, False, False), (2.0, True, False),
+                          (2.0, False, True)])
+def test_volume256_matches_oracle(fcm, m, recompute, deterministic):
+    """Full 16.7M-voxel run; U compared on a 200k-voxel sample. By default the
+    whole-run kernel hands part of every pass to whichever warps ask first;
+    deterministic=True keeps every tile in a fixed warp share."""
     x, _, u0, C = phantom.single_image("volume256")
-    g, gU, gV = gpu_run(fcm, x, C, m, u0=u0, recompute=recompute)
+    kw = dict(recompute=recompute, deterministic=deterministic)
+    g, gU, gV = gpu_run(fcm, x, C, m, u0=u0, **kw)
     o = oracle_run(x, C, m, EPS, MAX_ITER, u0=u0, quantized=True, want_U=False)
     assert abs(g.iters - o["iters"]) <= 1
     k = min(g.iters, o["iters"])
     if g.iters > k:
-        g, gU, gV = gpu_run(fcm, x, C, m, max_iter=k, u0=u0, recompute=recompute)
+        g, gU, gV = gpu_run(fcm, x, C, m, max_iter=k, u0=u0, **kw)
     if o["iters"] > k:
         o = oracle_run(x, C, m, EPS, k, u0=u0, quantized=True, want_U=False)
     idx = np.random.default_rng(0).choice(x.size, 200_000, replace=False)
@@ -225,6 +230,23 @@ def test_graph_and_host_loop_agree_bitwise(fcm):
     b, bU, bV = gpu_run(fcm, x, C, 2.0, u0=u0, graph=False)
     assert a.iters == b.iters and np.array_equal(aU, bU) and np.array_equal(aV, bV)
     assert np.array_equal(a.V64, b.V64)
+
+
+def test_volume256_runs_repeat(fcm):
+    """Two default runs of the volume may round their block sums differently
+    (part of every pass goes to whichever warps ask first) and agree to FP32
+    rounding; two runs with FCM_OPT_DETERMINISTIC give the same bits."""
+    x, _, u0, C = phantom.single_image("volume256")
+    a, aU, aV = gpu_run(fcm, x, C, 2.0, u0=u0)
+    b, bU, bV = gpu_run(fcm, x, C, 2.0, u0=u0)
+    assert abs(a.iters - b.iters) <= 1
+    if a.iters == b.iters:
+        assert center_err(aV, bV) <= 1e-6 and np.max(np.abs(aU - bU)) <= 1e-6
+    del aU, bU
+    c, cU, cV = gpu_run(fcm, x, C, 2.0, u0=u0, deterministic=True)
+    d, dU, dV = gpu_run(fcm, x, C, 2.0, u0=u0, deterministic=True)
+    assert c.iters == d.iters and np.array_equal(cU, dU) and np.array_equal(cV, dV)
+    assert np.array_equal(c.V64, d.V64) and c.J == d.J
 
 
 def test_repeatable(fcm):
