@@ -31,17 +31,18 @@
  *     threads and blocks (center numerators/denominators and J) in
  *     compensated FP32 (double-float, about 44 bits) or FP64, in a fixed
  *     order. A run is deterministic, with one exception: on images large
- *     enough that every warp of the whole-run kernel holds more than a ring
- *     of tiles (about 4 million pixels), 40% of each pass's tiles go to
- *     whichever warps ask first, so SMs that stream faster take more of them
- *     (about 11% faster on a 256^3 volume). Which block sums which tile then
- *     depends on timing, and so does the FP32 rounding of the block sums:
- *     results agree to rounding, and the iteration count can differ by one
- *     when delta_k lands at eps. FCM_OPT_DETERMINISTIC keeps fixed shares
- *     for bit-reproducible runs. The histogram-domain entry points
- *     form V^1 the same way from the pixels; their loop over the 256 bins
- *     sums non-negative terms in FP32 within each warp (a fixed tree, at
- *     most five roundings) and combines the warp totals in double-float.
+ *     enough that every warp of the default whole-run kernel (stored U)
+ *     holds more than a ring of tiles (about 4 million pixels), 40% of each
+ *     pass's tiles go to whichever warps ask first, so SMs that stream
+ *     faster take more of them (about 11% faster on a 256^3 volume). Which
+ *     block sums which tile then depends on timing, and so does the FP32
+ *     rounding of the block sums: results agree to rounding, and the
+ *     iteration count can differ by one when delta_k lands at eps.
+ *     FCM_OPT_DETERMINISTIC keeps fixed shares for bit-reproducible runs.
+ *     The histogram-domain entry points form V^1 the same way from the
+ *     pixels; their loop over the 256 bins sums non-negative terms in FP32
+ *     within each warp (a fixed tree, at most five roundings) and combines
+ *     the warp totals in double-float.
  *   - Ownership: the caller owns x, U, V and every output array; the library
  *     never frees them. A handle owns its device workspace, CUDA graphs and
  *     autotuning cache, and frees them in fcm_destroy.
@@ -78,6 +79,8 @@ extern "C" {
 
 /* Report flags. */
 #define FCM_FLAG_EMPTY_CLUSTER 1 /* some sum_i u_ij^m underflowed to 0: v_j kept */
+#define FCM_FLAG_BOUNDS 2 /* a FCM_DEBUG_BOUNDS build skipped an out-of-range access
+                             (a library bug; never set by the normal build) */
 
 /* Initialisation modes (Algorithm 1 step 2). */
 #define FCM_INIT_U 0 /* U holds the initial membership U^0 on entry         */

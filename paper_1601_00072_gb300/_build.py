@@ -7,6 +7,12 @@ count (``-DFCM_INST_C=1..8``), and the
 two batched kernels twice each, once per block size (``-DFCM_BATCH_NT`` and
 ``-DFCM_ROUNDS_NT`` = 256, 512).
 Nothing is rebuilt when the library is newer than every source.
+
+With FCM_DEBUG_BOUNDS=1 in the environment the bounds-guarded variant is
+built instead, into ``_build_bounds/`` (``-DFCM_DEBUG_BOUNDS``: the kernels
+that issue TMA copies or index lookup tables check their indices, skip an
+out-of-range access and report FCM_FLAG_BOUNDS); the loader picks the same
+variant from the same variable.
 """
 from __future__ import annotations
 
@@ -20,12 +26,13 @@ PKG = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
-BUILD = os.path.join(PKG, "_build")
+DEBUG_BOUNDS = os.environ.get("FCM_DEBUG_BOUNDS", "0") not in ("", "0")
+BUILD = os.path.join(PKG, "_build_bounds" if DEBUG_BOUNDS else "_build")
 LIB = os.path.join(BUILD, "libfcm_gb300.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
-         "-I" + INCLUDE, "-I" + CSRC, "--expt-relaxed-constexpr"]
+         "-I" + INCLUDE, "-I" + CSRC, "--expt-relaxed-constexpr"] + (["-DFCM_DEBUG_BOUNDS=1"] if DEBUG_BOUNDS else [])
 
 
 def nvcc() -> str:

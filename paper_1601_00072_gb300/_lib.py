@@ -21,6 +21,7 @@ FCM_ERR_TIMEOUT = -5
 FCM_ERR_TOO_LARGE = -6
 FCM_NOALLOC_MAX_BLOCKS = 512
 FCM_FLAG_EMPTY_CLUSTER = 1
+FCM_FLAG_BOUNDS = 2
 FCM_INIT_U = 0
 FCM_INIT_V = 1
 FCM_OPT_TRACE = 1

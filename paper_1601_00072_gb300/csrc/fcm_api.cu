@@ -422,6 +422,7 @@ const char* fcm_last_error(fcm_handle h) {
 
 int fcm_run(fcm_handle h, const float* x, int64_t n, int C, float m, float eps, int max_iter,
             int init_mode, const float* U0, float* U, float* V, int options, fcm_report* rep) {
+    NvtxRange nvtx_range("fcm_run");
     if (!h) return FCM_ERR_INVALID_ARG;
     if (!x || !U || !V) return ctx_invalid(h, "null x, U or V");
     if (n < 1) return ctx_invalid(h, "n must be >= 1");
@@ -545,7 +546,7 @@ int fcm_run(fcm_handle h, const float* x, int64_t n, int C, float m, float eps, 
         std::memset(rep, 0, sizeof(*rep));
         rep->iters = hs->iters;
         rep->status = hs->status;
-        rep->flags = hs->flags;
+        rep->flags = hs->flags | (int)hs->bounds;
         rep->C = C;
         rep->delta = hs->delta;
         rep->J = hs->J;
@@ -562,6 +563,7 @@ int fcm_run(fcm_handle h, const float* x, int64_t n, int C, float m, float eps, 
 int fcm_run_stream(fcm_handle h, int n_images, const float* const* x, int64_t n, int C, float m, float eps,
                    int max_iter, const float* const* U0, float* const* U, float* V, int options,
                    fcm_report* reps) {
+    NvtxRange nvtx_range("fcm_run_stream");
     if (!h) return FCM_ERR_INVALID_ARG;
     if (n_images < 1 || !x || !U || !V) return ctx_invalid(h, "n_images >= 1 and non-null x, U and V");
     for (int i = 0; i < n_images; ++i)
@@ -686,7 +688,7 @@ int fcm_run_stream(fcm_handle h, int n_images, const float* const* x, int64_t n,
             std::memset(rep, 0, sizeof(*rep));
             rep->iters = hs->iters;
             rep->status = hs->status;
-            rep->flags = hs->flags;
+            rep->flags = hs->flags | (int)hs->bounds;
             rep->C = C;
             rep->delta = hs->delta;
             rep->J = hs->J;
@@ -701,6 +703,7 @@ int fcm_run_stream(fcm_handle h, int n_images, const float* const* x, int64_t n,
 
 int fcm_time_pass(fcm_handle h, const float* x, int64_t n, int C, float m, float* U, const float* V,
                   int launches, int options, float* ms_per_launch) {
+    NvtxRange nvtx_range("fcm_time_pass");
     if (!h) return FCM_ERR_INVALID_ARG;
     if (!x || !U || !V || !ms_per_launch) return ctx_invalid(h, "null argument");
     if (n < 1 || C < 1 || C > FCM_MAX_CLUSTERS || !(m > 1.0f) || launches < 1)

@@ -787,6 +787,7 @@ int presolve_hints(fcm_ctx* h, const fcm_slice* slices, int n, std::vector<int>*
 extern "C" {
 
 int fcm_run_batched(fcm_handle h, fcm_slice* slices, int n_slices, int options) {
+    NvtxRange nvtx_range("fcm_run_batched");
     if (!h) return FCM_ERR_INVALID_ARG;
     bool in_place = false;
     int rc = check_slices(h, slices, n_slices, (int64_t)1 << 40, &in_place);
@@ -880,6 +881,7 @@ int fcm_run_batched(fcm_handle h, fcm_slice* slices, int n_slices, int options) 
 }
 
 int fcm_run_batched_hist(fcm_handle h, fcm_slice* slices, int n_slices) {
+    NvtxRange nvtx_range("fcm_run_batched_hist");
     if (!h) return FCM_ERR_INVALID_ARG;
     bool in_place = false;
     // 32-bit bin counters per slice

@@ -115,7 +115,8 @@ struct BinArgs {
     int phase;               // solve: 0 first attempt, 1 the runs that needed pass B
     unsigned* hist;          // [n_slices][256] pixel counts
     int* rep;                // [n_slices][256] some pixel of each grey level, or -1
-    unsigned* bad;           // [n_slices] bit 0: not all grey levels; bit 1: a bad U^0
+    unsigned* bad;           // [n_slices] bit 0: not all grey levels; bit 1: a bad U^0;
+                             // bit 2: a FCM_DEBUG_BOUNDS guard skipped an access
     float2* part;            // [n_chunks][2 * FCM_MAX_CLUSTERS] (hi, lo) sums of V^1
     float* table;            // [n_runs][256][FCM_MAX_CLUSTERS] U^1, then U^k, per grey level
     unsigned* d1;            // [n_runs] first stopping quantity from pass B (float bits)

@@ -31,6 +31,7 @@
 #include <vector>
 
 #include "fcm_batched.h"
+#include "fcm_bounds.cuh"
 #include "fcm_device.cuh"
 #include "fcm_df.cuh"
 #include "fcm_hist_bins.cuh"
@@ -40,6 +41,7 @@ namespace fcm {
 namespace {
 
 constexpr int BNT = HNT;                 // threads of every kernel here (one per grey level)
+constexpr unsigned BAD_BOUNDS = 4u;      // bit 2 of BinArgs::bad
 constexpr int BNW = BNT / 32;
 constexpr int PX_PER_THREAD = BIN_CHUNK / BNT;
 constexpr int LOADS = 4;                 // pixels per thread whose loads are issued together
@@ -368,6 +370,7 @@ __global__ void __launch_bounds__(BNT) k_bins_pass_b(BinArgs a) {
     float mx = 0.0f;
     for (int i = lo + threadIdx.x; i < hi; i += BNT) {
         const int g = (int)__ldg(d.x + i);  // grey levels only: pass A checked them
+        if (!in_bounds(g >= 0 && g < 256, &a.bad[ch.slice], BAD_BOUNDS)) continue;
         for (int j = 0; j < C; ++j) mx = fmaxf(mx, fabsf(T[g * FCM_MAX_CLUSTERS + j] - __ldg(d.U0 + (int64_t)j * d.n + i)));
     }
     mx = warp_max(mx);
@@ -400,8 +403,16 @@ __global__ void __launch_bounds__(BNT) k_bins_pass_c(BinArgs a) {
     float* __restrict__ U = d.U;
     for (int i = lo + threadIdx.x; i < hi; i += BNT) {
         const int g = (int)__ldg(d.x + i);
+        if (!in_bounds(g >= 0 && g < 256, &a.bad[ch.slice], BAD_BOUNDS)) continue;
         for (int j = 0; j < C; ++j) __stcs(U + (int64_t)j * d.n + i, T[g * FCM_MAX_CLUSTERS + j]);
     }
+}
+
+// FCM_DEBUG_BOUNDS builds only, last in stream order: the runs of a slice
+// whose guards skipped an access report FCM_FLAG_BOUNDS.
+__global__ void k_bins_bounds_flags(BinArgs a) {
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < a.n_runs; r += gridDim.x * blockDim.x)
+        if (a.bad[a.runs[r].slice] & BAD_BOUNDS) a.results[r].flags |= FCM_FLAG_BOUNDS;
 }
 
 }  // namespace
@@ -586,6 +597,7 @@ cudaError_t launch_bins(const BinArgs& a0, bool write_any, cudaStream_t s) {
     a.phase = 1;
     k_bins_solve<<<a.n_runs, SNT, 0, s>>>(a);
     if (write_any && a.n_chunks > 0) k_bins_pass_c<<<a.n_chunks, BNT, 0, s>>>(a);
+    if (kBoundsChecks && a.n_runs > 0) k_bins_bounds_flags<<<(a.n_runs + 255) / 256, 256, 0, s>>>(a);
     return cudaGetLastError();
 }
 

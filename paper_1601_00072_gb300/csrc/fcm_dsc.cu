@@ -96,6 +96,7 @@ bool on_device(const void* p) {
 
 extern "C" int fcm_dsc(fcm_handle h, const float* U, int64_t n, int C, const uint8_t* truth,
                        const int* class_of_cluster, int n_classes, int64_t* counts, double* dsc) {
+    NvtxRange nvtx_range("fcm_dsc");
     if (!h) return FCM_ERR_INVALID_ARG;
     if (!U || !truth || !class_of_cluster || !dsc) return ctx_invalid(h, "null U, truth, map or dsc");
     if (n < 1 || C < 1 || C > FCM_MAX_CLUSTERS) return ctx_invalid(h, "n >= 1 and C in [1, 8]");

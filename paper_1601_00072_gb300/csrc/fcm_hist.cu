@@ -21,6 +21,7 @@
 #include <cstring>
 
 #include "fcm.h"
+#include "fcm_bounds.cuh"
 #include "fcm_device.cuh"
 #include "fcm_df.cuh"
 #include "fcm_hist_bins.cuh"
@@ -36,7 +37,8 @@ struct alignas(16) HistState {
     double delta, J;
     unsigned d1bits;  // max |U^1 - U^0| over the pixels, as float bits (from U^0)
     int bad;
-    int iters, status, flags, pad;
+    int iters, status, flags;
+    unsigned bounds;  // FCM_FLAG_BOUNDS from a FCM_DEBUG_BOUNDS build's guards
 };
 
 struct HistWorkspace {
@@ -261,6 +263,7 @@ __global__ void __launch_bounds__(HNT) k_hist_delta1(const float* __restrict__ x
     const int64_t stride = (int64_t)gridDim.x * HNT;
     for (int64_t i = (int64_t)blockIdx.x * HNT + threadIdx.x; i < n; i += stride) {
         const int b = (int)__ldg(x + i);
+        if (!in_bounds(b >= 0 && b < 256, &st->bounds)) continue;
 #pragma unroll
         for (int j = 0; j < C; ++j) d = fmaxf(d, fabsf(T[b][j] - __ldg(U0 + (int64_t)j * n + i)));
     }
@@ -332,6 +335,7 @@ __global__ void __launch_bounds__(HNT) k_hist_emit(const float* __restrict__ x, 
     const int64_t stride = (int64_t)gridDim.x * HNT;
     for (int64_t i = (int64_t)blockIdx.x * HNT + threadIdx.x; i < n; i += stride) {
         const int b = (int)__ldg(x + i);
+        if (!in_bounds(b >= 0 && b < 256, const_cast<unsigned*>(&st->bounds))) continue;
 #pragma unroll
         for (int j = 0; j < C; ++j) __stcs(U + (int64_t)j * n + i, T[b * C + j]);
     }
@@ -413,6 +417,7 @@ void fcm_release_hist(fcm_ctx* h) {
 
 extern "C" int fcm_run_hist(fcm_handle h, const float* x, int64_t n, int C, float m, float eps, int max_iter,
                             int init_mode, const float* U0, float* U, float* V, fcm_report* rep) {
+    NvtxRange nvtx_range("fcm_run_hist");
     if (!h) return FCM_ERR_INVALID_ARG;
     if (!x || !U || !V) return ctx_invalid(h, "null x, U or V");
     if (n < 1 || n > ((int64_t)1 << 40)) return ctx_invalid(h, "n must be in [1, 2^40]");
@@ -466,7 +471,7 @@ extern "C" int fcm_run_hist(fcm_handle h, const float* x, int64_t n, int C, floa
         std::memset(rep, 0, sizeof(*rep));
         rep->iters = hs->iters;
         rep->status = hs->status;
-        rep->flags = hs->flags;
+        rep->flags = hs->flags | (int)hs->bounds;
         rep->C = C;
         rep->delta = hs->delta;
         rep->J = hs->J;

@@ -11,9 +11,9 @@ namespace fcm {
 constexpr int NT = 256;                                  // threads per block of the pass
 constexpr int NWARP = NT / 32;
 constexpr int WARP_TILE = 128;                           // pixels per warp tile of the TMA kernels
-constexpr int DCHUNK = 4;  // tiles per grab from the shared part of a pass (whole-run kernels)
-// Issue-side state of one warp's TMA ring in the whole-run kernels (lane 0
-// only, kept in shared memory): copies issued, next tile of the chunk being
+constexpr int DCHUNK = 4;  // tiles per grab from the shared part of a pass (stored-U whole-run kernel)
+// Issue-side state of one warp's TMA ring in the stored-U whole-run kernel
+// (lane 0 only, kept in shared memory): copies issued, next tile of the chunk being
 // issued, pass, index in the fixed share, ring slot, tiles left in the chunk,
 // and the counter value grabbed for the next chunk.
 struct IssueState {
@@ -77,12 +77,13 @@ struct alignas(128) RunState {
     unsigned int ticket;  // last-block-done counter of the current pass
     int launches;         // passes started in this run (loop guard)
     WaitLimits lim;
-    // whole-run kernel: percent of each pass's tiles dealt to the warps in
-    // fixed shares (100: all of them); the rest is taken in chunks from
+    // stored-U whole-run kernel: percent of each pass's tiles dealt to the
+    // warps in fixed shares (100: all of them); the rest is taken in chunks from
     // dyn[pass & 1] (zeroed by the upload of this state, re-zeroed on the
     // device two passes before each reuse)
     int static_pct;
     unsigned int dyn[2];
+    unsigned int bounds;  // FCM_FLAG_BOUNDS from a FCM_DEBUG_BOUNDS build's guards
 };
 constexpr int DEFAULT_STATIC_PCT = 60;
 

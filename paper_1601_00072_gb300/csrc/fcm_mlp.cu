@@ -626,6 +626,7 @@ int fcm_model_loss_grad(fcm_handle h, const float* feats, const float* targets, 
 
 int fcm_model_train(fcm_handle h, const float* feats, const float* targets, const int* Cs, int n, int epochs,
                     int batch, float lr, uint64_t seed, float* last_loss) {
+    NvtxRange nvtx_range("fcm_model_train");
     if (!h || !feats || !targets || !Cs || n < 1 || epochs < 1 || batch < 1 || !(lr > 0.0f))
         return FCM_ERR_INVALID_ARG;
     int rc = need_model(h);
@@ -677,6 +678,7 @@ int fcm_model_train(fcm_handle h, const float* feats, const float* targets, cons
 }
 
 int fcm_features(fcm_handle h, const fcm_slice* slices, int n, float* feats) {
+    NvtxRange nvtx_range("fcm_features");
     const int rc = fcm_features_impl(h, slices, n, feats);
     if (rc) return rc;
     DeviceGuard g(h->device);
@@ -685,10 +687,12 @@ int fcm_features(fcm_handle h, const fcm_slice* slices, int n, float* feats) {
 }
 
 int fcm_predict_centers(fcm_handle h, fcm_slice* slices, int n) {
+    NvtxRange nvtx_range("fcm_predict_centers");
     return predict_v0(h, slices, n, nullptr);
 }
 
 int fcm_run_batched_warm(fcm_handle h, fcm_slice* slices, int n, int options, int* n_cold) {
+    NvtxRange nvtx_range("fcm_run_batched_warm");
     if (!h || !slices || n < 1) return FCM_ERR_INVALID_ARG;
     if (n_cold) *n_cold = 0;
     for (int i = 0; i < n; ++i)

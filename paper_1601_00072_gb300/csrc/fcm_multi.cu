@@ -71,6 +71,7 @@ void fcm_release_multi(fcm_ctx* h) {
 extern "C" int fcm_run_multi(fcm_handle h, const float* x, int64_t n, int D, int C, float m, float eps,
                              int max_iter, int init_mode, const float* U0, float* U, float* V, double* V64,
                              fcm_report* rep) {
+    NvtxRange nvtx_range("fcm_run_multi");
     if (!h) return FCM_ERR_INVALID_ARG;
     if (!x || !U || !V) return ctx_invalid(h, "null x, U or V");
     if (n < 1 || n > ((int64_t)1 << 40)) return ctx_invalid(h, "n must be in [1, 2^40]");

@@ -12,16 +12,10 @@
 // stop decision.
 //
 // Structure as the stored-U run kernel: one cooperative launch, each warp
-// streams 128-pixel tiles through a private ring of TMA bulk copies across
-// all passes, every block adds the per-block sums in the same order after a
-// bounded grid barrier, so all blocks take the same decisions. Tiles are dealt
-// in the same two parts: a fixed warp share (st->static_pct percent of the
-// tiles) that the ring streams across passes, and the rest of each pass in
-// chunks of DCHUNK tiles from a per-pass counter, so warps on faster SMs take
-// more of it. No tile is re-read across warps: U^0 is an input, and U is only
-// written, in the last pass.
-#include <climits>
-
+// streams its own 128-pixel tiles through a private ring of TMA bulk copies
+// across all passes, every block adds the per-block sums in the same order
+// after a bounded grid barrier, so all blocks take the same decisions.
+#include "fcm_bounds.cuh"
 #include "fcm_device.cuh"
 #include "fcm_exchange.cuh"
 #include "fcm_internal.h"
@@ -156,10 +150,6 @@ __global__ void __launch_bounds__(NT, (C <= 4 ? 3 : 2)) k_fcm_run_rc(RunState* _
     __shared__ DF s_vq[C];
     __shared__ int s_empty[C];
     __shared__ int s_err;
-    // what each ring stage holds: tile and pass (pass INT_MAX: nothing)
-    __shared__ int64_t s_tile[NWARP][Sh::STAGES];
-    __shared__ int s_pass[NWARP][Sh::STAGES];
-    __shared__ IssueState s_iss[NWARP];
 
     const float* __restrict__ x = st->x;
     const float* U0 = st->Uprev;
@@ -187,14 +177,9 @@ __global__ void __launch_bounds__(NT, (C <= 4 ? 3 : 2)) k_fcm_run_rc(RunState* _
     const int64_t nwarps = (int64_t)gridDim.x * NWARP;
     const int64_t gw = (int64_t)blockIdx.x * NWARP + warp;
     const int64_t ntiles = (n + WTILE - 1) / WTILE;
-    // fixed share: ks tiles per warp when every warp has more than a ring of
-    // them; otherwise every tile in fixed shares (nk per warp)
-    const int64_t ks = ntiles * (int64_t)st->static_pct / 100 / nwarps;
-    const bool shared_part = st->static_pct < 100 && ks > Sh::STAGES;
-    const int nk = shared_part ? (int)ks : (int)(ntiles > gw ? (ntiles - 1 - gw) / nwarps + 1 : 0);
-    const int64_t n_fixed = shared_part ? ks * nwarps : ntiles;
-    const int64_t n_chunks = (ntiles - n_fixed + DCHUNK - 1) / DCHUNK;
+    const int nk = (int)(ntiles > gw ? (ntiles - 1 - gw) / nwarps + 1 : 0);
     const int look = nk < Sh::STAGES ? nk : Sh::STAGES;
+    const int64_t tile_stride = nwarps * (int64_t)WTILE;
     const int npass = 2 + max_iter;  // INIT, max_iter iterations, the U write
     const uint32_t wait_limit = st->lim.tma_polls, grid_spins = st->lim.grid_spins;
     const unsigned phantoms = st->lim.phantoms;
@@ -203,29 +188,31 @@ __global__ void __launch_bounds__(NT, (C <= 4 ? 3 : 2)) k_fcm_run_rc(RunState* _
 
     if (lane == 0) {
 #pragma unroll
-        for (int s = 0; s < Sh::STAGES; ++s) {
-            mbar_init(&full[s], 1);
-            s_pass[warp][s] = INT_MAX;
-        }
+        for (int s = 0; s < Sh::STAGES; ++s) mbar_init(&full[s], 1);
         mbar_fence_init();
     }
     if (threadIdx.x == 0) s_err = 0;
     __syncthreads();
 
-    // Issue side (lane 0), kept in shared memory so that it takes no
-    // registers during the tile work: pass ip, index ik in the fixed share,
-    // the chunk being issued (next tile cb, cl tiles left), the grab for the
-    // next chunk, ring slot is, and the copies issued so far.
-    IssueState& q = s_iss[warp];
-    if (lane == 0) q = IssueState{0, 0, 0, 0, 0, 0, 0u};
-    auto issue_tile = [&](int64_t tile, int ip) {
-        const int64_t i0 = tile * WTILE;
+    // Issue side (lane 0): pass ip, tile ik of the next load, ring slot is.
+    int ip = 0, ik = 0, is = 0;
+    int64_t issued = 0;
+    auto issue_next = [&]() {
+        if (ip >= npass || nk == 0) return;
+        const int64_t i0 = gw * (int64_t)WTILE + ik * tile_stride;
         const uint32_t bytes = (uint32_t)min((int64_t)WTILE, n - i0) * 4u;  // multiple of 16
         const bool with_u = INIT == P_ACCUM0 && ip <= 1;
-        const int is = q.is;
         float* dst = ring + is * Sh::STAGE_FLOATS;
-        s_tile[warp][is] = tile;
-        s_pass[warp][is] = ip;
+        if (!in_bounds(i0 >= 0 && i0 < n && i0 % 4 == 0, &st->bounds)) {
+            mbar_expect_tx(&full[is], 0u);  // arrive without copies: the consumer's tile is empty
+            ++issued;
+            if (++ik == nk) {
+                ik = 0;
+                ++ip;
+            }
+            if (++is == Sh::STAGES) is = 0;
+            return;
+        }
         mbar_expect_tx(&full[is], bytes * (with_u ? 1 + C : 1));
         bulk_g2s(dst, x + i0, bytes, &full[is], pol_x);
         if (with_u) {
@@ -233,38 +220,15 @@ __global__ void __launch_bounds__(NT, (C <= 4 ? 3 : 2)) k_fcm_run_rc(RunState* _
             for (int j = 0; j < C; ++j)
                 bulk_g2s(dst + (1 + j) * WTILE, U0 + (int64_t)j * n + i0, bytes, &full[is], pol_u);
         }
-        ++q.issued;
-        q.is = is + 1 == Sh::STAGES ? 0 : is + 1;
-    };
-    auto issue_next = [&]() {
-        while (q.ip < npass && nk > 0) {
-            const int ip = q.ip;
-            if (q.ik < nk) {
-                const int64_t tile = gw + (int64_t)q.ik * nwarps;
-                if (++q.ik == nk && shared_part) q.grab = atomicAdd(&st->dyn[ip & 1], 1u);  // first chunk, ahead
-                issue_tile(tile, ip);
-                return;
-            }
-            if (q.cl == 0) {
-                if (shared_part && (int64_t)q.grab < n_chunks) {
-                    q.cb = n_fixed + (int64_t)q.grab * DCHUNK;
-                    q.cl = (int)min((int64_t)DCHUNK, ntiles - q.cb);
-                    q.grab = atomicAdd(&st->dyn[ip & 1], 1u);  // the chunk after this one, ahead
-                } else {
-                    ++q.ip;  // pass ip is dealt out: on to the next pass's fixed share
-                    q.ik = 0;
-                    continue;
-                }
-            }
-            --q.cl;
-            issue_tile(q.cb++, ip);
-            return;
+        ++issued;
+        if (++ik == nk) {
+            ik = 0;
+            ++ip;
         }
-        s_pass[warp][q.is] = INT_MAX;  // nothing more to load
+        if (++is == Sh::STAGES) is = 0;
     };
     if (lane == 0)
         for (int t = 0; t < look; ++t) issue_next();
-    __syncwarp();
 
     int cs = 0;
     uint32_t parity = 0;
@@ -279,14 +243,14 @@ __global__ void __launch_bounds__(NT, (C <= 4 ? 3 : 2)) k_fcm_run_rc(RunState* _
 #pragma unroll
             for (int j = 0; j < C; ++j) a.bad |= !finite_f(v[j]);
         }
-        // ---- the pass over this warp's tiles: the ring's items of pass p ----
-        while (s_pass[warp][cs] == p) {
+        // ---- the pass over this warp's tiles ----
+        int64_t i0 = gw * (int64_t)WTILE;
+        for (int k = 0; k < nk; ++k, i0 += tile_stride) {
             const bool ok = mbar_wait_bounded(&full[cs], parity, wait_limit);
             if (__any_sync(0xffffffffu, !ok)) {
                 err = true;
                 break;
             }
-            const int64_t i0 = s_tile[warp][cs] * WTILE;
             const int cnt = (int)min((int64_t)WTILE, n - i0);
             const float* sb = ring + cs * Sh::STAGE_FLOATS;
             if (emit)
@@ -302,7 +266,6 @@ __global__ void __launch_bounds__(NT, (C <= 4 ? 3 : 2)) k_fcm_run_rc(RunState* _
             __syncwarp();
             ++consumed;
             if (lane == 0) issue_next();
-            __syncwarp();  // the stage records written by lane 0
             if (++cs == Sh::STAGES) {
                 cs = 0;
                 parity ^= 1u;
@@ -368,9 +331,6 @@ __global__ void __launch_bounds__(NT, (C <= 4 ? 3 : 2)) k_fcm_run_rc(RunState* _
         __syncthreads();
         const float delta = s_mx[0];
         const bool bad = s_mx[1] != 0.0f, tmo = s_mx[2] != 0.0f;
-        // every chunk of pass p was taken before this barrier; its counter
-        // serves pass p + 2, whose first grab follows the next barrier
-        if (blockIdx.x == 0 && threadIdx.x == 0) st->dyn[p & 1] = 0u;
         bool update = false;
         if (tmo) {
             status = FCM_ERR_TIMEOUT;
@@ -437,7 +397,7 @@ __global__ void __launch_bounds__(NT, (C <= 4 ? 3 : 2)) k_fcm_run_rc(RunState* _
     if (lane == 0) {
         int ds = cs;
         uint32_t dp = parity;
-        for (int64_t t = consumed; t < q.issued; ++t) {
+        for (int64_t q = consumed; q < issued; ++q) {
             mbar_wait_bounded(&full[ds], dp, wait_limit);
             if (++ds == Sh::STAGES) {
                 ds = 0;

@@ -86,6 +86,7 @@ bool on_device(const void* p) {
 extern "C" {
 
 int fcm_init_dirichlet(fcm_handle h, int64_t n, int C, uint64_t seed, float* U) {
+    NvtxRange nvtx_range("fcm_init_dirichlet");
     if (!h) return FCM_ERR_INVALID_ARG;
     if (n < 1 || n > ((int64_t)1 << 40) || C < 1 || C > FCM_MAX_CLUSTERS || !U)
         return ctx_invalid(h, "n >= 1, C in [1, 8] and a device U are required");
@@ -101,6 +102,7 @@ int fcm_init_dirichlet(fcm_handle h, int64_t n, int C, uint64_t seed, float* U) 
 
 int fcm_run_seeded(fcm_handle h, const float* x, int64_t n, int C, float m, float eps, int max_iter,
                    uint64_t seed, float* U, float* V, int options, fcm_report* rep) {
+    NvtxRange nvtx_range("fcm_run_seeded");
     const int rc = fcm_init_dirichlet(h, n, C, seed, U);
     if (rc) return rc;
     return fcm_run(h, x, n, C, m, eps, max_iter, FCM_INIT_U, nullptr, U, V, options, rep);

@@ -31,6 +31,7 @@
 // No block waits for another: the ticket only elects the finisher.
 #include <climits>
 
+#include "fcm_bounds.cuh"
 #include "fcm_device.cuh"
 #include "fcm_exchange.cuh"
 #include "fcm_internal.h"
@@ -441,6 +442,10 @@ __global__ void __launch_bounds__(NT, 2) k_fcm_pass_tma(RunState* __restrict__ s
         const int64_t i0 = (gw + k * nwarps) * (int64_t)WTILE;
         const uint32_t bytes = (uint32_t)min((int64_t)WTILE, n - i0) * 4u;  // multiple of 16
         float* dst = ring + s * Sh::STAGE_FLOATS;
+        if (!in_bounds(i0 >= 0 && i0 < n && i0 % 4 == 0 && s < Sh::STAGES, &st->bounds)) {
+            mbar_expect_tx(&full[s], 0u);  // arrive without copies: the consumer skips the tile
+            return;
+        }
         mbar_expect_tx(&full[s], bytes * Sh::ROWS);
         bulk_g2s(dst, x + i0, bytes, &full[s], pol_x);
         if (PASS != P_INITV) {
@@ -597,8 +602,15 @@ __global__ void __launch_bounds__(NT, 2) k_fcm_run_tma(RunState* __restrict__ st
         const float* Usrc = (ip == 0 || (ip == 1 && INIT == P_ACCUM0)) ? U0 : U;
         const int is = q.is;
         float* dst = ring + is * Sh::STAGE_FLOATS;
-        s_tile[warp][is] = tile;
         s_pass[warp][is] = ip;
+        if (!in_bounds(tile >= 0 && tile < ntiles && is < Sh::STAGES, &st->bounds)) {
+            s_tile[warp][is] = -1;  // the consumer skips it
+            mbar_expect_tx(&full[is], 0u);  // arrive without copies
+            ++q.issued;
+            q.is = is + 1 == Sh::STAGES ? 0 : is + 1;
+            return;
+        }
+        s_tile[warp][is] = tile;
         mbar_expect_tx(&full[is], bytes * (with_u ? 1 + C : 1));
         bulk_g2s(dst, x + i0, bytes, &full[is], pol_x);
         if (with_u) {
@@ -659,13 +671,17 @@ __global__ void __launch_bounds__(NT, 2) k_fcm_run_tma(RunState* __restrict__ st
                 err = true;
                 break;
             }
-            const int64_t i0 = s_tile[warp][cs] * WTILE;
+            const int64_t tile = s_tile[warp][cs];
+            const int64_t i0 = tile * WTILE;
             const int cnt = (int)min((int64_t)WTILE, n - i0);
             const float* sb = ring + cs * Sh::STAGE_FLOATS;
-            if (p == 0)
+            if (kBoundsChecks && tile < 0) {
+                // a copy the guards skipped: nothing to compute or store
+            } else if (p == 0) {
                 tile_work<C, MK, INIT>(sb, cnt, i0, lane, U, n, v, v2, m, inv_m1, pol_u, a);
-            else
+            } else {
                 tile_work<C, MK, P_ITER>(sb, cnt, i0, lane, U, n, v, v2, m, inv_m1, pol_u, a);
+            }
             // this lane's stores of U must precede any TMA re-read of the tile:
             // the warp's own (fixed share, next pass) or another warp's after
             // the grid barrier (shared part)

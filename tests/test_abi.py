@@ -84,3 +84,17 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
     monkeypatch.setattr(_lib, "library_path", lambda: str(tmp_path / "libfcm_gb300.so"))
     with pytest.raises(RuntimeError, match="not built"):
         _lib.load()
+
+
+def test_bounds_variant_is_a_separate_build():
+    """FCM_DEBUG_BOUNDS=1 selects the bounds-guarded variant: its own build
+    folder and -DFCM_DEBUG_BOUNDS on every translation unit."""
+    import subprocess
+    import sys
+    code = ("from paper_1601_00072_gb300 import _build, _lib; "
+            "print(_build.LIB); print(_lib.library_path()); print('-DFCM_DEBUG_BOUNDS=1' in _build.FLAGS)")
+    for val, folder, flag in (("1", "_build_bounds", "True"), ("0", "_build", "False")):
+        env = dict(os.environ, FCM_DEBUG_BOUNDS=val)
+        out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, check=True,
+                             cwd=ROOT).stdout.split()
+        assert out[0] == out[1] and os.path.basename(os.path.dirname(out[0])) == folder and out[2] == flag

@@ -1,0 +1,99 @@
+"""The bounds-guarded build (FCM_DEBUG_BOUNDS=1) against the normal build
+(needs a GPU).
+
+compute-sanitizer is closed on this machine, so the library has a build whose
+kernels check the indices of their TMA copies and lookup tables, skip an
+out-of-range access and report FCM_FLAG_BOUNDS. The guards add no
+arithmetic, so on valid inputs the guarded build must give the normal build's
+bits (on the paths that are deterministic) and report no skipped access. Each
+build runs in its own process, because the variant is chosen when the
+library is loaded.
+"""
+import os
+import subprocess
+import sys
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+CASES = r"""
+import sys
+import numpy as np
+import torch
+sys.path.insert(0, ROOT)
+import phantom
+from paper_1601_00072_gb300 import _build, _lib
+_build.build()
+from paper_1601_00072_gb300.fcm import FCM, Slice
+
+out = {"lib": np.array(_lib.library_path())}
+h = FCM(0)
+img, _ = phantom.phantom2d(21, 200, 200, 8.0)
+x = torch.from_numpy(img.reshape(-1).astype(np.float32)).cuda()
+u0 = torch.from_numpy(phantom.dirichlet_u0((21, 1), 4, x.numel())).cuda()
+flags = []
+for name, kw in (("run", {}), ("pass", {"persistent": False}), ("loop", {"persistent": False, "graph": False}),
+                 ("plain", {"tma": False}), ("rc", {"recompute": True})):
+    r = h.run(x, 4, 2.0, 1e-5, 300, U0=u0, **kw)
+    out[name + "_U"], out[name + "_V"], out[name + "_it"] = r.U.cpu().numpy(), r.V.cpu().numpy(), np.array(r.iters)
+    flags.append(r.flags)
+r = h.run_hist(x, 4, 2.0, 1e-5, 300, U0=u0)
+out["hist_U"], out["hist_V"], out["hist_it"] = r.U.cpu().numpy(), r.V.cpu().numpy(), np.array(r.iters)
+flags.append(r.flags)
+# 4 M pixels: the default whole-run kernel hands part of every pass out at run time
+big, _ = phantom.phantom2d(22, 2048, 2048, 10.0)
+xb = torch.from_numpy(big.reshape(-1).astype(np.float32)).cuda()
+ub = torch.from_numpy(phantom.dirichlet_u0((22, 1), 4, xb.numel())).cuda()
+r = h.run(xb, 4, 2.0, 1e-5, 300, U0=ub)
+out["big_V"], out["big_it"] = r.V.cpu().numpy(), np.array(r.iters)
+flags.append(r.flags)
+r = h.run(xb, 4, 2.0, 1e-5, 300, U0=ub, deterministic=True)
+out["bigdet_U"], out["bigdet_V"], out["bigdet_it"] = r.U.cpu().numpy(), r.V.cpu().numpy(), np.array(r.iters)
+flags.append(r.flags)
+# a batch in the histogram domain
+sl = []
+for i, (hh, ww, C) in enumerate(((64, 80, 3), (131, 97, 4), (256, 256, 5))):
+    im, _ = phantom.phantom2d(30 + i, hh, ww, 6.0)
+    xs = torch.from_numpy(im.reshape(-1).astype(np.float32)).cuda()
+    sl.append(Slice(x=xs, C=C, U0=torch.from_numpy(phantom.dirichlet_u0((30 + i, 1), C, xs.numel())).cuda()))
+h.run_batched_hist(sl)
+for i, s in enumerate(sl):
+    out[f"bh{i}_U"], out[f"bh{i}_V"], out[f"bh{i}_it"] = s.U.cpu().numpy(), np.asarray(s.V.cpu()), np.array(s.iters)
+    flags.append(s.flags)
+out["flags"] = np.array(flags)
+h.close()
+np.savez(sys.argv[1], **out)
+"""
+
+
+def _run(tmp_path, name, bounds):
+    env = dict(os.environ)
+    env.pop("FCM_DEBUG_BOUNDS", None)
+    if bounds:
+        env["FCM_DEBUG_BOUNDS"] = "1"
+    path = str(tmp_path / f"{name}.npz")
+    script = f"ROOT = {ROOT!r}\n" + CASES
+    subprocess.run([sys.executable, "-c", script, path], env=env, check=True, timeout=1200, cwd=ROOT)
+    return dict(np.load(path))
+
+
+def test_bounds_build_matches_normal_build(tmp_path):
+    from paper_1601_00072_gb300 import _lib
+    a = _run(tmp_path, "normal", False)
+    b = _run(tmp_path, "bounds", True)
+    assert str(a["lib"]).endswith(os.path.join("_build", "libfcm_gb300.so"))
+    assert str(b["lib"]).endswith(os.path.join("_build_bounds", "libfcm_gb300.so"))
+    # no guard fired on valid inputs, in either build
+    assert not np.any(a["flags"] & _lib.FCM_FLAG_BOUNDS) and not np.any(b["flags"] & _lib.FCM_FLAG_BOUNDS)
+    # the guards add no arithmetic: the deterministic paths give the same bits
+    for k in a:
+        if k in ("lib", "flags") or k.startswith("big_"):
+            continue
+        assert np.array_equal(a[k], b[k]), k
+    # the run-time shared part rounds its block sums in timing order
+    assert abs(int(a["big_it"]) - int(b["big_it"])) <= 1
+    assert np.max(np.abs(a["big_V"] - b["big_V"]) / np.maximum(np.abs(a["big_V"]), 1.0)) <= 1e-6
