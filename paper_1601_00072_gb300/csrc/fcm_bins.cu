@@ -44,8 +44,12 @@ constexpr int BNT = HNT;                 // threads of every kernel here (one pe
 constexpr unsigned BAD_BOUNDS = 4u;      // bit 2 of BinArgs::bad
 constexpr int BNW = BNT / 32;
 constexpr int PX_PER_THREAD = BIN_CHUNK / BNT;
-constexpr int LOADS = 4;                 // pixels per thread whose loads are issued together
-static_assert(PX_PER_THREAD % LOADS == 0, "chunk");
+// pixels per thread whose loads pass A issues together: more for fewer
+// clusters (each pixel loads x and C memberships), as many as fit in the
+// registers of three CTAs per SM without spilling
+template <int C>
+constexpr int loads_a() { return C <= 3 ? 8 : (C == 4 ? 6 : 4); }
+constexpr int LOADS_C = 8;               // pixels per thread whose x loads pass C issues together
 
 __device__ __forceinline__ float uint_to_floatbits(unsigned u) { return __uint_as_float(u); }
 
@@ -72,6 +76,7 @@ __device__ __noinline__ void pass_a_chunk(const BinArgs& a, const SliceDesc& d, 
     for (int q = 0; q < 2 * C; ++q) acc[q] = DF{0.0f, 0.0f};
     bool bad_x = false, bad_u = false;
     unsigned* hw = sh.sub[warp];
+    constexpr int LOADS = loads_a<C>();
     for (int i0 = lo + t; i0 < hi; i0 += BNT * LOADS) {
         float xc[LOADS], uc[LOADS][C];
 #pragma unroll
@@ -90,10 +95,9 @@ __device__ __noinline__ void pass_a_chunk(const BinArgs& a, const SliceDesc& d, 
             const int i = i0 + q * BNT;
             if (i >= hi) break;
             const float xi = xc[q];
-            const bool good = grey_level(xi);
-            bad_x |= !good;
-            if (!good) continue;
-            const int g = (int)xi;
+            const int g = grey_index(xi);
+            bad_x |= g < 0;
+            if (g < 0) continue;
             atomicAdd(&hw[g], 1u);
             sh.rep[g] = i;  // any pixel of the grey level will do
             if (from_u) {
@@ -139,7 +143,7 @@ __device__ __noinline__ void pass_a_chunk(const BinArgs& a, const SliceDesc& d, 
     }
 }
 
-__global__ void __launch_bounds__(BNT) k_bins_pass_a(BinArgs a) {
+__global__ void __launch_bounds__(BNT, 3) k_bins_pass_a(BinArgs a) {
     __shared__ PassAShared sh;
     const int k = blockIdx.x;
     if (k >= a.n_chunks) return;
@@ -401,10 +405,20 @@ __global__ void __launch_bounds__(BNT) k_bins_pass_c(BinArgs a) {
     __syncthreads();
     const int lo = ch.lo, hi = (int)min((int64_t)lo + BIN_CHUNK, d.n);
     float* __restrict__ U = d.U;
-    for (int i = lo + threadIdx.x; i < hi; i += BNT) {
-        const int g = (int)__ldg(d.x + i);
-        if (!in_bounds(g >= 0 && g < 256, &a.bad[ch.slice], BAD_BOUNDS)) continue;
-        for (int j = 0; j < C; ++j) __stcs(U + (int64_t)j * d.n + i, T[g * FCM_MAX_CLUSTERS + j]);
+    for (int i0 = lo + threadIdx.x; i0 < hi; i0 += BNT * LOADS_C) {
+        int g[LOADS_C];
+#pragma unroll
+        for (int q = 0; q < LOADS_C; ++q) {
+            const int i = i0 + q * BNT;
+            g[q] = i < hi ? (int)__ldg(d.x + i) : 0;
+        }
+#pragma unroll
+        for (int q = 0; q < LOADS_C; ++q) {
+            const int i = i0 + q * BNT;
+            if (i >= hi) break;
+            if (!in_bounds(g[q] >= 0 && g[q] < 256, &a.bad[ch.slice], BAD_BOUNDS)) continue;
+            for (int j = 0; j < C; ++j) __stcs(U + (int64_t)j * d.n + i, T[g[q] * FCM_MAX_CLUSTERS + j]);
+        }
     }
 }
 

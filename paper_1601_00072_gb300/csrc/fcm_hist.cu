@@ -58,9 +58,12 @@ namespace {
 constexpr int HCHUNK = 4;  // pixels per thread whose loads are issued together in the first pass
 
 // Pass over the pixels: histogram, input checks, and (from U^0) the
-// numerators and denominators of V^1 (Eq. 3) as per-block FP64 slots.
-// Up to C = 4, four blocks per SM fit in 64 registers without spills: twice
-// the warps of an unbounded build to cover the loads' latency.
+// numerators and denominators of V^1 (Eq. 3) as per-block FP64 slots. A
+// negative U^0 entry is caught here; a NaN or infinite one makes the sums of
+// V^1 non-finite, which the next kernel rejects (so does an entry whose u^m
+// overflows FP32).
+// Up to C = 4, four blocks per SM fit in 64 registers (a few bytes spill at
+// C = 4): twice the warps of an unbounded build to cover the loads' latency.
 template <int C, int MK, bool FROM_U>
 __global__ void __launch_bounds__(HNT, C <= 4 ? 4 : 2) k_hist_pass0(const float* __restrict__ x, const float* __restrict__ U0,
                                                    int64_t n, float m, HistState* st, double* __restrict__ part) {
@@ -72,6 +75,7 @@ __global__ void __launch_bounds__(HNT, C <= 4 ? 4 : 2) k_hist_pass0(const float*
 #pragma unroll
     for (int q = 0; q < 2 * C; ++q) acc[q] = DF{0.0f, 0.0f};
     bool bad = false;
+    float umin = 0.0f;  // smallest U^0 entry seen (negative entries are bad input)
     const int64_t stride = (int64_t)gridDim.x * HNT;
     const int lane_id = threadIdx.x & 31;
     unsigned* hw = hs[threadIdx.x >> 5];
@@ -99,16 +103,17 @@ __global__ void __launch_bounds__(HNT, C <= 4 ? 4 : 2) k_hist_pass0(const float*
             if (i - lane_id >= n) break;  // warp-uniform
             const bool in = i < n;
             const float xi = xc[q];
-            const bool good = in && grey_level(xi);
+            const int g = grey_index(xi);
+            const bool good = in && g >= 0;
             bad |= in && !good;
             // shared-memory atomics: lanes of a warp on the same grey level are
             // serialised by the hardware; counts are exact in any order
-            if (good) atomicAdd(&hw[(int)xi], 1u);
+            if (good) atomicAdd(&hw[g], 1u);
             if (FROM_U && good) {
 #pragma unroll
                 for (int j = 0; j < C; ++j) {
                     const float u0 = uc[q][j];
-                    bad |= !(u0 >= 0.0f) || !finite_f(u0);
+                    umin = fminf(umin, u0);  // NaN and infinities show in the sums instead
                     const float wt = pow_m<MK>(u0, m);
                     num[j] = fmaf(wt, xi, num[j]);
                     den[j] += wt;
@@ -129,7 +134,7 @@ __global__ void __launch_bounds__(HNT, C <= 4 ? 4 : 2) k_hist_pass0(const float*
         for (int v = 0; v < HNT / 32; ++v) t += hs[v][b];
         if (t) atomicAdd(&st->hist[b], (unsigned long long)t);
     }
-    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(&st->bad, 1);
+    if (__syncthreads_or(bad || umin < 0.0f) && threadIdx.x == 0) atomicOr(&st->bad, 1);
     if (!FROM_U) return;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
@@ -208,6 +213,23 @@ __global__ void __launch_bounds__(HNT) k_hist_init(HistState* st, const double* 
             for (int q = 0; q < 2 * C; ++q) s[q] += part[(int64_t)b * 2 * C + q];
         }
         block_sums<2 * C>(s, mx, red, tot);
+        bool finite = true;
+#pragma unroll
+        for (int q = 0; q < 2 * C; ++q) finite &= isfinite(tot[q]);
+        if (!finite) {
+            // a NaN or infinite U^0 entry (pass 0 checks only for negative ones)
+            if (threadIdx.x == 0) {
+                st->bad = 1;
+                st->status = FCM_ERR_BAD_INPUT;
+                st->iters = 0;
+#pragma unroll
+                for (int j = 0; j < C; ++j) {
+                    st->V[j] = st->V0[j];
+                    st->V64[j] = st->V0[j];
+                }
+            }
+            return;
+        }
     } else {
         const int b = threadIdx.x;
         const double hb = (double)st->hist[b];

@@ -18,6 +18,19 @@ __device__ __forceinline__ bool grey_level(float v) {
     return v >= 0.0f && v <= 255.0f && v == rintf(v);  // false for NaN
 }
 
+// The grey level of v when v is an integer in [0, 255], else -1 (the same
+// test as grey_level, with the index). Adding 1.5 * 2^23 rounds any
+// |v| < 2^22 to an integer held in the low mantissa bits; v is that integer
+// exactly when subtracting the constant gives v back. NaN fails the
+// comparison; infinities and values outside [0, 255] give an index outside
+// [0, 255] (as unsigned).
+__device__ __forceinline__ int grey_index(float v) {
+    constexpr float kShift = 12582912.0f;  // 1.5 * 2^23
+    const float t = __fadd_rn(v, kShift);
+    const int g = __float_as_int(t) - __float_as_int(kShift);
+    return ((unsigned)g <= 255u && __fsub_rn(t, kShift) == v) ? g : -1;
+}
+
 // The loop runs in one CTA of HNT threads, thread b holding grey level b.
 // A sum over the bins is taken in two steps: a five-level FP32 xor tree in
 // each warp (non-negative terms: at most five roundings, no cancellation),

@@ -44,10 +44,14 @@ for name, kw in (("run", {}), ("pass", {"persistent": False}), ("loop", {"persis
 r = h.run_hist(x, 4, 2.0, 1e-5, 300, U0=u0)
 out["hist_U"], out["hist_V"], out["hist_it"] = r.U.cpu().numpy(), r.V.cpu().numpy(), np.array(r.iters)
 flags.append(r.flags)
-# 4 M pixels: the default whole-run kernel hands part of every pass out at run time
-big, _ = phantom.phantom2d(22, 2048, 2048, 10.0)
+# 4 M pixels: the default whole-run kernel hands part of every pass out at run
+# time. This phantom is one whose FP64 trajectory is stable at the FP32
+# rounding scale (the oracle restarted from V^1 perturbed by 1e-6 stops at the
+# same iteration); key 22 with sigma 10 is not (its restarts differ by 98
+# iterations and relabel the clusters), so rounding alone could move it.
+big, _ = phantom.phantom2d(24, 2048, 2048, 8.0)
 xb = torch.from_numpy(big.reshape(-1).astype(np.float32)).cuda()
-ub = torch.from_numpy(phantom.dirichlet_u0((22, 1), 4, xb.numel())).cuda()
+ub = torch.from_numpy(phantom.dirichlet_u0((24, 1), 4, xb.numel())).cuda()
 r = h.run(xb, 4, 2.0, 1e-5, 300, U0=ub)
 out["big_V"], out["big_it"] = r.V.cpu().numpy(), np.array(r.iters)
 flags.append(r.flags)

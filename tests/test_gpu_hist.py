@@ -139,12 +139,22 @@ def test_non_grey_level_input_is_rejected(fcm, bad):
     assert g.status == -4
 
 
-def test_invalid_u0_is_rejected(fcm):
+@pytest.mark.parametrize("bad", ["negative", "nan", "inf", "last"])
+@pytest.mark.parametrize("m", [2.0, 2.5])
+def test_invalid_u0_is_rejected(fcm, bad, m):
+    """A negative entry is caught in the pixel pass; a NaN or infinite one
+    through the non-finite V^1 sums it produces (m = 2.5 takes the generic
+    power). The handle runs a good input correctly afterwards."""
     x, _, u0, C = phantom.single_image("phantom200")
+    good = u0
     u0 = u0.copy()
-    u0[1, 5] = -0.25
-    g, *_ = gpu_hist(fcm, x, C, 2.0, u0=u0, raise_on_error=False)
+    where = (C - 1, x.size - 1) if bad == "last" else (1, 5)
+    u0[where] = {"negative": -0.25, "nan": np.nan, "inf": np.inf, "last": np.nan}[bad]
+    g, *_ = gpu_hist(fcm, x, C, m, u0=u0, raise_on_error=False)
     assert g.status == -4
+    g, gU, gV = gpu_hist(fcm, x, C, m, u0=good)
+    o = oracle_q(x, C, m, EPS, MAX_ITER, u0=good)
+    assert abs(g.iters - o["iters"]) <= 1 and g.status == 0
 
 
 def test_repeatable(fcm):
