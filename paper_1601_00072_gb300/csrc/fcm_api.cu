@@ -80,6 +80,18 @@ int default_static_pct() {
     return DEFAULT_STATIC_PCT;
 }
 
+// Grid of a whole-run kernel for n pixels when at most max_blocks blocks are
+// co-resident: the fewest blocks that keep the largest number of 128-pixel
+// tiles per warp that max_blocks would give, so every warp holds about the
+// same number of tiles (8,192 tiles on 304 blocks would leave a third of the
+// warps one tile more than the rest; 256 blocks give each warp 4).
+int run_grid(int64_t n, int64_t max_blocks) {
+    if (max_blocks < 1) return 0;
+    const int64_t ntiles = (n + WARP_TILE - 1) / WARP_TILE;
+    const int64_t per_warp = (ntiles + max_blocks * NWARP - 1) / (max_blocks * NWARP);
+    return (int)std::max<int64_t>(1, (ntiles + per_warp * NWARP - 1) / (per_warp * NWARP));
+}
+
 bool is_device_pointer(const void* p) {
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
@@ -502,9 +514,7 @@ int fcm_run(fcm_handle h, const float* x, int64_t n, int C, float m, float eps, 
         return ctx_invalid(h, "FCM_OPT_RECOMPUTE needs n % 4 == 0, 16-byte-aligned rows and cooperative launch");
     if (recompute ||
         (aligned && h->coop && !(options & (FCM_OPT_NO_TMA | FCM_OPT_NO_PERSISTENT | FCM_OPT_NO_GRAPH)))) {
-        const int bps = blocks_per_sm(h, krun, run_smem);
-        const int64_t want = (n + (int64_t)WARP_TILE * NWARP - 1) / ((int64_t)WARP_TILE * NWARP);
-        run_blocks = (int)std::min<int64_t>(want, (int64_t)h->num_sms * bps);
+        run_blocks = run_grid(n, (int64_t)h->num_sms * blocks_per_sm(h, krun, run_smem));
     }
     if (run_blocks > 0) {
         // the whole run: one cooperative launch (all blocks co-resident)
@@ -609,9 +619,7 @@ int fcm_run_stream(fcm_handle h, int n_images, const float* const* x, int64_t n,
     const bool recompute = (options & FCM_OPT_RECOMPUTE) != 0;
     const void* krun = recompute ? (const void*)g_rc.run[C][mk][0] : (const void*)g_table.run[C][mk][0];
     const int run_smem = recompute ? g_rc.smem[C][0] : g_table.run_smem[C];
-    const int bps = blocks_per_sm(h, krun, run_smem);
-    const int64_t want = (n + (int64_t)WARP_TILE * NWARP - 1) / ((int64_t)WARP_TILE * NWARP);
-    const int run_blocks = (int)std::min<int64_t>(want, (int64_t)h->num_sms * bps);
+    const int run_blocks = run_grid(n, (int64_t)h->num_sms * blocks_per_sm(h, krun, run_smem));
     if (run_blocks < 1) return ctx_invalid(h, "the whole-run kernel does not fit on this device");
 
     // the copy streams start behind the work already queued on the handle's stream
