@@ -74,6 +74,7 @@ extern "C" {
 #define FCM_ERR_CUDA (-2)        /* a CUDA runtime call failed               */
 #define FCM_ERR_OOM (-3)         /* workspace allocation failed              */
 #define FCM_ERR_BAD_INPUT (-4)   /* NaN/Inf in x or V0, or NaN/Inf/negative U0 */
+#define FCM_ERR_NONFINITE FCM_ERR_BAD_INPUT /* the same code, named after its commonest cause */
 #define FCM_ERR_TIMEOUT (-5)     /* a bounded device-side wait gave up       */
 #define FCM_ERR_TOO_LARGE (-6)   /* beyond a fixed limit of fcm_run_noalloc  */
 

@@ -17,6 +17,7 @@ FCM_ERR_INVALID_ARG = -1
 FCM_ERR_CUDA = -2
 FCM_ERR_OOM = -3
 FCM_ERR_BAD_INPUT = -4
+FCM_ERR_NONFINITE = FCM_ERR_BAD_INPUT
 FCM_ERR_TIMEOUT = -5
 FCM_ERR_TOO_LARGE = -6
 FCM_NOALLOC_MAX_BLOCKS = 512
