@@ -7,7 +7,7 @@ Nothing here faults, traps or hangs the GPU:
   a short poll limit. Every block gives up at the first barrier, records
   FCM_ERR_TIMEOUT and returns; the same handle then runs the image correctly.
 * An allocation is made to fail by the library's own allocation wrapper
-  (``fail_alloc_in``), without asking the driver for anything; the entry point
+  (``fail_alloc_in``) before it calls cudaMalloc at all; the entry point
   returns FCM_ERR_OOM and a later call completes the workspace.
 """
 import numpy as np
